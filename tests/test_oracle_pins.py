@@ -1,0 +1,423 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by the
+mathematics of the lattice Boltzmann method -- never against the oracle
+itself and never against the CUDA library.
+
+Each test names the passage of Kuron et al. (arXiv:1903.04799) it pins and is
+chosen so that a plausible slip in the oracle (a dropped term, a wrong sign,
+index or weight, a transposed operand) makes it fail.
+"""
+import math
+import os
+from fractions import Fraction
+from itertools import product
+
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def fluid_totals(s):
+    """Mass and momentum of the fluid cells with compensated summation."""
+    f = s.populations()[:, s.owner() == 0]
+    c = O.velocities().astype(float)
+    m = math.fsum(f.ravel())
+    p = np.array([math.fsum((f * c[:, a:a + 1]).ravel()) for a in range(3)])
+    return m, p
+
+
+# --------------------------------------------------------------- Sec. III: D3Q19
+
+def test_velocity_set_is_d3q19():
+    """Sec. III: 19 velocities -- rest, 6 faces, 12 edges; i and its opposite."""
+    c = O.velocities()
+    assert len({tuple(v) for v in c}) == 19
+    norms = sorted(int(v @ v) for v in c)
+    assert norms == [0] + [1] * 6 + [2] * 12
+    for i in range(19):
+        j = O.opposite(i)
+        assert (c[j] == -c[i]).all()
+        assert O.opposite(j) == i
+
+
+def test_weight_isotropy_exact():
+    """Lattice isotropy: sum w = 1, sum w c_a c_b = d_ab / 3,
+    sum w c_a c_b c_c c_d = (d_ab d_cd + d_ac d_bd + d_ad d_bc) / 9, odd moments 0.
+    Checked in exact rationals after recovering each weight as a fraction."""
+    c = O.velocities()
+    w = [Fraction(x).limit_denominator(1000) for x in O.weights()]
+    for x, q in zip(O.weights(), w):
+        assert abs(float(q) - x) < 1e-16
+    assert sum(w) == 1
+    d = lambda a, b: 1 if a == b else 0  # noqa: E731
+    for a in range(3):
+        assert sum(wi * ci[a] for wi, ci in zip(w, c)) == 0
+        for b in range(3):
+            assert sum(wi * ci[a] * ci[b] for wi, ci in zip(w, c)) == Fraction(d(a, b), 3)
+            for g in range(3):
+                assert sum(wi * ci[a] * ci[b] * ci[g] for wi, ci in zip(w, c)) == 0
+                for h in range(3):
+                    m4 = sum(wi * ci[a] * ci[b] * ci[g] * ci[h] for wi, ci in zip(w, c))
+                    assert m4 == Fraction(d(a, b) * d(g, h) + d(a, g) * d(b, h) + d(a, h) * d(b, g), 9)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_equilibrium_moments(seed):
+    """Sec. III (f_eq, read with coefficients 9/2, 3/2): sum f_eq = rho,
+    sum f_eq c = rho u, sum f_eq c c = rho/3 I + rho u u."""
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + 0.1 * rng.standard_normal()
+    u = 0.05 * rng.standard_normal(3)
+    f = O.feq(rho, u)
+    c = O.velocities().astype(float)
+    assert abs(f.sum() - rho) < 1e-15
+    np.testing.assert_allclose(f @ c, rho * u, rtol=0, atol=1e-16)
+    P = np.einsum("i,ia,ib->ab", f, c, c)
+    np.testing.assert_allclose(P, rho / 3 * np.eye(3) + rho * np.outer(u, u), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_collision_conserves_mass_and_momentum(seed):
+    """Eq. "lb": the collision leaves rho and j unchanged (roundoff)."""
+    rng = np.random.default_rng(seed)
+    f = O.weights() * (1.0 + 0.2 * rng.random(19))
+    lo = O.lambda_odd(1.3, 3 / 16)
+    g = O.collide(f, 1.3, lo)
+    r0, j0 = O.moments(f)
+    r1, j1 = O.moments(g)
+    assert abs(r1 - r0) < 1e-15
+    np.testing.assert_allclose(j1, j0, rtol=0, atol=1e-16)
+
+
+def test_trt_relaxes_even_and_odd_parts_separately():
+    """Eq. "lb": the symmetric part relaxes with lambda_e and the antisymmetric
+    part with lambda_o: (f*+ - feq+) = (1 - lambda_e)(f+ - feq+), same for -."""
+    rng = np.random.default_rng(5)
+    f = O.weights() * (1.0 + 0.3 * rng.random(19))
+    le, lo = 0.8, 1.7
+    g = O.collide(f, le, lo)
+    rho, j = O.moments(f)
+    e = O.feq(rho, j / rho)
+    for i in range(19):
+        k = O.opposite(i)
+        fp, fm = (f[i] + f[k]) / 2, (f[i] - f[k]) / 2
+        gp, gm = (g[i] + g[k]) / 2, (g[i] - g[k]) / 2
+        ep, em = (e[i] + e[k]) / 2, (e[i] - e[k]) / 2
+        assert abs((gp - ep) - (1 - le) * (fp - ep)) < 1e-15
+        assert abs((gm - em) - (1 - lo) * (fm - em)) < 1e-15
+
+
+def test_bgk_is_trt_with_equal_rates():
+    """BGK is the special case lambda_o = lambda_e: f* = f - lambda (f - f_eq)."""
+    rng = np.random.default_rng(9)
+    f = O.weights() * (1.0 + 0.3 * rng.random(19))
+    rho, j = O.moments(f)
+    e = O.feq(rho, j / rho)
+    np.testing.assert_allclose(O.collide(f, 0.9, 0.9), f - 0.9 * (f - e), rtol=0, atol=1e-16)
+
+
+def test_magic_parameter():
+    """Sec. III, read as the TRT magic parameter (1/le - 1/2)(1/lo - 1/2) = 3/16:
+    lambda_e = 1 gives lambda_o = 8/7."""
+    assert O.lambda_odd(1.0, 3 / 16) == pytest.approx(8 / 7, rel=1e-15)
+    for le in (0.6, 1.0, 1.5):
+        lo = O.lambda_odd(le, 3 / 16)
+        assert (1 / le - 0.5) * (1 / lo - 0.5) == pytest.approx(3 / 16, rel=1e-14)
+
+
+# --------------------------------------------------------------- lattice dynamics
+
+def _shear_decay_rate(L, le, steps):
+    s = O.OracleSim(1, L, 1, lambda_e=le, collision="bgk")
+    y = np.arange(L)
+    U = 1e-4
+    u = np.zeros((3, L))
+    u[0] = U * np.sin(2 * np.pi * y / L)
+    s.set_equilibrium(np.ones(L), u)
+    s.step(50)  # let the non-equilibrium part settle
+    a0 = s.fields()[1][0] @ np.sin(2 * np.pi * y / L)
+    s.step(steps)
+    a1 = s.fields()[1][0] @ np.sin(2 * np.pi * y / L)
+    k = 2 * np.pi / L
+    return -math.log(a1 / a0) / (k * k * steps)
+
+
+@pytest.mark.parametrize("le", [1.0, 1.6])
+def test_shear_wave_decay_gives_viscosity(le):
+    """Sec. III: eta = rho (1/(3 lambda_e) - 1/6), i.e. nu = (1/le - 1/2)/3.
+    A shear wave decays as exp(-nu k^2 t); the error shrinks ~ L^-2."""
+    nu = (1 / le - 0.5) / 3
+    e64 = abs(_shear_decay_rate(64, le, 2000) / nu - 1)
+    e32 = abs(_shear_decay_rate(32, le, 500) / nu - 1)
+    assert e64 < 1e-3
+    assert e64 < e32 / 3 or e64 < 1e-6
+
+
+def test_periodic_box_conserves_mass_and_momentum():
+    """Sec. I / III: LB conserves mass and momentum to machine precision."""
+    n = 12
+    rng = np.random.default_rng(3)
+    x = np.arange(n)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    ph = rng.random(6) * 2 * np.pi
+    rho = 1 + 0.01 * np.sin(2 * np.pi * X / n + ph[0]) * np.cos(2 * np.pi * Z / n + ph[1])
+    u = 0.02 * np.stack([np.sin(2 * np.pi * Y / n + ph[2]), np.cos(2 * np.pi * Z / n + ph[3]),
+                         np.sin(2 * np.pi * X / n + ph[4])])
+    s = O.OracleSim(n, n, n, lambda_e=1.2, collision="trt")
+    # x-fastest layout: transpose (x,y,z) -> (z,y,x)
+    s.set_equilibrium(rho.transpose(2, 1, 0).ravel(), u.transpose(0, 3, 2, 1).reshape(3, -1))
+
+    def totals():
+        f = s.populations()
+        c = O.velocities().astype(float)
+        return math.fsum(f.ravel()), np.array([math.fsum((f * c[:, a:a + 1]).ravel()) for a in range(3)])
+
+    m0, p0 = totals()
+    s.step(300)
+    m1, p1 = totals()
+    assert abs(m1 - m0) < 1e-11 * m0
+    np.testing.assert_allclose(p1, p0, rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------- Sec. III: walls
+
+def test_couette_flow_is_linear_and_wall_stress_exact():
+    """Sec. III shifted bounce-back: a wall moving at U drives a linear profile
+    between walls located half-way between nodes; the momentum exchange on
+    each wall equals the shear stress rho nu U / H times the wall area."""
+    ny, U, le = 14, 1e-3, 1.0
+    s = O.OracleSim(2, ny, 3, lambda_e=le, collision="bgk")
+    s.add_plane_wall(1, 0)
+    top = s.add_plane_wall(1, ny - 1, vel=(U, 0, 0))
+    s.step(12000)
+    rho, u = s.fields()
+    ux = u[0].reshape(3, ny, 2)[:, :, 0][0]
+    y = np.arange(1, ny - 1)
+    H = ny - 2
+    np.testing.assert_allclose(ux[1:-1], U * (y - 0.5) / H, rtol=1e-9, atol=1e-14)
+    nu = (1 / le - 0.5) / 3
+    F, _ = s.force_torque(top)
+    assert F[0] == pytest.approx(-nu * U / H * 2 * 3, rel=1e-8)
+
+
+@pytest.mark.parametrize("le", [1.0, 1.6])
+def test_trt_poiseuille_exact_with_magic_3_16(le):
+    """Sec. III: with the TRT magic parameter 3/16 (the boundary-faithfulness
+    property of the TRT reference cited there), a body-force-driven channel
+    between bounce-back walls is exactly parabolic with walls half-way
+    between nodes.  The body force here is test-only: the method itself has
+    no external force."""
+    ny, g = 18, 1e-6
+    s = O.OracleSim(1, ny, 1, lambda_e=le, collision="trt", magic=3 / 16)
+    s.add_plane_wall(1, 0)
+    s.add_plane_wall(1, ny - 1)
+    s.set_body_force([g, 0, 0])
+    s.step(40000)
+    rho, u = s.fields()
+    nu = (1 / le - 0.5) / 3
+    y = np.arange(1, ny - 1)
+    exact = g / (2 * nu) * (y - 0.5) * (ny - 1.5 - y)
+    vel = (u[0][1:-1] * rho[1:-1] + g / 2) / rho[1:-1]
+    np.testing.assert_allclose(vel, exact, rtol=1e-8)
+    # a wrong odd rate (the literal reading lambda_o = 3/16 / lambda_e) breaks it
+    bad = O.OracleSim(1, ny, 1, lambda_e=le, collision="trt", magic=3 / 16)
+    bad._lib.osim_destroy(bad._h)
+    bad._h = bad._lib.osim_create(1, ny, 1, le, (3 / 16) / le, 1.0)
+    bad.add_plane_wall(1, 0)
+    bad.add_plane_wall(1, ny - 1)
+    bad.set_body_force([g, 0, 0])
+    bad.step(40000)
+    rb, ub = bad.fields()
+    vb = (ub[0][1:-1] * rb[1:-1] + g / 2) / rb[1:-1]
+    assert np.abs(vb / exact - 1).max() > 1e-3
+
+
+# --------------------------------------------------------------- Sec. II: squirmer
+
+def test_slip_closed_form_in_spherical_coordinates():
+    """Eq. "squirmer": on r = R the slip is tangential with polar component
+    B1 sin(theta) (1 + beta cos(theta)) along the polar unit vector."""
+    rng = np.random.default_rng(11)
+    B1, beta, R = 0.01, -3.0, 7.5
+    for _ in range(50):
+        th, ph = math.acos(rng.uniform(-1, 1)), rng.uniform(0, 2 * math.pi)
+        d = R * np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        theta_hat = np.array([math.cos(th) * math.cos(ph), math.cos(th) * math.sin(ph), -math.sin(th)])
+        v = O.slip(d, [0, 0, 1], B1, beta * B1)
+        np.testing.assert_allclose(v, B1 * math.sin(th) * (1 + beta * math.cos(th)) * theta_hat,
+                                   rtol=0, atol=1e-17)
+    # arbitrary orientation: rotate the frame
+    e = np.array([1.0, 2.0, -2.0]) / 3.0
+    d = np.array([0.3, -0.4, 1.1])
+    v = O.slip(d, e, B1, beta * B1)
+    assert abs(v @ d) < 1e-16 * np.linalg.norm(v) * np.linalg.norm(d)  # tangential
+    ct = e @ d / np.linalg.norm(d)
+    assert np.linalg.norm(v) == pytest.approx(abs(B1 * math.sqrt(1 - ct * ct) * (1 + beta * ct)), rel=1e-13)
+
+
+def test_minimum_image():
+    assert O.min_image(7.0, 16) == 7.0
+    assert O.min_image(8.0, 16) == 8.0       # (-n/2, n/2]: +n/2 stays
+    assert O.min_image(-8.0, 16) == 8.0      # -n/2 maps to +n/2
+    assert O.min_image(9.5, 16) == -6.5
+    assert O.min_image(-12.25, 16) == 3.75
+
+
+@pytest.mark.parametrize("pos,R", [((8.0, 8.0, 8.0), 3.0),          # nodes exactly on |d| = R
+                                   ((0.0, 15.0, 0.5), 4.0),         # wraps on every axis
+                                   ((3.7, 12.2, 9.9), 4.4),
+                                   ((7.5, 7.5, 7.5), 2.5)])
+def test_classification_brute_force(pos, R):
+    """Cells inside a sphere (strict |d| < R, minimum image) match a brute-force
+    scan over the whole lattice -- including the exact ties at |d| = R."""
+    n = 16
+    s = O.OracleSim(n, n, n)
+    oid = s.add_sphere(pos, [0, 0, 1], R, mobile=False)
+    own = s.owner().reshape(n, n, n)  # [z][y][x]
+    for z, y, x in product(range(n), repeat=3):
+        d = [O.min_image(x - pos[0], n), O.min_image(y - pos[1], n), O.min_image(z - pos[2], n)]
+        exp = ((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) < R * R
+        assert (own[z, y, x] == oid) == exp, (x, y, z)
+
+
+def test_links_are_fluid_to_solid_pairs():
+    """Every boundary link joins a fluid node to a solid neighbour, once."""
+    n = 14
+    s = O.OracleSim(n, n, n)
+    s.add_sphere((5.3, 6.1, 12.9), [0, 0, 1], 3.2, mobile=False)
+    own = s.owner()
+    c = O.velocities()
+    links = s.links()
+    exp = []
+    for cell in range(n ** 3):
+        if own[cell]:
+            continue
+        x, y, z = cell % n, (cell // n) % n, cell // (n * n)
+        for i in range(1, 19):
+            nb = ((x + c[i, 0]) % n) + n * (((y + c[i, 1]) % n) + n * ((z + c[i, 2]) % n))
+            if own[nb]:
+                exp.append(cell * 32 + i)
+    assert list(links) == exp
+
+
+# --------------------------------------------------------------- coupling invariants
+
+def test_fixed_neutral_squirmer_symmetry():
+    """A fixed beta = 0 squirmer centred on a node, oriented along +z: by the
+    mirror symmetries of the node set F_x = F_y = 0 and T = 0, and by the
+    z-mirror pairing of links mass is conserved to roundoff (the C1 set-up)."""
+    n = 20
+    s = O.OracleSim(n, n, n, lambda_e=1.0, collision="bgk")
+    oid = s.add_sphere((10, 10, 10), (0, 0, 1), 4.0, B1=0.01, beta=0.0, mobile=False)
+
+    def mass():
+        return math.fsum(s.populations()[:, s.owner() == 0].ravel())
+
+    m0 = mass()
+    s.step(60)
+    F, T = s.force_torque(oid)
+    assert abs(F[0]) < 1e-12 * F[2] and abs(F[1]) < 1e-12 * F[2]
+    assert np.abs(T).max() < 1e-11 * F[2]
+    assert F[2] > 1e-4  # thrust along e on a held squirmer
+    assert abs(mass() - m0) < 1e-12 * m0
+
+
+def test_momentum_balance_fixed_body():
+    """Eqs. "bbforce": the momentum exchange is exactly what the fluid loses:
+    P_fluid(t) + sum_s F_bb(s) = P_fluid(0) for a body that does not move."""
+    n = 16
+    s = O.OracleSim(n, n, n, lambda_e=1.0, collision="trt")
+    oid = s.add_sphere((7.6, 8.2, 8.1), (0.2, 0.5, 1.0), 4.3, B1=0.01, beta=2.0, mobile=False)
+    _, p0 = fluid_totals(s)
+    acc = np.zeros(3)
+    for _ in range(80):
+        s.step(1)
+        acc += s.force_torque(oid)[0]
+    _, p1 = fluid_totals(s)
+    np.testing.assert_allclose(p1 + acc, p0, rtol=0, atol=1e-13)
+    assert np.abs(acc).max() > 1e-3
+
+
+def test_momentum_balance_free_swimmer():
+    """Sec. III: with conversion forces (Eq. "consforce") and momentum exchange
+    the total momentum fluid + body (+ booked conversion force) is conserved
+    exactly while the body moves and cells change between fluid and solid."""
+    n = 20
+    s = O.OracleSim(n, n, n, lambda_e=1.0, collision="trt")
+    oid = s.add_sphere((9.7, 10.2, 10.1), (0.3, 0.2, 1.0), 4.0, B1=0.02, beta=-3.0, mobile=True)
+    M = 4 / 3 * math.pi * 4 ** 3
+    changed = 0
+    prev = s.owner()
+    for _ in range(250):
+        s.step(1)
+        own = s.owner()
+        changed += int((own != prev).sum())
+        prev = own
+        _, P = fluid_totals(s)
+        _, v, _, _ = s.state(oid)
+        Fc, _ = s.pending_conversion(oid)
+        np.testing.assert_allclose(P + M * v + Fc, 0.0, rtol=0, atol=1e-12)
+    assert changed > 0
+
+
+def test_swim_speed_matches_fig_resolution():
+    """Eq. "squirmer-speed" and Fig. "resolution": a free squirmer of R = 4 in a
+    periodic box L = 10R swims at the speed the paper prints, 0.9737 v0
+    (v0 = 2 B1 / 3), within 1.5%."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "fig_resolution_squirmer.txt"))
+    ref = rows[(rows[:, 0] == 4) & (rows[:, 1] == 10)][0, 2]
+    R, L, B1 = 4, 40, 0.01
+    s = O.OracleSim(L, L, L, lambda_e=1.0, collision="trt")
+    oid = s.add_sphere((L / 2 + 0.1, L / 2 + 0.2, L / 2), (0, 0, 1), R, B1=B1, beta=0.0)
+    vs = []
+    for k in range(1500):
+        s.step(1)
+        if k >= 750:
+            _, v, e, _ = s.state(oid)
+            vs.append(v @ e)
+    ratio = np.mean(vs) / (2 * B1 / 3)
+    assert abs(ratio / ref - 1) < 0.015, ratio
+
+
+def test_stresslet_sign_pusher_and_puller():
+    """Eq. "squirmerflow": the B2 term is a force dipole of strength
+    S = -4 pi eta R^2 B2 (e e - I/3) exerted on the fluid -- extensile
+    (S_zz > 0) for a pusher (beta < 0), contractile for a puller."""
+    R, L, B1 = 4, 24, 0.01
+    eta = 1 / 6
+    out = {}
+    for beta in (-5.0, 5.0):
+        s = O.OracleSim(L, L, L, lambda_e=1.0, collision="trt")
+        oid = s.add_sphere((L / 2, L / 2, L / 2), (0, 0, 1), R, B1=B1, beta=beta, mobile=True)
+        acc = np.zeros(6)
+        for k in range(600):
+            s.step(1)
+            if k >= 300:
+                acc += s.stresslet(oid)
+        out[beta] = acc / 300
+    for beta, S in out.items():
+        exp_zz = -4 * math.pi * eta * R * R * beta * B1 * 2 / 3
+        assert np.sign(S[2]) == np.sign(exp_zz)
+        assert 0.5 < S[2] / exp_zz < 1.5, (beta, S)
+        assert abs(S[0] + S[1] + S[2]) < 1e-12  # traceless
+
+
+# --------------------------------------------------------------- Eq. "wca"
+
+def test_wca_force_is_minus_gradient_and_cut():
+    """Eq. "wca" (read as -dU/dr of the shifted Lennard-Jones potential): the
+    force equals a numerical derivative of U and vanishes at 2^(1/6) sigma."""
+    sig, eps = 1.0, 0.01
+
+    def U(r):
+        return 4 * eps * ((sig / r) ** 12 - (sig / r) ** 6) + eps
+
+    for r in (0.9, 1.0, 1.05, 1.1):
+        h = 1e-6
+        assert O.wca(r, sig, eps) == pytest.approx(-(U(r + h) - U(r - h)) / (2 * h), rel=1e-6)
+    rc = 2 ** (1 / 6) * sig
+    assert O.wca(rc, sig, eps) == 0.0
+    assert abs(O.wca(rc - 1e-9, sig, eps)) < 1e-6
+    assert U(rc) == pytest.approx(0.0, abs=1e-15)
