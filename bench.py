@@ -1,0 +1,377 @@
+"""Benchmark of the lattice Boltzmann squirmer hot path on GB300.
+
+One step = one whole time step of the method on the device: fused TRT
+stream-collide of every cell, shifted bounce-back on every boundary link with
+the squirmer surface velocity, FP64 momentum-exchange force/torque reduction,
+symplectic Euler update, and (when a lattice node crosses the surface) cell
+conversion and link rebuild.
+
+Headline: the 128^3 free-swimmer configuration (R = 8, B1 = 0.005, beta = 0,
+TRT magic 3/16) with FP32 deviation storage, in MLUPS (million lattice-cell
+updates per second, all cells counted).  L2 is flushed (512 MiB write)
+before every timed step and the flush is outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--skip-accuracy] [--skip-extra]
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank advances its own
+lattice (independent replicas, weak scaling); time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline, mixed-prec vs FP64 (≤1e-3 U err); p50/p99 latency"
+FALLBACK_HBM_GBS = 6800.0
+BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+ARITH = {"f64": "f64", "f32": "f32", "f16dev": "f32", "bf16dev": "f32"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def sweep_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "lbsq_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1903_04799_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key: str):
+    """DRAM bytes per launch of the sweep from a committed ncu summary, or None
+    when there is none or the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(key)
+    if not d or d.get("source_sha") != sweep_source_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during a timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        load = [s for s in sm if smax and s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def build_lattice(storage, shape, bodies, collision="trt", lambda_e=1.0, device=0):
+    from paper_1903_04799_gb300 import Lattice
+    g = Lattice(shape, collision=collision, lambda_e=lambda_e, storage=storage, device=device)
+    ids = [g.add_squirmer(b.pos, b.e, b.R, b.B1, b.beta, mobile=b.mobile) for b in bodies]
+    return g, ids
+
+
+def timed_steps(g, steps, flush, torch):
+    """K steps, each between CUDA events on the lattice's stream, L2 flushed
+    before each (outside the events); kernels traced with events too."""
+    s = torch.cuda.ExternalStream(g._stream.cuda_stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches0 = g.launches
+    g.profile_begin()
+    with torch.cuda.stream(s):
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(s)
+            g.step(1)
+            ev[k][1].record(s)
+    prof = g.profile_end()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    return step_ms, prof, g.launches - launches0
+
+
+def run_variant(storage, wl, steps, warmup, flush, torch, device=0):
+    g, ids = build_lattice(storage, wl.shape, wl.bodies, wl.collision, wl.lambda_e, device)
+    g.step(warmup)
+    g.sync()
+    step_ms, prof, launches = timed_steps(g, steps, flush, torch)
+    g.close()
+    total = sum(step_ms)
+    cells = wl.cells
+    sweep_ms = prof["sweep"][0] / max(prof["sweep"][1], 1)
+    return {"ms_per_step": total / steps, "mlups": cells * steps / (total * 1e-3) / 1e6,
+            "sweep_ms": sweep_ms, "sweep_bytes": cells * 2 * 19 * BYTES[storage],
+            "kernels_ms": {k: v[0] / max(steps, 1) for k, v in prof.items()},
+            "launches": launches}
+
+
+def swim_speed(storage, wl, torch, device=0, chunk=200):
+    g, ids = build_lattice(storage, wl.shape, wl.bodies, wl.collision, wl.lambda_e, device)
+    v = []
+    steps = wl.steps
+    for k in range(0, steps, chunk):
+        g.step(chunk)
+        if k >= steps // 2:
+            _, vel, e, _ = g.state(ids[0])
+            v.append(float(vel @ e))
+    g.close()
+    return float(np.mean(v))
+
+
+def e2e_run(wl, storage, steps, device, torch):
+    """The public API end to end from host buffers: initial fields uploaded,
+    every step the body's trajectory read back, the fields read at the end."""
+    from paper_1903_04799_gb300 import workloads as W
+    from paper_1903_04799_gb300 import lbsq
+    rho, u = W.smooth_fields(wl.shape, seed=1, drho=0.0, umax=0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g, ids = build_lattice(storage, wl.shape, wl.bodies, wl.collision, wl.lambda_e, device)
+    g.set_fields(rho, u)
+    traj = np.empty((steps, 12))
+    for k in range(steps):
+        g.step(1)
+        p, vel, e, w = g.state(ids[0])
+        traj[k] = np.concatenate([p, vel, e, w])
+    rho_out, u_out = g.fields()
+    g.close()
+    t = time.perf_counter() - t0
+    N = wl.cells
+    return {"value": N * steps / t / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": int(4 * N * 8 / steps),
+            "d2h_bytes_per_step": int(12 * 8 + 4 * N * 8 / steps),
+            "steps": steps, "wall_s": t}
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    """The oracle as it stands, on the host cores, a bounded sample of the workload."""
+    from oracle import oracle as O
+    s = O.OracleSim(*wl.shape, lambda_e=wl.lambda_e, collision=wl.collision)
+    for b in wl.bodies:
+        s.add_sphere(b.pos, b.e, b.R, b.B1, b.beta, b.mobile)
+    s.step(1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and n < 10000:
+        s.step(1)
+        n += 1
+    t = time.perf_counter() - t0
+    return {"value": wl.cells * n / t / 1e6, "unit": "MLUPS", "cores": O.num_threads(),
+            "kind": "oracle", "sample": f"{n} full time steps of {wl.name} after 1 warm-up step"}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, ws, local, dist
+
+
+def ours(args):
+    import torch
+    from paper_1903_04799_gb300 import lbsq
+    from paper_1903_04799_gb300 import workloads as W
+    rank, ws, local, dist = dist_init()
+    torch.cuda.set_device(local)
+    lbsq.load()
+    hbm, peak_kind = peaks()
+    wl = W.c2_free_swimmer(beta=0.0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    head = args.storage
+
+    # ---- headline timed region
+    g, ids = build_lattice(head, wl.shape, wl.bodies, wl.collision, wl.lambda_e, local)
+    g.step(args.warmup)
+    g.sync()
+    clocks = ClockSampler(local) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    step_ms, prof, launches = timed_steps(g, args.steps, flush, torch)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    g.close()
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    cells = wl.cells
+    value = ws * cells * args.steps / (total_ms * 1e-3) / 1e6
+    sweep_ms = prof["sweep"][0] / max(prof["sweep"][1], 1)
+    sweep_bytes = cells * 2 * 19 * BYTES[head]
+    achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    res = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": ARITH[head],
+        "data": "synthetic",
+        "config": {"workload": wl.name, "shape": list(wl.shape), "R": 8, "B1": 0.005, "beta": 0.0,
+                   "collision": "trt(lambda_e=1, magic=3/16)", "storage": head,
+                   "step": "sweep + links/force/Newton-Euler + classify + convert + rebuild",
+                   "l2": "flushed before every timed step (512 MiB write, outside the events)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": ncu_traffic(f"sweep_{head}_{wl.name}"),
+                     "kernel": "k_sweep", "bytes_per_launch": sweep_bytes,
+                     "per_unit": f"2*19*{BYTES[head]} B per cell update", "peak_kind": peak_kind,
+                     "sweep_ms": sweep_ms},
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if ws == 1:
+        variants = {head: {"mlups": value, "sweep_frac": achieved / hbm}}
+        if not args.skip_variants:
+            for st in ("f64", "f32", "f16dev", "bf16dev"):
+                if st == head:
+                    continue
+                r = run_variant(st, wl, min(args.steps, 1000), args.warmup, flush, torch, local)
+                variants[st] = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"],
+                                "sweep_frac": r["sweep_bytes"] / (r["sweep_ms"] * 1e-3) / 1e9 / hbm,
+                                "kernels_ms_per_step": r["kernels_ms"]}
+            res["mixed_vs_f64"] = {st: variants[st]["mlups"] / variants["f64"]["mlups"]
+                                   for st in variants if "f64" in variants}
+        res["variants"] = variants
+        if not args.skip_accuracy:
+            acc = {}
+            v0 = 2 * 0.005 / 3
+            ref = None
+            for st in ("f64", "f32", "f16dev", "bf16dev"):
+                U = swim_speed(st, wl, torch, local)
+                ref = U if st == "f64" else ref
+                acc[st] = {"U_over_v0": U / v0, "rel_err_vs_f64": abs(U - ref) / abs(ref)}
+            res["swim_speed_c2"] = {"steps": wl.steps, "window": "mean of v.e over the last half", **acc}
+        if not args.skip_extra:
+            extra = {}
+            for wlx, sts in ((W.c3_pusher(), ("f64", "f32", "f16dev", "bf16dev")), (W.c4_suspension(), ("f32",))):
+                for st in sts:
+                    r = run_variant(st, wlx, 30, 3, flush, torch, local)
+                    extra[f"{wlx.name}_{st}"] = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"],
+                                                 "sweep_frac": r["sweep_bytes"] / (r["sweep_ms"] * 1e-3) / 1e9 / hbm,
+                                                 "kernels_ms_per_step": r["kernels_ms"]}
+            res["extra"] = extra
+        res["e2e"] = e2e_run(wl, head, min(args.steps, 1000), local, torch)
+        if not args.skip_cpu:
+            res["cpu_baseline"] = cpu_baseline(wl)
+    else:
+        res["e2e"] = None
+    print(json.dumps(res), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+
+def reference(args):
+    """The oracle timed as it stands on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1903_04799_gb300 import workloads as W
+    wl = W.c2_free_swimmer(beta=0.0)
+    s = O.OracleSim(*wl.shape, lambda_e=wl.lambda_e, collision=wl.collision)
+    for b in wl.bodies:
+        s.add_sphere(b.pos, b.e, b.R, b.B1, b.beta, b.mobile)
+    for _ in range(args.warmup):
+        s.step(1)
+    budget, n, t0 = 150.0, 0, time.perf_counter()
+    while n < args.steps and time.perf_counter() - t0 < budget:
+        s.step(1)
+        n += 1
+    t = time.perf_counter() - t0
+    v = wl.cells * n / t / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": 0,
+        "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(n, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "shape": list(wl.shape), "storage": "f64 (oracle)"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{n} of the requested {args.steps} full time steps of {wl.name} "
+                                   f"(bounded to {budget:.0f} s)"},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=list(BYTES))
+    ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true")
+    ap.add_argument("--skip-variants", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

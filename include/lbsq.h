@@ -1,0 +1,225 @@
+/*
+ * lbsq.h -- C ABI of a GB300-native (sm_103a) lattice Boltzmann library for
+ * squirmers, after Kuron, Staerk, Burkard, de Graaf & Holm, "A Lattice
+ * Boltzmann Model for Squirmers" (arXiv:1903.04799).
+ *
+ * One context = one periodic D3Q19 lattice resident on one GPU, with
+ * spherical bodies (squirmers, fixed obstacles) and plane walls.  One time
+ * step does, on the GPU:
+ *   - the fused stream-collide of every cell with the TRT (or BGK) operator
+ *     of Sec. III, Eq. "lb" (in-place AA pattern, populations stored as FP64,
+ *     or as FP32 / FP16 / BF16 deviations from w_i rho0 collided in FP32);
+ *   - shifted link bounce-back on every boundary link (Sec. III), with the
+ *     wall velocity v + omega x r of Eq. "vb" plus the squirmer slip of
+ *     Eq. "squirmer";
+ *   - the momentum-exchange force and torque of Eqs. "bbforce", "bbtorque"
+ *     summed per body in FP64 in a fixed order;
+ *   - a symplectic Euler update of every mobile sphere (Sec. III, last
+ *     paragraph), including the optional WCA contact force of Eq. "wca";
+ *   - the fluid/solid conversion of cells a moving sphere covers or
+ *     uncovers, with the conversion force of Eq. "consforce", and the
+ *     rebuild of the boundary-link lists.
+ *
+ * Conventions
+ *   - Units are lattice units (a_grid = tau_grid = 1).
+ *   - Cells are indexed x-fastest: n = x + nx*(y + ny*z), 0 <= x < nx ...
+ *   - The lattice is periodic on all three axes; confinement is built from
+ *     wall cells (lb_add_wall).
+ *   - Every call returns an lb_status; out-parameters are written only on
+ *     LB_OK.  No C++ exception crosses this boundary.
+ *   - lb_step is stream-ordered: it enqueues work on the context's stream
+ *     and returns.  Errors found on the device (overlap, capacity, a
+ *     diverged body) are reported by the next synchronising call (lb_sync
+ *     and every getter).  An error found on the device is sticky: the
+ *     context then refuses lb_step with LB_ERR_STATE.
+ *   - A context must not be used from two host threads at once.
+ *   - Host buffers passed in are read or written before the call returns;
+ *     the library keeps no pointer to them.  Device memory is owned by the
+ *     context and freed by lb_destroy.
+ *
+ * D3Q19 velocity order (the layout of population arrays in this API):
+ *   i = 0 rest; 1,2 = (+-1,0,0); 3,4 = (0,+-1,0); 5,6 = (0,0,+-1);
+ *   7,8 = +-(1,1,0); 9,10 = +-(1,-1,0); 11,12 = +-(1,0,1); 13,14 = +-(1,0,-1);
+ *   15,16 = +-(0,1,1); 17,18 = +-(0,1,-1).  The opposite of i >= 1 is
+ *   i+1 for odd i and i-1 for even i.
+ */
+#ifndef LBSQ_H
+#define LBSQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_INVALID = 1,  /* bad argument; nothing changed */
+    LB_ERR_OOM = 2,      /* device allocation failed */
+    LB_ERR_CUDA = 3,     /* a CUDA runtime call failed (message in lb_last_error) */
+    LB_ERR_OVERLAP = 4,  /* a body overlaps another body or a wall */
+    LB_ERR_DIVERGED = 5, /* a body reached |v| >= 1/2 (the scheme needs |v| << 1) */
+    LB_ERR_TIMEOUT = 6,  /* a bounded device wait ran out */
+    LB_ERR_STATE = 7,    /* the context holds an earlier device error */
+    LB_ERR_CAPACITY = 8  /* a boundary-link list outgrew its capacity */
+} lb_status;
+
+typedef enum { LB_BGK = 0, LB_TRT = 1 } lb_collision;
+
+/* Population storage.  LB_F64 stores f_i; the others store the deviation
+ * d_i = f_i - w_i rho0 (FP16 scaled by 2^dev_scale_log2), decoded to FP32,
+ * collided in FP32 and rounded to nearest even on store.  Bodies, forces and
+ * the Newton-Euler update are FP64 for every storage. */
+typedef enum { LB_F64 = 0, LB_F32 = 1, LB_F16DEV = 2, LB_BF16DEV = 3 } lb_storage;
+
+/* Optional device allocator (for example a caching allocator of the host
+ * framework).  alloc returns a device pointer of at least `bytes` bytes on
+ * the context's device, or NULL; free receives the same pointer and size. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, size_t bytes, void* user);
+    void* user;
+} lb_allocator;
+
+typedef struct {
+    int32_t nx, ny, nz;  /* lattice size, each >= 1; nx*ny*nz < 2^31 */
+    int32_t collision;   /* lb_collision */
+    double lambda_e;     /* even (viscous) relaxation rate, 0 < lambda_e < 2;
+                            kinematic viscosity (1/lambda_e - 1/2)/3 (Sec. III) */
+    double magic;        /* TRT magic parameter (1/le - 1/2)(1/lo - 1/2),
+                            3/16 in the paper; ignored for BGK (lo = le) */
+    double rho0;         /* rest density, > 0 */
+    int32_t storage;     /* lb_storage */
+    int32_t dev_scale_log2; /* FP16 deviation scale exponent; -1 = default (20) */
+    int32_t device;      /* CUDA device ordinal */
+    void* stream;        /* cudaStream_t to run on; NULL = a stream the context creates */
+    const lb_allocator* allocator; /* NULL = cudaMalloc / cudaFree */
+} lb_params;
+
+/* Fill *p with: 32^3, BGK, lambda_e = 1, magic = 3/16, rho0 = 1, FP64,
+ * default FP16 scale, device 0, own stream, cudaMalloc. */
+void lb_params_default(lb_params* p);
+
+/* Create a lattice with every population at rest equilibrium w_i rho0 and
+ * every cell fluid (Sec. III).  *out receives the context.  Errors:
+ * LB_ERR_INVALID (sizes, rates, storage), LB_ERR_OOM, LB_ERR_CUDA. */
+lb_status lb_create(const lb_params* p, lb_ctx** out);
+
+/* Free all device memory of the context.  NULL is accepted. */
+lb_status lb_destroy(lb_ctx* c);
+
+/* Add a sphere of radius R centred at pos (wrapped into the box) with unit
+ * orientation e (normalised here) and squirmer modes B1, B2 = beta*B1
+ * (Sec. II, Eq. "squirmer"; B1 = 0 gives a passive sphere).  mobile = 0
+ * holds it fixed (force and torque still measured), mobile = 1 lets the
+ * Newton-Euler update move it.  density: body density (mass
+ * density * 4/3 pi R^3, moment of inertia 2/5 M R^2).  Cells whose node
+ * lies strictly inside (|d| < R, minimum image) become solid.  *id
+ * receives the body id (>= 1).  Errors: LB_ERR_INVALID (R <= 0,
+ * 2R + 6 >= min(n), |e| = 0, density <= 0), LB_ERR_OVERLAP (a covered
+ * cell is already solid; nothing changed). */
+lb_status lb_add_squirmer(lb_ctx* c, const double pos[3], const double e[3], double R, double B1,
+                          double beta, int32_t mobile, double density, int32_t* id);
+
+/* Add a wall (static boundary, Sec. III shifted bounce-back).
+ *   kind 0, plane wall:  params = {axis, index [, vx, vy, vz]} -- one layer
+ *           of solid cells at coordinate `index` along `axis` (0,1,2),
+ *           moving with velocity v (default 0, a no-slip wall);
+ *   kind 1, square tube along z: params = {} -- plane walls at x = 0,
+ *           x = nx-1, y = 0, y = ny-1 (four ids; *id receives the first);
+ *   kind 2, fixed sphere obstacle: params = {x, y, z, radius} -- a body that
+ *           never moves and has no slip (Sec. V B obstacle).
+ * Errors: LB_ERR_INVALID, LB_ERR_OVERLAP. */
+lb_status lb_add_wall(lb_ctx* c, int32_t kind, const double* params, int32_t nparams, int32_t* id);
+
+/* WCA contact force (Eq. "wca") between mobile spheres and every other body
+ * and wall, as a function of the surface gap r: -dU/dr of
+ * U = 4 eps((sigma/r)^12 - (sigma/r)^6) + eps for r < 2^(1/6) sigma (gap
+ * clamped below at 0.05 sigma).  eps = 0 (default) switches it off. */
+lb_status lb_set_contact(lb_ctx* c, double sigma, double eps);
+
+/* Set every cell's populations to the equilibrium of host fields rho[N] and
+ * u[3][N] (SoA, x-fastest).  Solid cells are overwritten too (harmless). */
+lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u);
+
+/* Copy all populations from / to a host buffer f[19][N] (absolute values
+ * f_i, velocity order above).  Reduced storages round on set. */
+lb_status lb_set_populations(lb_ctx* c, const double* f);
+lb_status lb_get_populations(lb_ctx* c, double* f);
+
+/* Enqueue nsteps >= 0 time steps.  Errors: LB_ERR_INVALID, LB_ERR_STATE,
+ * LB_ERR_CUDA. */
+lb_status lb_step(lb_ctx* c, int64_t nsteps);
+
+/* Wait for the context's stream and report the device error word. */
+lb_status lb_sync(lb_ctx* c);
+
+/* Steps taken so far. */
+int64_t lb_step_count(const lb_ctx* c);
+
+/* Macroscopic fields (Sec. III): rho[N] and u[3][N] with u = j / rho, into
+ * caller-owned HOST buffers; solid cells report 0.  Either pointer may be
+ * NULL.  Synchronises. */
+lb_status lb_get_fields(lb_ctx* c, double* rho, double* u);
+
+/* As lb_get_fields, into caller-owned DEVICE buffers on the context's
+ * device; stream-ordered (does not synchronise). */
+lb_status lb_get_fields_device(lb_ctx* c, double* rho_dev, double* u_dev);
+
+/* Cell owners into a host buffer owner[N]: 0 = fluid, else the body or wall id. */
+lb_status lb_get_owner(lb_ctx* c, int32_t* owner);
+
+/* Hydrodynamic force and torque on body `id` that entered the last update:
+ * momentum exchange of the last step (Eqs. "bbforce", "bbtorque") plus the
+ * conversion force booked by the step before (Eq. "consforce"); FP64.  For
+ * walls the momentum exchange of the last step.  Synchronises. */
+lb_status lb_get_force_torque(lb_ctx* c, int32_t id, double F[3], double T[3]);
+
+/* Position, velocity, orientation and angular velocity of body `id`.
+ * Synchronises.  Any pointer may be NULL. */
+lb_status lb_get_object_state(lb_ctx* c, int32_t id, double pos[3], double vel[3], double e[3],
+                              double omega[3]);
+
+/* Stresslet exerted on the fluid by body `id` in the last step:
+ * S = -sum_links symtraceless(d (x) dF), d the link midpoint relative to
+ * the centre and dF the momentum given to the body on that link; order
+ * xx, yy, zz, xy, xz, yz.  The far field of Eq. "squirmerflow" gives
+ * S = -4 pi eta R^2 B2 (e e - I/3).  Synchronises. */
+lb_status lb_get_stresslet(lb_ctx* c, int32_t id, double S[6]);
+
+/* Mass sum(rho) and momentum sum(j) over fluid cells, FP64, summed in a
+ * fixed order (conserved to roundoff, Sec. I).  Either pointer may be NULL.
+ * Synchronises. */
+lb_status lb_get_mass(lb_ctx* c, double* mass, double mom[3]);
+
+/* Boundary links of body `id` (0 = all bodies, by id), each as
+ * cell_index * 32 + direction i, where cell_index is the fluid node and
+ * node + c_i the solid one.  Writes at most cap entries; *count receives
+ * the number of links.  Synchronises. */
+lb_status lb_get_links(lb_ctx* c, int32_t id, int64_t* out, int64_t cap, int64_t* count);
+
+/* Message of the last failing call on c, or "" -- valid until the next call on c. */
+const char* lb_last_error(const lb_ctx* c);
+
+/* Number of kernel launches the context has enqueued so far (all kinds). */
+int64_t lb_kernel_launches(const lb_ctx* c);
+
+/* Kernel tracing.  Between lb_profile_begin and lb_profile_end, lb_step
+ * launches each kernel of a step directly (no graph) with a CUDA event
+ * recorded on the context's stream before and after it.  lb_profile_end
+ * synchronises and writes, per kernel kind in launch order
+ *   0 sweep, 1 links (bounce-back, force reduction, Newton-Euler),
+ *   2 classify, 3 convert, 4 rebuild,
+ * the summed device time in ms (total_ms[5]) and the launch count
+ * (launches[5]).  Either pointer may be NULL. */
+lb_status lb_profile_begin(lb_ctx* c);
+lb_status lb_profile_end(lb_ctx* c, double total_ms[5], int64_t launches[5]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBSQ_H */

@@ -382,14 +382,17 @@ int32_t osim_add_sphere(osim* s, const double* pos, const double* e, double R, d
 }
 
 /* Add a plane wall: one layer of solid cells at coordinate `index` along `axis`,
- * moving with velocity `vel` (zero for a no-slip wall).  Returns id or -error. */
+ * moving with velocity `vel` (zero for a no-slip wall).  Cells of the layer
+ * that already belong to another wall stay with it (the corner columns of a
+ * tube); a cell owned by a sphere is an overlap.  Returns id or -error. */
 int32_t osim_add_plane_wall(osim* s, int32_t axis, int32_t index, const double* vel) {
     int n[3] = {s->nx, s->ny, s->nz};
     if (axis < 0 || axis > 2 || index < 0 || index >= n[axis]) return -OERR_INVALID;
     for (long c = 0; c < s->N; ++c) {
         int x[3];
         coords(s, c, &x[0], &x[1], &x[2]);
-        if (x[axis] == index && s->owner[c] != 0) return -OERR_OVERLAP;
+        if (x[axis] == index && s->owner[c] != 0 && s->obj[s->owner[c] - 1].kind == OBJ_SPHERE)
+            return -OERR_OVERLAP;
     }
     oobj* o = new_object(s);
     o->kind = OBJ_WALL;
@@ -400,7 +403,7 @@ int32_t osim_add_plane_wall(osim* s, int32_t axis, int32_t index, const double* 
     for (long c = 0; c < s->N; ++c) {
         int x[3];
         coords(s, c, &x[0], &x[1], &x[2]);
-        if (x[axis] == index) s->owner[c] = id;
+        if (x[axis] == index && s->owner[c] == 0) s->owner[c] = id;
     }
     s->nobj++;
     return id;

@@ -1,0 +1,814 @@
+// api.cu -- the C ABI of include/lbsq.h: context life cycle, validation,
+// device memory, body set-up and the per-step launch sequence (replayed from
+// a CUDA graph of two steps, even + odd, once the body set is fixed).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbsq.h"
+#include "lbsq_internal.cuh"
+
+namespace lbsq {
+void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, cudaStream_t st);
+void launch_body_step(const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
+                      cudaStream_t st);
+void launch_relink(const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
+                   cudaStream_t st);
+void launch_fill_rest(const Lattice& L, cudaStream_t st);
+void launch_set_eq(const Lattice& L, const double* rho, const double* u, int q, cudaStream_t st);
+void launch_set_pop(const Lattice& L, const double* f, int q, cudaStream_t st);
+void launch_get_pop(const Lattice& L, double* f, int q, cudaStream_t st);
+void launch_fields(const Lattice& L, const int32_t* own, double* rho, double* u, int q, cudaStream_t st);
+int mass_partial_blocks(const Lattice& L);
+void launch_mass(const Lattice& L, const int32_t* own, double* part, double* out, int q, cudaStream_t st);
+void launch_sphere_overlap(const Lattice& L, const int32_t* own, const double* pos, double R, int W, int* count,
+                           cudaStream_t st);
+void launch_plane_overlap(const Lattice& L, const int32_t* own, const int* kind, int axis, int index, int* count,
+                          cudaStream_t st);
+void launch_plane_claim(const Lattice& L, int32_t* own, int axis, int index, int id, cudaStream_t st);
+void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, int relink, cudaStream_t st);
+void launch_classify_only(const Lattice& L, const Bodies& B, int32_t* own, const int32_t* own_prev, int parity,
+                          cudaStream_t st);
+void launch_body_kernel(int which, const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
+                        cudaStream_t st);
+}  // namespace lbsq
+
+using namespace lbsq;
+
+struct lb_ctx {
+    lb_params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Lattice L{};
+    double lambda_e = 1.0, lambda_o = 1.0;
+    int32_t* own = nullptr;
+    int32_t* own_prev = nullptr;
+    // bodies
+    std::vector<BodyParams> par;
+    std::vector<int> kind;
+    int cap = 0;
+    BodyParams* d_par = nullptr;
+    BodyState* d_state[2] = {nullptr, nullptr};
+    BodyAcc* d_acc = nullptr;
+    int* d_kind = nullptr;
+    uint32_t* d_links = nullptr;
+    int64_t links_total = 0;
+    double* d_part_links = nullptr;
+    double* d_part_conv = nullptr;
+    int* d_part_count = nullptr;
+    int G_links = 1, G_box = 1;
+    double wca_sigma = 1.0, wca_eps = 0.0;
+    // scratch
+    double* d_mass_part = nullptr;
+    double* d_small = nullptr;  // 8 doubles
+    int* d_err = nullptr;
+    int* d_count = nullptr;
+    double* d_fields = nullptr;  // 4 N doubles, allocated on first host export
+    double* d_pop = nullptr;     // 19 N doubles, allocated on first population I/O
+    // bookkeeping
+    int64_t step = 0;
+    int64_t launches = 0;
+    int sticky = 0;
+    std::string msg;
+    std::vector<std::pair<void*, size_t>> allocs;
+    // graph of two steps (even then odd)
+    cudaGraphExec_t graph = nullptr;
+    // kernel tracing
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_used;  // (kernel kind, index of the start event)
+};
+
+namespace {
+
+lb_status fail(lb_ctx* c, lb_status s, const std::string& m) {
+    if (c) c->msg = m;
+    return s;
+}
+
+lb_status cuda_fail(lb_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, LB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+void* dalloc(lb_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (c->p.allocator && c->p.allocator->alloc) {
+        p = c->p.allocator->alloc(bytes, c->p.allocator->user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocs.emplace_back(p, bytes);
+    return p;
+}
+
+void dfree(lb_ctx* c, void* p) {
+    if (!p) return;
+    for (size_t k = 0; k < c->allocs.size(); ++k) {
+        if (c->allocs[k].first == p) {
+            if (c->p.allocator && c->p.allocator->free) c->p.allocator->free(p, c->allocs[k].second, c->p.allocator->user);
+            else cudaFree(p);
+            c->allocs.erase(c->allocs.begin() + k);
+            return;
+        }
+    }
+}
+
+template <class T>
+T* dalloc_t(lb_ctx* c, size_t n) {
+    return (T*)dalloc(c, n * sizeof(T));
+}
+
+void drop_graph(lb_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+Bodies bodies_view(const lb_ctx* c) {
+    Bodies B;
+    B.n = (int)c->par.size();
+    B.par = c->d_par;
+    B.state[0] = c->d_state[0];
+    B.state[1] = c->d_state[1];
+    B.acc = c->d_acc;
+    B.links = c->d_links;
+    B.part_links = c->d_part_links;
+    B.part_conv = c->d_part_conv;
+    B.part_count = c->d_part_count;
+    B.G_links = c->G_links;
+    B.G_box = c->G_box;
+    B.wca_sigma = c->wca_sigma;
+    B.wca_eps = c->wca_eps;
+    B.err = c->d_err;
+    return B;
+}
+
+// Upper bound on the boundary links of a sphere of radius R: 18 per lattice
+// node within the shell R - 0.9 < |d| < R + 2.3 (covers any centre offset).
+int64_t sphere_link_cap(double R) {
+    double a = R + 2.3, b = std::max(R - 0.9, 0.0);
+    double v = 4.0 / 3.0 * M_PI * (a * a * a - b * b * b);
+    return 18 * (int64_t)std::ceil(v) + 64;
+}
+
+bool check_device_error(lb_ctx* c, lb_status* out) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        *out = cuda_fail(c, e, "synchronise");
+        return true;
+    }
+    if (h != 0) {
+        c->sticky = h;
+        const char* what = h == LB_ERR_OVERLAP    ? "a body overlaps another body or a wall"
+                           : h == LB_ERR_DIVERGED ? "a body reached |v| >= 1/2"
+                           : h == LB_ERR_CAPACITY ? "a boundary-link list outgrew its capacity"
+                                                  : "device error";
+        *out = fail(c, (lb_status)h, what);
+        return true;
+    }
+    return false;
+}
+
+lb_status sync_checked(lb_ctx* c) {
+    lb_status s;
+    if (check_device_error(c, &s)) return s;
+    return LB_OK;
+}
+
+// Grow the body arrays to hold at least n bodies, keeping their contents.
+lb_status ensure_body_capacity(lb_ctx* c, int n) {
+    if (n <= c->cap) return LB_OK;
+    int nc = std::max(8, c->cap * 2);
+    while (nc < n) nc *= 2;
+    BodyParams* par = dalloc_t<BodyParams>(c, nc);
+    BodyState* s0 = dalloc_t<BodyState>(c, nc);
+    BodyState* s1 = dalloc_t<BodyState>(c, nc);
+    BodyAcc* acc = dalloc_t<BodyAcc>(c, nc);
+    int* kind = dalloc_t<int>(c, nc);
+    if (!par || !s0 || !s1 || !acc || !kind) return fail(c, LB_ERR_OOM, "body arrays");
+    CK(cudaMemsetAsync(acc, 0, sizeof(BodyAcc) * nc, c->stream));
+    int nb = (int)c->par.size();
+    if (nb > 0) {
+        CK(cudaMemcpyAsync(par, c->d_par, sizeof(BodyParams) * nb, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(s0, c->d_state[0], sizeof(BodyState) * nb, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(s1, c->d_state[1], sizeof(BodyState) * nb, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(acc, c->d_acc, sizeof(BodyAcc) * nb, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(kind, c->d_kind, sizeof(int) * nb, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c, c->d_par);
+    dfree(c, c->d_state[0]);
+    dfree(c, c->d_state[1]);
+    dfree(c, c->d_acc);
+    dfree(c, c->d_kind);
+    c->d_par = par;
+    c->d_state[0] = s0;
+    c->d_state[1] = s1;
+    c->d_acc = acc;
+    c->d_kind = kind;
+    c->cap = nc;
+    return LB_OK;
+}
+
+// After the body set changed: assign link segments, size the partial-sum
+// buffers and upload the body parameters.
+lb_status relayout(lb_ctx* c) {
+    const int nb = (int)c->par.size();
+    int64_t off = 0, max_cap = 0, max_box = 0;
+    for (auto& b : c->par) {
+        b.link_off = off;
+        off += b.link_cap;
+        max_cap = std::max(max_cap, b.link_cap);
+        max_box = std::max(max_box, (int64_t)b.box_w[0] * b.box_w[1] * b.box_w[2]);
+    }
+    if (off > c->links_total) {
+        dfree(c, c->d_links);
+        c->d_links = dalloc_t<uint32_t>(c, (size_t)off);
+        if (!c->d_links) return fail(c, LB_ERR_OOM, "link lists");
+        c->links_total = off;
+    }
+    c->G_links = (int)std::min<int64_t>(128, std::max<int64_t>(1, (max_cap + 2047) / 2048));
+    c->G_box = (int)std::min<int64_t>(256, std::max<int64_t>(1, (max_box + 2047) / 2048));
+    dfree(c, c->d_part_links);
+    dfree(c, c->d_part_conv);
+    dfree(c, c->d_part_count);
+    c->d_part_links = dalloc_t<double>(c, (size_t)nb * c->G_links * 12);
+    c->d_part_conv = dalloc_t<double>(c, (size_t)nb * c->G_box * 6);
+    c->d_part_count = dalloc_t<int>(c, (size_t)nb * c->G_box);
+    if (!c->d_part_links || !c->d_part_conv || !c->d_part_count) return fail(c, LB_ERR_OOM, "partials");
+    CK(cudaMemcpyAsync(c->d_par, c->par.data(), sizeof(BodyParams) * nb, cudaMemcpyHostToDevice, c->stream));
+    // both state buffers hold the current state
+    const int cur = (int)(c->step & 1);
+    CK(cudaMemcpyAsync(c->d_state[1 - cur], c->d_state[cur], sizeof(BodyState) * nb, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    drop_graph(c);
+    return LB_OK;
+}
+
+// Rebuild every link list (no conversion) and commit the owners.
+lb_status relink_all(lb_ctx* c) {
+    const int nb = (int)c->par.size();
+    const int cur = (int)(c->step & 1);
+    Bodies B = bodies_view(c);
+    launch_set_flags(c->d_acc, nb, -1, 0, 1, c->stream);
+    launch_relink(c->L, B, c->own, c->own_prev, 1 - cur, c->stream);
+    launch_set_flags(c->d_acc, nb, -1, 0, 0, c->stream);
+    c->launches += 4;
+    CK(cudaMemcpyAsync(c->own_prev, c->own, sizeof(int32_t) * c->L.N, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaGetLastError());
+    return sync_checked(c);
+}
+
+lb_status new_body(lb_ctx* c, const BodyParams& bp, const BodyState& st, int kind_code, int32_t* id_out) {
+    const int nb = (int)c->par.size();
+    lb_status s = ensure_body_capacity(c, nb + 1);
+    if (s != LB_OK) return s;
+    CK(cudaMemcpyAsync(c->d_par + nb, &bp, sizeof(BodyParams), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_state[0] + nb, &st, sizeof(BodyState), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_state[1] + nb, &st, sizeof(BodyState), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->d_acc + nb, 0, sizeof(BodyAcc), c->stream));
+    CK(cudaMemcpyAsync(c->d_kind + nb, &kind_code, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    c->par.push_back(bp);
+    c->kind.push_back(kind_code);
+    *id_out = nb + 1;
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lb_params_default(lb_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->nx = p->ny = p->nz = 32;
+    p->collision = LB_BGK;
+    p->lambda_e = 1.0;
+    p->magic = 3.0 / 16.0;
+    p->rho0 = 1.0;
+    p->storage = LB_F64;
+    p->dev_scale_log2 = -1;
+    p->device = 0;
+    p->stream = nullptr;
+    p->allocator = nullptr;
+}
+
+lb_status lb_create(const lb_params* p, lb_ctx** out) {
+    if (!p || !out) return LB_ERR_INVALID;
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || N >= (int64_t(1) << 27)) return LB_ERR_INVALID;
+    if (!(p->lambda_e > 0.0 && p->lambda_e < 2.0) || !(p->rho0 > 0.0)) return LB_ERR_INVALID;
+    if (p->collision != LB_BGK && p->collision != LB_TRT) return LB_ERR_INVALID;
+    if (p->storage < LB_F64 || p->storage > LB_BF16DEV) return LB_ERR_INVALID;
+    if (p->collision == LB_TRT && !(p->magic > 0.0)) return LB_ERR_INVALID;
+    if (p->dev_scale_log2 < -1 || p->dev_scale_log2 > 40) return LB_ERR_INVALID;
+    lb_ctx* c = new (std::nothrow) lb_ctx();
+    if (!c) return LB_ERR_OOM;
+    c->p = *p;
+    auto bail = [&](lb_status s) {
+        lb_destroy(c);
+        return s;
+    };
+    if (cudaSetDevice(p->device) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(LB_ERR_CUDA);
+    }
+    if (p->stream) {
+        c->stream = (cudaStream_t)p->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(LB_ERR_CUDA);
+        c->own_stream = true;
+    }
+    c->lambda_e = p->lambda_e;
+    // TRT odd rate from the magic parameter (1/le - 1/2)(1/lo - 1/2) = magic (Sec. III)
+    c->lambda_o = p->collision == LB_BGK ? p->lambda_e : 1.0 / (0.5 + p->magic / (1.0 / p->lambda_e - 0.5));
+    Lattice& L = c->L;
+    L.nx = p->nx;
+    L.ny = p->ny;
+    L.nz = p->nz;
+    L.N = N;
+    L.Np = (N + 63) / 64 * 64;
+    L.storage = p->storage;
+    L.rho0 = p->rho0;
+    const int k = p->dev_scale_log2 < 0 ? 20 : p->dev_scale_log2;
+    L.scale = p->storage == LB_F16DEV ? std::ldexp(1.0f, k) : 1.0f;
+    L.inv_scale = 1.0f / L.scale;
+    L.F = dalloc(c, (size_t)Q * L.Np * storage_bytes(p->storage));
+    c->own = dalloc_t<int32_t>(c, (size_t)N);
+    c->own_prev = dalloc_t<int32_t>(c, (size_t)N);
+    c->d_mass_part = dalloc_t<double>(c, (size_t)mass_partial_blocks(L) * 4);
+    c->d_small = dalloc_t<double>(c, 8);
+    c->d_err = dalloc_t<int>(c, 2);
+    c->d_count = dalloc_t<int>(c, 2);
+    if (!L.F || !c->own || !c->own_prev || !c->d_mass_part || !c->d_small || !c->d_err || !c->d_count)
+        return bail(LB_ERR_OOM);
+    if (cudaMemsetAsync(c->own, 0, sizeof(int32_t) * N, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->own_prev, 0, sizeof(int32_t) * N, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_err, 0, sizeof(int) * 2, c->stream) != cudaSuccess)
+        return bail(LB_ERR_CUDA);
+    launch_fill_rest(L, c->stream);
+    c->launches += 1;
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(LB_ERR_CUDA);
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_ctx* c) {
+    if (!c) return LB_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    while (!c->allocs.empty()) dfree(c, c->allocs.back().first);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return LB_OK;
+}
+
+const char* lb_last_error(const lb_ctx* c) { return c ? c->msg.c_str() : "null context"; }
+int64_t lb_step_count(const lb_ctx* c) { return c ? c->step : -1; }
+int64_t lb_kernel_launches(const lb_ctx* c) { return c ? c->launches : -1; }
+
+lb_status lb_add_squirmer(lb_ctx* c, const double pos[3], const double e[3], double R, double B1, double beta,
+                          int32_t mobile, double density, int32_t* id) {
+    if (!c || !pos || !e || !id) return LB_ERR_INVALID;
+    if (c->sticky) return fail(c, LB_ERR_STATE, "context holds a device error");
+    const int nmin = std::min(c->L.nx, std::min(c->L.ny, c->L.nz));
+    const double ne = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    if (!(R > 0.0) || !(2.0 * R + 6.0 < (double)nmin)) return fail(c, LB_ERR_INVALID, "radius vs box");
+    if (!(ne > 0.0) || !std::isfinite(ne)) return fail(c, LB_ERR_INVALID, "orientation");
+    if (!(density > 0.0) || !std::isfinite(B1) || !std::isfinite(beta)) return fail(c, LB_ERR_INVALID, "parameters");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(pos[a])) return fail(c, LB_ERR_INVALID, "position");
+    CK(cudaSetDevice(c->p.device));
+    const int n3[3] = {c->L.nx, c->L.ny, c->L.nz};
+    BodyState st{};
+    for (int a = 0; a < 3; ++a) {
+        st.pos[a] = pos[a] - std::floor(pos[a] / n3[a]) * n3[a];
+        st.e[a] = e[a] / ne;
+    }
+    const int W = (int)std::ceil(2.0 * R) + 6;
+    // overlap check before anything changes
+    CK(cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream));
+    CK(cudaMemcpyAsync(c->d_small, st.pos, 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    launch_sphere_overlap(c->L, c->own, st.pos, R, W, c->d_count, c->stream);
+    c->launches += 1;
+    int hcount = 0;
+    CK(cudaMemcpyAsync(&hcount, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hcount != 0) return fail(c, LB_ERR_OVERLAP, "the sphere overlaps a solid cell");
+    BodyParams bp{};
+    bp.kind = BODY_SPHERE;
+    bp.mobile = mobile ? 1 : 0;
+    bp.R = R;
+    bp.B1 = B1;
+    bp.B2 = beta * B1;
+    bp.mass = density * (4.0 / 3.0) * M_PI * R * R * R;
+    bp.inertia = 0.4 * bp.mass * R * R;
+    bp.link_cap = sphere_link_cap(R);
+    bp.box_w[0] = bp.box_w[1] = bp.box_w[2] = W;
+    int32_t nid = 0;
+    lb_status s = new_body(c, bp, st, BODY_SPHERE, &nid);
+    if (s != LB_OK) return s;
+    s = relayout(c);
+    if (s != LB_OK) return s;
+    // claim the covered cells and record the node margin with a classify pass
+    // "after a step of parity 1 - cur" (it reads state[cur])
+    const int nb = (int)c->par.size();
+    const int cur = (int)(c->step & 1);
+    launch_set_flags(c->d_acc, nb, -1, 0, 0, c->stream);
+    launch_set_flags(c->d_acc, nb, nid - 1, 1, 0, c->stream);
+    launch_classify_only(c->L, bodies_view(c), c->own, c->own_prev, 1 - cur, c->stream);
+    c->launches += 3;
+    CK(cudaGetLastError());
+    s = relink_all(c);
+    if (s != LB_OK) return s;
+    *id = nid;
+    return LB_OK;
+}
+
+lb_status lb_add_wall(lb_ctx* c, int32_t kind, const double* params, int32_t nparams, int32_t* id) {
+    if (!c || !id) return LB_ERR_INVALID;
+    if (c->sticky) return fail(c, LB_ERR_STATE, "context holds a device error");
+    CK(cudaSetDevice(c->p.device));
+    const int n3[3] = {c->L.nx, c->L.ny, c->L.nz};
+    if (kind == 2) {
+        if (!params || nparams < 4) return fail(c, LB_ERR_INVALID, "obstacle needs x, y, z, radius");
+        const double e[3] = {0.0, 0.0, 1.0};
+        return lb_add_squirmer(c, params, e, params[3], 0.0, 0.0, 0, 1.0, id);
+    }
+    if (kind == 1) {
+        // square tube along z: plane walls x = 0, x = nx-1, y = 0, y = ny-1
+        const double walls[4][2] = {{0, 0}, {0, (double)(n3[0] - 1)}, {1, 0}, {1, (double)(n3[1] - 1)}};
+        int32_t first = 0;
+        for (int w = 0; w < 4; ++w) {
+            int32_t wid = 0;
+            lb_status s = lb_add_wall(c, 0, walls[w], 2, &wid);
+            if (s != LB_OK) return s;
+            if (w == 0) first = wid;
+        }
+        *id = first;
+        return LB_OK;
+    }
+    if (kind != 0 || !params || (nparams != 2 && nparams != 5)) return fail(c, LB_ERR_INVALID, "wall kind/params");
+    const int axis = (int)params[0], index = (int)params[1];
+    if (params[0] != axis || params[1] != index || axis < 0 || axis > 2 || index < 0 || index >= n3[axis])
+        return fail(c, LB_ERR_INVALID, "plane wall axis/index");
+    CK(cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream));
+    if (!c->par.empty()) {
+        launch_plane_overlap(c->L, c->own, c->d_kind, axis, index, c->d_count, c->stream);
+        c->launches += 1;
+    }
+    int hcount = 0;
+    CK(cudaMemcpyAsync(&hcount, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hcount != 0) return fail(c, LB_ERR_OVERLAP, "the wall overlaps a sphere");
+    BodyParams bp{};
+    bp.kind = BODY_WALL;
+    bp.mobile = 0;
+    bp.wall_axis = axis;
+    bp.wall_index = index;
+    if (nparams == 5)
+        for (int a = 0; a < 3; ++a) bp.wall_vel[a] = params[2 + a];
+    const int64_t area = c->L.N / n3[axis];
+    bp.link_cap = 10 * area + 64;
+    for (int a = 0; a < 3; ++a) bp.box_w[a] = n3[a];
+    bp.box_w[axis] = std::min(3, n3[axis]);
+    BodyState st{};
+    st.e[2] = 1.0;
+    int32_t nid = 0;
+    lb_status s = new_body(c, bp, st, BODY_WALL, &nid);
+    if (s != LB_OK) return s;
+    launch_plane_claim(c->L, c->own, axis, index, nid, c->stream);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    s = relayout(c);
+    if (s == LB_OK) s = relink_all(c);
+    if (s != LB_OK) return s;
+    *id = nid;
+    return LB_OK;
+}
+
+lb_status lb_set_contact(lb_ctx* c, double sigma, double eps) {
+    if (!c || !(sigma > 0.0) || !(eps >= 0.0)) return LB_ERR_INVALID;
+    c->wca_sigma = sigma;
+    c->wca_eps = eps;
+    drop_graph(c);
+    return LB_OK;
+}
+
+static lb_status ensure_scratch(lb_ctx* c, double** buf, size_t n) {
+    if (*buf) return LB_OK;
+    *buf = dalloc_t<double>(c, n);
+    return *buf ? LB_OK : fail(c, LB_ERR_OOM, "export buffer");
+}
+
+lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u) {
+    if (!c || !rho || !u) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    const size_t N = (size_t)c->L.N;
+    lb_status s = ensure_scratch(c, &c->d_fields, 4 * N);
+    if (s != LB_OK) return s;
+    CK(cudaMemcpyAsync(c->d_fields, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_fields + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    launch_set_eq(c->L, c->d_fields, c->d_fields + N, (int)(c->step & 1), c->stream);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_set_populations(lb_ctx* c, const double* f) {
+    if (!c || !f) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    const size_t N = (size_t)c->L.N;
+    lb_status s = ensure_scratch(c, &c->d_pop, Q * N);
+    if (s != LB_OK) return s;
+    CK(cudaMemcpyAsync(c->d_pop, f, Q * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    launch_set_pop(c->L, c->d_pop, (int)(c->step & 1), c->stream);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_get_populations(lb_ctx* c, double* f) {
+    if (!c || !f) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    const size_t N = (size_t)c->L.N;
+    lb_status s = ensure_scratch(c, &c->d_pop, Q * N);
+    if (s != LB_OK) return s;
+    launch_get_pop(c->L, c->d_pop, (int)(c->step & 1), c->stream);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(f, c->d_pop, Q * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return sync_checked(c);
+}
+
+static cudaEvent_t pool_event(lb_ctx* c, size_t k) {
+    while (c->ev_pool.size() <= k) {
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[k];
+}
+
+static void enqueue_step(lb_ctx* c, int parity) {
+    if (c->profiling) {
+        // each kernel between its own pair of events
+        const int nk = c->par.empty() ? 1 : 5;
+        for (int k = 0; k < nk; ++k) {
+            const size_t e0 = 2 * c->ev_used.size();
+            cudaEventRecord(pool_event(c, e0), c->stream);
+            if (k == 0) launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->stream);
+            else launch_body_kernel(k, c->L, bodies_view(c), c->own, c->own_prev, parity, c->stream);
+            cudaEventRecord(pool_event(c, e0 + 1), c->stream);
+            c->ev_used.emplace_back(k, (int)e0);
+        }
+        c->launches += nk;
+        return;
+    }
+    launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->stream);
+    c->launches += 1;
+    if (!c->par.empty()) {
+        launch_body_step(c->L, bodies_view(c), c->own, c->own_prev, parity, c->stream);
+        c->launches += 4;
+    }
+}
+
+static lb_status build_graph(lb_ctx* c) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t saved = c->launches;
+    enqueue_step(c, 0);
+    enqueue_step(c, 1);
+    c->launches = saved;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "capture");
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return cuda_fail(c, e, "instantiate");
+    }
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx* c, int64_t nsteps) {
+    if (!c || nsteps < 0) return LB_ERR_INVALID;
+    if (c->sticky) return fail(c, LB_ERR_STATE, "context holds a device error");
+    CK(cudaSetDevice(c->p.device));
+    const int per_step = 1 + (c->par.empty() ? 0 : 4);
+    int64_t left = nsteps;
+    if (left > 0 && (c->step & 1)) {
+        enqueue_step(c, 1);
+        c->step++;
+        left--;
+    }
+    if (c->profiling) {
+        for (; left > 0; --left) {
+            enqueue_step(c, (int)(c->step & 1));
+            c->step++;
+        }
+    }
+    if (left >= 2) {
+        if (!c->graph) {
+            lb_status s = build_graph(c);
+            if (s != LB_OK) return s;
+        }
+        while (left >= 2) {
+            CK(cudaGraphLaunch(c->graph, c->stream));
+            c->launches += 2 * per_step;
+            c->step += 2;
+            left -= 2;
+        }
+    }
+    if (left == 1) {
+        enqueue_step(c, 0);
+        c->step++;
+    }
+    CK(cudaGetLastError());
+    return LB_OK;
+}
+
+lb_status lb_profile_begin(lb_ctx* c) {
+    if (!c) return LB_ERR_INVALID;
+    c->profiling = true;
+    c->ev_used.clear();
+    return LB_OK;
+}
+
+lb_status lb_profile_end(lb_ctx* c, double total_ms[5], int64_t launches[5]) {
+    if (!c) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    c->profiling = false;
+    lb_status s = sync_checked(c);
+    double t[5] = {0, 0, 0, 0, 0};
+    int64_t n[5] = {0, 0, 0, 0, 0};
+    for (auto& u : c->ev_used) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c->ev_pool[u.second], c->ev_pool[u.second + 1]) == cudaSuccess) {
+            t[u.first] += ms;
+            n[u.first] += 1;
+        }
+    }
+    c->ev_used.clear();
+    if (s != LB_OK) return s;
+    for (int k = 0; k < 5; ++k) {
+        if (total_ms) total_ms[k] = t[k];
+        if (launches) launches[k] = n[k];
+    }
+    return LB_OK;
+}
+
+lb_status lb_sync(lb_ctx* c) {
+    if (!c) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    return sync_checked(c);
+}
+
+lb_status lb_get_fields_device(lb_ctx* c, double* rho_dev, double* u_dev) {
+    if (!c) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    launch_fields(c->L, c->own, rho_dev, u_dev, (int)(c->step & 1), c->stream);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    return LB_OK;
+}
+
+lb_status lb_get_fields(lb_ctx* c, double* rho, double* u) {
+    if (!c) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    const size_t N = (size_t)c->L.N;
+    lb_status s = ensure_scratch(c, &c->d_fields, 4 * N);
+    if (s != LB_OK) return s;
+    launch_fields(c->L, c->own, c->d_fields, c->d_fields + N, (int)(c->step & 1), c->stream);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    s = sync_checked(c);
+    if (s != LB_OK) return s;
+    if (rho) CK(cudaMemcpyAsync(rho, c->d_fields, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (u) CK(cudaMemcpyAsync(u, c->d_fields + N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_get_owner(lb_ctx* c, int32_t* owner) {
+    if (!c || !owner) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    lb_status s = sync_checked(c);
+    if (s != LB_OK) return s;
+    CK(cudaMemcpyAsync(owner, c->own, sizeof(int32_t) * c->L.N, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+static lb_status read_acc(lb_ctx* c, int32_t id, BodyAcc* a) {
+    if (id < 1 || id > (int32_t)c->par.size()) return fail(c, LB_ERR_INVALID, "bad body id");
+    CK(cudaSetDevice(c->p.device));
+    lb_status s = sync_checked(c);
+    if (s != LB_OK) return s;
+    CK(cudaMemcpyAsync(a, c->d_acc + (id - 1), sizeof(BodyAcc), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_get_force_torque(lb_ctx* c, int32_t id, double F[3], double T[3]) {
+    if (!c || !F || !T) return LB_ERR_INVALID;
+    BodyAcc a;
+    lb_status s = read_acc(c, id, &a);
+    if (s != LB_OK) return s;
+    for (int k = 0; k < 3; ++k) {
+        F[k] = a.Fapp[k];
+        T[k] = a.Tapp[k];
+    }
+    return LB_OK;
+}
+
+lb_status lb_get_stresslet(lb_ctx* c, int32_t id, double S[6]) {
+    if (!c || !S) return LB_ERR_INVALID;
+    BodyAcc a;
+    lb_status s = read_acc(c, id, &a);
+    if (s != LB_OK) return s;
+    for (int k = 0; k < 6; ++k) S[k] = a.Sbb[k];
+    return LB_OK;
+}
+
+lb_status lb_get_object_state(lb_ctx* c, int32_t id, double pos[3], double vel[3], double e[3], double omega[3]) {
+    if (!c) return LB_ERR_INVALID;
+    if (id < 1 || id > (int32_t)c->par.size()) return fail(c, LB_ERR_INVALID, "bad body id");
+    CK(cudaSetDevice(c->p.device));
+    lb_status s = sync_checked(c);
+    if (s != LB_OK) return s;
+    BodyState st;
+    CK(cudaMemcpyAsync(&st, c->d_state[c->step & 1] + (id - 1), sizeof(BodyState), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 3; ++k) {
+        if (pos) pos[k] = st.pos[k];
+        if (vel) vel[k] = st.vel[k];
+        if (e) e[k] = st.e[k];
+        if (omega) omega[k] = st.omega[k];
+    }
+    return LB_OK;
+}
+
+lb_status lb_get_mass(lb_ctx* c, double* mass, double mom[3]) {
+    if (!c) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    launch_mass(c->L, c->own, c->d_mass_part, c->d_small, (int)(c->step & 1), c->stream);
+    c->launches += 2;
+    CK(cudaGetLastError());
+    lb_status s = sync_checked(c);
+    if (s != LB_OK) return s;
+    double h[4];
+    CK(cudaMemcpyAsync(h, c->d_small, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (mass) *mass = h[0];
+    if (mom)
+        for (int k = 0; k < 3; ++k) mom[k] = h[1 + k];
+    return LB_OK;
+}
+
+lb_status lb_get_links(lb_ctx* c, int32_t id, int64_t* out, int64_t cap, int64_t* count) {
+    if (!c || !count || cap < 0 || (cap > 0 && !out)) return LB_ERR_INVALID;
+    if (id < 0 || id > (int32_t)c->par.size()) return fail(c, LB_ERR_INVALID, "bad body id");
+    CK(cudaSetDevice(c->p.device));
+    lb_status s = sync_checked(c);
+    if (s != LB_OK) return s;
+    const int nb = (int)c->par.size();
+    std::vector<BodyAcc> acc(nb);
+    if (nb) CK(cudaMemcpyAsync(acc.data(), c->d_acc, sizeof(BodyAcc) * nb, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int64_t n = 0;
+    std::vector<uint32_t> buf;
+    for (int k = 0; k < nb; ++k) {
+        if (id != 0 && k != id - 1) continue;
+        const int64_t m = acc[k].link_count;
+        buf.resize((size_t)m);
+        if (m) {
+            CK(cudaMemcpyAsync(buf.data(), c->d_links + c->par[k].link_off, m * sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        for (int64_t l = 0; l < m; ++l, ++n)
+            if (n < cap) out[n] = (int64_t)buf[(size_t)l];
+    }
+    *count = n;
+    return LB_OK;
+}
+
+}  // extern "C"

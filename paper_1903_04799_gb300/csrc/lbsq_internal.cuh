@@ -1,0 +1,214 @@
+// lbsq_internal.cuh -- device-side building blocks shared by the CUDA
+// translation units of the library (never by the CPU oracle).
+//
+// Population layout: one array F of 19 planes, plane i holding population i
+// of every cell, x-fastest (F[i * Np + n], n = x + nx*(y + ny*z), Np = the
+// cell count padded to 64).  Streaming is the in-place AA pattern:
+//   even step: cell n reads F[i][n] and writes its post-collision f_i to F[ib][n];
+//   odd step:  cell n reads f_i from F[ib][n - c_i] and writes f_i to F[i][n + c_i];
+// (ib = opposite of i).  Both touch the same 19 slots of a cell, so the update
+// is race-free in place.  Before a step of parity Q, population i of cell n
+// sits in its "read slot": Q = 0: F[i][n]; Q = 1: F[ib][n - c_i].
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace lbsq {
+
+constexpr int Q = 19;
+
+// D3Q19 velocities (Sec. III): rest, 6 faces, 12 edges; opposite pairs adjacent.
+// Component c+1 of velocity i is packed in bits 2i..2i+1 of a 64-bit constant,
+// so cx(i) folds to a literal for a compile-time i and costs a shift for a
+// run-time one.  Velocities, in order:
+//   (0,0,0) (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1)
+//   (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
+//   (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+constexpr unsigned long long kCX = 0x1548889549ull;
+constexpr unsigned long long kCY = 0x895609495ull;
+constexpr unsigned long long kCZ = 0x20a0954955ull;
+__host__ __device__ constexpr int cx(int i) { return (int)((kCX >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ constexpr int cy(int i) { return (int)((kCY >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ constexpr int cz(int i) { return (int)((kCZ >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+static_assert(cx(1) == 1 && cx(2) == -1 && cy(9) == -1 && cz(13) == -1 && cz(18) == 1 && cy(17) == 1,
+              "packed D3Q19 table");
+// weights 1/3 (rest), 1/18 (faces), 1/36 (edges)
+__host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+enum Storage : int { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+
+// Storage traits: the stored type, the arithmetic type of the collision, and
+// whether the store holds a deviation from w_i rho0.
+template <int S> struct StoreT;
+template <> struct StoreT<ST_F64> {
+    using T = double;
+    using R = double;
+    static constexpr bool dev = false;
+    __device__ static R load(const T* p, R) { return *p; }
+    __device__ static void store(T* p, R v, R) { *p = v; }
+};
+template <> struct StoreT<ST_F32> {
+    using T = float;
+    using R = float;
+    static constexpr bool dev = true;
+    __device__ static R load(const T* p, R) { return *p; }
+    __device__ static void store(T* p, R v, R) { *p = v; }
+};
+template <> struct StoreT<ST_F16> {
+    using T = __half;
+    using R = float;
+    static constexpr bool dev = true;
+    __device__ static R load(const T* p, R inv_scale) { return __half2float(*p) * inv_scale; }
+    __device__ static void store(T* p, R v, R scale) { *p = __float2half_rn(v * scale); }
+};
+template <> struct StoreT<ST_BF16> {
+    using T = __nv_bfloat16;
+    using R = float;
+    static constexpr bool dev = true;
+    __device__ static R load(const T* p, R inv_scale) { return __bfloat162float(*p) * inv_scale; }
+    __device__ static void store(T* p, R v, R scale) { *p = __float2bfloat16_rn(v * scale); }
+};
+
+inline int storage_bytes(int s) { return s == ST_F64 ? 8 : (s == ST_F32 ? 4 : 2); }
+
+// Lattice geometry and population array, as seen by kernels.
+struct Lattice {
+    void* F;          // populations, storage-typed
+    int nx, ny, nz;
+    int64_t N, Np;    // cells, padded plane stride
+    int storage;
+    double rho0;
+    float scale, inv_scale;  // FP16 deviation scale (1 for other storages)
+};
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ int64_t cell_index(const Lattice& L, int x, int y, int z) {
+    return (int64_t)x + (int64_t)L.nx * ((int64_t)y + (int64_t)L.ny * (int64_t)z);
+}
+
+__device__ __forceinline__ void cell_coords(const Lattice& L, int64_t n, int& x, int& y, int& z) {
+    x = (int)(n % L.nx);
+    int64_t r = n / L.nx;
+    y = (int)(r % L.ny);
+    z = (int)(r / L.ny);
+}
+
+// Flat index (plane * Np + cell) of the read slot of population i of cell
+// (x,y,z) before a step of parity q.
+__device__ __forceinline__ int64_t read_slot(const Lattice& L, int i, int x, int y, int z, int q) {
+    if (q == 0) return (int64_t)i * L.Np + cell_index(L, x, y, z);
+    int xs = wrapi(x - cx(i), L.nx), ys = wrapi(y - cy(i), L.ny), zs = wrapi(z - cz(i), L.nz);
+    return (int64_t)opp(i) * L.Np + cell_index(L, xs, ys, zs);
+}
+
+// Absolute value f_i from a stored slot, in FP64.
+__device__ __forceinline__ double load_abs(const Lattice& L, int64_t slot, int i) {
+    switch (L.storage) {
+        case ST_F64: return ((const double*)L.F)[slot];
+        case ST_F32: return wgt(i) * L.rho0 + (double)((const float*)L.F)[slot];
+        case ST_F16: return wgt(i) * L.rho0 + (double)(__half2float(((const __half*)L.F)[slot]) * L.inv_scale);
+        default: return wgt(i) * L.rho0 + (double)(__bfloat162float(((const __nv_bfloat16*)L.F)[slot]) * L.inv_scale);
+    }
+}
+
+// Store an absolute value f_i into a slot (reduced storages keep f_i - w_i rho0).
+__device__ __forceinline__ void store_abs(const Lattice& L, int64_t slot, int i, double f) {
+    switch (L.storage) {
+        case ST_F64: ((double*)L.F)[slot] = f; break;
+        case ST_F32: ((float*)L.F)[slot] = (float)(f - wgt(i) * L.rho0); break;
+        case ST_F16: ((__half*)L.F)[slot] = __float2half_rn((float)(f - wgt(i) * L.rho0) * L.scale); break;
+        default: ((__nv_bfloat16*)L.F)[slot] = __float2bfloat16_rn((float)(f - wgt(i) * L.rho0) * L.scale); break;
+    }
+}
+
+// Minimum image of a coordinate difference into (-n/2, n/2].
+__device__ __forceinline__ double min_image(double d, int n) {
+    double h = 0.5 * (double)n;
+    if (d > h) d = __dadd_rn(d, -(double)n);
+    else if (d <= -h) d = __dadd_rn(d, (double)n);
+    return d;
+}
+
+// Inside test (dx*dx + dy*dy) + dz*dz < R*R, rounded step by step (no FMA).
+__device__ __forceinline__ bool inside_sphere(double dx, double dy, double dz, double R) {
+    double s = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    s = __dadd_rn(s, __dmul_rn(dz, dz));
+    return s < __dmul_rn(R, R);
+}
+
+// ------------------------------------------------------------------ bodies
+
+enum BodyKind : int { BODY_WALL = 0, BODY_SPHERE = 1 };
+
+struct BodyParams {
+    int kind, mobile;
+    double R, B1, B2, mass, inertia;
+    double wall_vel[3];
+    int wall_axis, wall_index;
+    int64_t link_off;  // first slot of this body's link segment
+    int64_t link_cap;  // capacity of the segment
+    int box_w[3];      // scan box extent (spheres: W = ceil(2R)+6 per axis)
+    int pad;
+};
+
+struct BodyState {  // ping-pong by step parity
+    double pos[3], vel[3], omega[3], e[3];
+};
+
+struct BodyAcc {
+    double Fbb[3], Tbb[3], Sbb[6];
+    double Fc[3], Tc[3];              // conversion force booked for the next update
+    double Fapp[3], Tapp[3];          // force/torque that entered the last update
+    double r_class[3];                // centre at the last classification
+    unsigned long long margin_bits;   // min | |x - r| - R | over the box at that time
+    int box_lo[3];                    // scan box origin of the current classification
+    int reclass, relink;              // work flags of the current step
+    long long link_count;
+    int counter_links, counter_conv;  // last-block counters (self-resetting)
+};
+
+struct Bodies {
+    int n;
+    const BodyParams* par;
+    BodyState* state[2];
+    BodyAcc* acc;
+    uint32_t* links;       // code = cell * 32 + i
+    double* part_links;    // [n][G_links][12]
+    double* part_conv;     // [n][G_box][6]
+    int* part_count;       // [n][G_box]
+    int G_links, G_box;
+    double wca_sigma, wca_eps;
+    int* err;
+};
+
+// Scan box of a body: origin and extent.
+__device__ __forceinline__ void body_box(const Lattice& L, const BodyParams& p, const BodyState& s, int lo[3],
+                                         int w[3]) {
+    if (p.kind == BODY_SPHERE) {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = (int)floor(s.pos[a] - p.R) - 2;
+            w[a] = p.box_w[a];
+        }
+    } else {
+        int n[3] = {L.nx, L.ny, L.nz};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = 0;
+            w[a] = n[a];
+        }
+        // a plane wall's links come from the two layers next to it
+        lo[p.wall_axis] = p.wall_index - 1;
+        w[p.wall_axis] = n[p.wall_axis] < 3 ? n[p.wall_axis] : 3;
+    }
+}
+
+__device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+}  // namespace lbsq

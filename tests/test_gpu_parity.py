@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, on the
+same seeded inputs, element by element.
+
+Tolerances:
+  * FP64 storage: 1e-12 relative (max |gpu - oracle| / max |oracle| per field),
+    the FP64 target; the two sides differ only in rounding order.
+  * cell classification and boundary-link sets: bit-exact.
+  * reduced storages: derived from the rounding of one stored value per
+    population per step (FP32 2^-24, FP16 2^-11, BF16 2^-8 of the deviation
+    f - w rho0) accumulated over the run; stated per test.
+"""
+import numpy as np
+import pytest
+
+from paper_1903_04799_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle.oracle import OracleSim  # noqa: E402
+from paper_1903_04799_gb300 import Lattice  # noqa: E402
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+
+
+def make_pair(shape, collision="bgk", lambda_e=1.0, storage="f64"):
+    g = Lattice(shape, collision=collision, lambda_e=lambda_e, storage=storage)
+    o = OracleSim(*shape, lambda_e=lambda_e, collision=collision)
+    return g, o
+
+
+# ------------------------------------------------------------------ bulk fluid
+
+@pytest.mark.parametrize("collision,lambda_e", [("bgk", 1.0), ("trt", 1.0), ("trt", 1.7), ("bgk", 0.6)])
+@pytest.mark.parametrize("steps", [1, 2, 37])
+def test_bulk_f64_parity(collision, lambda_e, steps):
+    """Periodic box, smooth random fields, ragged sizes (not multiples of 32):
+    FP64 populations within 1e-12 after even and odd step counts."""
+    shape = (45, 19, 23)
+    g, o = make_pair(shape, collision, lambda_e)
+    rho, u = W.smooth_fields(shape, seed=7, drho=0.02, umax=0.05)
+    g.set_fields(rho, u)
+    o.set_equilibrium(rho, u)
+    g.step(steps)
+    o.step(steps)
+    fg, fo = g.populations(), o.populations()
+    assert rel(fg - o.lambda_e * 0, fo) < 1e-12
+    # deviations from rest: tighter view of the same comparison
+    assert np.abs(fg - fo).max() < 1e-14
+
+
+def test_bulk_random_populations_f64():
+    """Far-from-equilibrium random populations (every relaxation mode excited)."""
+    shape = (33, 17, 9)
+    g, o = make_pair(shape, "trt", 1.3)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    f = W.random_populations(int(np.prod(shape)), seed=3, base=w, spread=0.2)
+    g.set_populations(f)
+    o.set_populations(f)
+    g.step(11)
+    o.step(11)
+    assert np.abs(g.populations() - o.populations()).max() < 1e-14
+
+
+def test_degenerate_lattices():
+    """Lattices of one cell along an axis (self-periodic) and tiny boxes."""
+    for shape in [(1, 16, 1), (7, 1, 5), (1, 1, 1), (2, 3, 64)]:
+        g, o = make_pair(shape, "trt", 1.1)
+        rho, u = W.smooth_fields(shape, seed=11)
+        g.set_fields(rho, u)
+        o.set_equilibrium(rho, u)
+        g.step(5)
+        o.step(5)
+        assert np.abs(g.populations() - o.populations()).max() < 1e-14, shape
+
+
+def test_mass_momentum_conserved_f64():
+    shape = (40, 30, 20)
+    g = Lattice(shape, collision="trt", storage="f64")
+    rho, u = W.smooth_fields(shape, seed=5)
+    g.set_fields(rho, u)
+    m0, j0 = g.mass()
+    g.step(200)
+    m1, j1 = g.mass()
+    assert abs(m1 - m0) < 1e-11 * m0
+    assert np.abs(j1 - j0).max() < 1e-11
+
+
+# ------------------------------------------------------------------ classification
+
+@pytest.mark.parametrize("pos,R", [((16.0, 16.0, 16.0), 4.0), ((0.0, 31.0, 0.5), 5.0),
+                                   ((3.7, 12.2, 29.9), 6.3), ((15.5, 15.5, 15.5), 3.5)])
+def test_classification_bit_exact(pos, R):
+    shape = (32, 32, 32)
+    g, o = make_pair(shape)
+    gi = g.add_squirmer(pos, (0, 0, 1), R, 0.0, 0.0, mobile=False)
+    oi = o.add_sphere(pos, (0, 0, 1), R, mobile=False)
+    assert gi == oi
+    assert (g.owner() == o.owner()).all()
+    assert np.array_equal(np.sort(g.links()), np.sort(o.links()))
+
+
+def test_overlap_rejected():
+    from paper_1903_04799_gb300.lbsq import LBError, LB_ERR_OVERLAP
+    g = Lattice((32, 32, 32))
+    g.add_squirmer((10, 10, 10), (0, 0, 1), 4.0, 0.0, 0.0, mobile=False)
+    before = g.owner()
+    with pytest.raises(LBError) as ei:
+        g.add_squirmer((16, 10, 10), (0, 0, 1), 4.0, 0.0, 0.0, mobile=False)
+    assert ei.value.status == LB_ERR_OVERLAP
+    assert (g.owner() == before).all()
+
+
+# ------------------------------------------------------------------ bodies
+
+W_I = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+C_NORM = np.array([0.0] + [1.0] * 6 + [np.sqrt(2.0)] * 12)
+
+
+def gross_flux(o, oid, rho0=1.0):
+    """Sum over the body's links of the magnitude of the exchanged momentum at
+    rest, 2 w_i rho0 |c_i|: the scale of the terms whose sum is the force.
+    The force is 10^2-10^4 times smaller than this sum of terms, so its FP64
+    rounding error (either side's) is relative to this scale, not to |F|."""
+    d = o.links(oid) % 32
+    return float((2 * W_I[d] * rho0 * C_NORM[d]).sum())
+
+
+def _compare_bodies(g, o, gids, oids, tol=1e-12, R=None):
+    """FP64 parity: fields and body state within `tol` relative; per-body sums
+    (F, T, S) within `tol` relative to the gross flux of their terms."""
+    rg, ug = g.fields()
+    ro, uo = o.fields()
+    assert (g.owner() == o.owner()).all(), "classification differs"
+    assert rel(ug, uo) < tol
+    assert rel(rg - 1.0 * (ro != 0), ro - 1.0 * (ro != 0)) < tol
+    for gi, oi in zip(gids, oids):
+        assert np.array_equal(np.sort(g.links(gi)), np.sort(o.links(oi)))
+        flux = gross_flux(o, oi)
+        Fg, Tg = g.force_torque(gi)
+        Fo, To = o.force_torque(oi)
+        lever = float(R) if R else 8.0  # |d| of the link midpoints, about R
+        assert np.abs(Fg - Fo).max() < tol * max(flux, np.abs(Fo).max()), (Fg, Fo)
+        assert np.abs(Tg - To).max() < tol * lever * max(flux, np.abs(Fo).max()), (Tg, To)
+        Sg, So = g.stresslet(gi), o.stresslet(oi)
+        assert np.abs(Sg - So).max() < tol * lever * max(flux, np.abs(Fo).max()), (Sg, So)
+        sg, so = g.state(gi), o.state(oi)
+        for a, b in zip(sg, so):
+            assert np.abs(a - b).max() < 1e-12
+
+
+def test_c1_fixed_squirmer_f64():
+    """The 32^3 fixed-squirmer configuration, 500 BGK steps: u field, force,
+    torque within 1e-12 of the oracle."""
+    wl = W.c1_fixed_squirmer()
+    g, o = make_pair(wl.shape, wl.collision, wl.lambda_e)
+    b = wl.bodies[0]
+    gi = g.add_squirmer(b.pos, b.e, b.R, b.B1, b.beta, mobile=b.mobile)
+    oi = o.add_sphere(b.pos, b.e, b.R, b.B1, b.beta, mobile=b.mobile)
+    g.step(wl.steps)
+    o.step(wl.steps)
+    _compare_bodies(g, o, [gi], [oi])
+
+
+@pytest.mark.parametrize("beta", [0.0, -5.0, 5.0])
+def test_free_swimmer_f64(beta):
+    """A free squirmer crossing cells (conversion, refill, relinking, Newton-Euler)."""
+    shape = (28, 26, 30)
+    g, o = make_pair(shape, "trt", 1.0)
+    args = ((13.3, 12.7, 14.1), (0.3, -0.4, 1.0), 4.5, 0.03, beta)
+    gi = g.add_squirmer(*args, mobile=True)
+    oi = o.add_sphere(*args, mobile=True)
+    changed = 0
+    prev = o.owner()
+    for _ in range(6):
+        g.step(50)
+        o.step(50)
+        own = o.owner()
+        changed += int((own != prev).sum())
+        prev = own
+        _compare_bodies(g, o, [gi], [oi])
+    assert changed > 0
+
+
+def test_walls_couette_and_tube():
+    """A moving plane wall (Couette) and a square tube with a fixed obstacle."""
+    shape = (6, 14, 5)
+    g, o = make_pair(shape, "bgk", 0.9)
+    g.add_plane_wall(1, 0)
+    gw = g.add_plane_wall(1, 13, vel=(1e-3, 0, 2e-4))
+    o.add_plane_wall(1, 0)
+    ow = o.add_plane_wall(1, 13, vel=(1e-3, 0, 2e-4))
+    g.step(301)
+    o.step(301)
+    _compare_bodies(g, o, [gw], [ow])
+
+    shape = (18, 18, 40)
+    g, o = make_pair(shape, "trt", 1.0)
+    g.add_tube()
+    for w in [(0, 0), (0, 17), (1, 0), (1, 17)]:
+        o.add_plane_wall(*w)
+    gs = g.add_squirmer((9.2, 8.9, 10.0), (0.1, 0.05, 1.0), 3.5, 0.02, 2.0, mobile=True)
+    os_ = o.add_sphere((9.2, 8.9, 10.0), (0.1, 0.05, 1.0), 3.5, 0.02, 2.0, mobile=True)
+    gob = g.add_obstacle((9.0, 9.0, 28.0), 3.0)
+    oob = o.add_sphere((9.0, 9.0, 28.0), (0, 0, 1), 3.0, 0.0, 0.0, mobile=False)
+    g.set_contact(1.0, 0.01)
+    o.set_contact(1.0, 0.01)
+    for _ in range(3):
+        g.step(60)
+        o.step(60)
+        _compare_bodies(g, o, [gs, gob], [os_, oob])
+
+
+def test_two_swimmers_f64():
+    shape = (40, 24, 24)
+    g, o = make_pair(shape, "trt", 1.0)
+    a = ((10.2, 12.1, 11.8), (1.0, 0.1, 0.0), 4.0, 0.03, -3.0)
+    b = ((29.7, 11.6, 12.3), (-1.0, 0.05, 0.1), 4.0, 0.03, 3.0)
+    gids = [g.add_squirmer(*a, mobile=True), g.add_squirmer(*b, mobile=True)]
+    oids = [o.add_sphere(*a, mobile=True), o.add_sphere(*b, mobile=True)]
+    for _ in range(4):
+        g.step(40)
+        o.step(40)
+        _compare_bodies(g, o, gids, oids)
+
+
+def test_determinism_bitwise():
+    """The same run twice gives the same bits (fixed-order reductions)."""
+    outs = []
+    for _ in range(2):
+        g = Lattice((28, 26, 30), collision="trt", storage="f64")
+        gi = g.add_squirmer((13.3, 12.7, 14.1), (0.3, -0.4, 1.0), 4.5, 0.03, -2.0, mobile=True)
+        g.step(150)
+        outs.append((g.populations(), g.force_torque(gi)[0], g.state(gi)[0]))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------ reduced storage
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16dev", 2e-2), ("bf16dev", 2e-1)])
+def test_reduced_storage_free_swimmer(storage, tol):
+    """Reduced storages against the FP64 oracle: u field and body velocity after
+    200 steps.  Tolerances: relative to max|u|, from the storage rounding of
+    the deviations (FP32 2^-24, FP16 2^-11, BF16 2^-8) accumulated over the run."""
+    shape = (28, 26, 30)
+    g = Lattice(shape, collision="trt", storage=storage)
+    o = OracleSim(*shape, lambda_e=1.0, collision="trt")
+    args = ((13.3, 12.7, 14.1), (0.3, -0.4, 1.0), 4.5, 0.03, -2.0)
+    gi = g.add_squirmer(*args, mobile=True)
+    oi = o.add_sphere(*args, mobile=True)
+    g.step(200)
+    o.step(200)
+    _, ug = g.fields()
+    _, uo = o.fields()
+    both = (g.owner() == 0) & (o.owner() == 0)
+    assert rel(ug[:, both], uo[:, both]) < tol
+    vg, vo = g.state(gi)[1], o.state(oi)[1]
+    assert np.abs(vg - vo).max() / np.abs(vo).max() < tol
