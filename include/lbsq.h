@@ -207,6 +207,12 @@ const char* lb_last_error(const lb_ctx* c);
 /* Number of kernel launches the context has enqueued so far (all kinds). */
 int64_t lb_kernel_launches(const lb_ctx* c);
 
+/* Tuning: the launch shape of the stream-collide kernel.  0 = default (two
+ * cells per thread with paired loads where nx is even, except FP64), 1 = one
+ * cell per thread, 2 = two cells per thread where nx is even.  Results are
+ * identical bit for bit; only the speed differs. */
+lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant);
+
 /* Kernel tracing.  Between lb_profile_begin and lb_profile_end, lb_step
  * launches each kernel of a step directly (no graph) with a CUDA event
  * recorded on the context's stream before and after it.  lb_profile_end

@@ -13,7 +13,7 @@
 #include "lbsq_internal.cuh"
 
 namespace lbsq {
-void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, cudaStream_t st);
+void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, cudaStream_t st);
 void launch_body_step(const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
                       cudaStream_t st);
 void launch_relink(const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
@@ -77,6 +77,7 @@ struct lb_ctx {
     std::vector<std::pair<void*, size_t>> allocs;
     // graph of two steps (even then odd)
     cudaGraphExec_t graph = nullptr;
+    int sweep_variant = 0;
     // kernel tracing
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -227,12 +228,19 @@ lb_status ensure_body_capacity(lb_ctx* c, int n) {
 // buffers and upload the body parameters.
 lb_status relayout(lb_ctx* c) {
     const int nb = (int)c->par.size();
-    int64_t off = 0, max_cap = 0, max_box = 0;
+    int64_t off = 0;
+    int gl = 1, gb = 1;
     for (auto& b : c->par) {
         b.link_off = off;
         off += b.link_cap;
-        max_cap = std::max(max_cap, b.link_cap);
-        max_box = std::max(max_box, (int64_t)b.box_w[0] * b.box_w[1] * b.box_w[2]);
+        // block counts depend on the body alone: one link kernel block per 2048
+        // link slots (at most 128), one box-kernel block per 512 box cells (at
+        // most 256); so do its fixed-order reductions
+        const int64_t box = (int64_t)b.box_w[0] * b.box_w[1] * b.box_w[2];
+        b.g_links = (int)std::min<int64_t>(128, std::max<int64_t>(1, (b.link_cap + 2047) / 2048));
+        b.g_box = (int)std::min<int64_t>(256, std::max<int64_t>(1, (box + 511) / 512));
+        gl = std::max(gl, b.g_links);
+        gb = std::max(gb, b.g_box);
     }
     if (off > c->links_total) {
         dfree(c, c->d_links);
@@ -240,8 +248,8 @@ lb_status relayout(lb_ctx* c) {
         if (!c->d_links) return fail(c, LB_ERR_OOM, "link lists");
         c->links_total = off;
     }
-    c->G_links = (int)std::min<int64_t>(128, std::max<int64_t>(1, (max_cap + 2047) / 2048));
-    c->G_box = (int)std::min<int64_t>(256, std::max<int64_t>(1, (max_box + 2047) / 2048));
+    c->G_links = gl;
+    c->G_box = gb;
     dfree(c, c->d_part_links);
     dfree(c, c->d_part_conv);
     dfree(c, c->d_part_count);
@@ -486,8 +494,7 @@ lb_status lb_add_wall(lb_ctx* c, int32_t kind, const double* params, int32_t npa
     bp.link_cap = 10 * area + 64;
     for (int a = 0; a < 3; ++a) bp.box_w[a] = n3[a];
     bp.box_w[axis] = std::min(3, n3[axis]);
-    BodyState st{};
-    st.e[2] = 1.0;
+    BodyState st{};  // a wall has no position, velocity or orientation of its own
     int32_t nid = 0;
     lb_status s = new_body(c, bp, st, BODY_WALL, &nid);
     if (s != LB_OK) return s;
@@ -573,7 +580,7 @@ static void enqueue_step(lb_ctx* c, int parity) {
         for (int k = 0; k < nk; ++k) {
             const size_t e0 = 2 * c->ev_used.size();
             cudaEventRecord(pool_event(c, e0), c->stream);
-            if (k == 0) launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->stream);
+            if (k == 0) launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, c->stream);
             else launch_body_kernel(k, c->L, bodies_view(c), c->own, c->own_prev, parity, c->stream);
             cudaEventRecord(pool_event(c, e0 + 1), c->stream);
             c->ev_used.emplace_back(k, (int)e0);
@@ -581,7 +588,7 @@ static void enqueue_step(lb_ctx* c, int parity) {
         c->launches += nk;
         return;
     }
-    launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->stream);
+    launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, c->stream);
     c->launches += 1;
     if (!c->par.empty()) {
         launch_body_step(c->L, bodies_view(c), c->own, c->own_prev, parity, c->stream);
@@ -641,6 +648,13 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
         c->step++;
     }
     CK(cudaGetLastError());
+    return LB_OK;
+}
+
+lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant) {
+    if (!c || variant < 0 || variant > 2) return LB_ERR_INVALID;
+    c->sweep_variant = variant;
+    drop_graph(c);
     return LB_OK;
 }
 

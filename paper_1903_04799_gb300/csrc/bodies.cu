@@ -136,6 +136,23 @@ __device__ __forceinline__ bool last_block(int* counter, int nblocks) {
     return is_last != 0;
 }
 
+// In the elected last block: stage the G x K partials in shared memory with
+// all threads (cache-global loads, so no stale L1 line is read), then thread 0
+// sums them in block order -- the same fixed order as a serial loop.
+constexpr int kMaxPart = 1536;
+template <int K>
+__device__ __forceinline__ void ordered_partial_sum(const double* part, int G, double (&tot)[K]) {
+    __shared__ double sp[kMaxPart];
+    for (int t = threadIdx.x; t < G * K; t += blockDim.x) sp[t] = __ldcg(part + t);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < K; ++c) tot[c] = 0.0;
+    if (threadIdx.x == 0)
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int c = 0; c < K; ++c) tot[c] += sp[g * K + c];
+}
+
 // ---------------------------------------------------------------- geometry
 
 __device__ __forceinline__ void cross3(const double* a, const double* b, double* c) {
@@ -207,6 +224,8 @@ template <int P>
 __global__ void __launch_bounds__(kBlock) k_links(const Lattice L, const Bodies B) {
     const int k = blockIdx.y;
     const BodyParams& p = B.par[k];
+    const int G = p.g_links;
+    if ((int)blockIdx.x >= G) return;
     const BodyState& s = B.state[P][k];
     BodyAcc& A = B.acc[k];
     const long long cnt = A.link_count;
@@ -215,8 +234,7 @@ __global__ void __launch_bounds__(kBlock) k_links(const Lattice L, const Bodies 
     double acc[12];
 #pragma unroll
     for (int c = 0; c < 12; ++c) acc[c] = 0.0;
-    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < cnt;
-         l += (long long)gridDim.x * blockDim.x) {
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < cnt; l += (long long)G * blockDim.x) {
         const uint32_t code = links[l];
         const int64_t n = code >> 5;
         const int i = code & 31, ib = opp(i);
@@ -255,15 +273,12 @@ __global__ void __launch_bounds__(kBlock) k_links(const Lattice L, const Bodies 
     double* part = B.part_links + ((size_t)k * B.G_links + blockIdx.x) * 12;
     if (threadIdx.x == 0)
         for (int c = 0; c < 12; ++c) part[c] = acc[c];
-    if (!last_block(&A.counter_links, gridDim.x)) return;
-    if (threadIdx.x != 0) return;
+    if (!last_block(&A.counter_links, G)) return;
 
     // ---- final fixed-order sum of the partials
     double tot[12];
-    for (int c = 0; c < 12; ++c) tot[c] = 0.0;
-    const volatile double* pb = B.part_links + (size_t)k * B.G_links * 12;
-    for (int g = 0; g < (int)gridDim.x; ++g)
-        for (int c = 0; c < 12; ++c) tot[c] += pb[g * 12 + c];
+    ordered_partial_sum<12>(B.part_links + (size_t)k * B.G_links * 12, G, tot);
+    if (threadIdx.x != 0) return;
     for (int a = 0; a < 3; ++a) {
         A.Fbb[a] = tot[a];
         A.Tbb[a] = tot[3 + a];
@@ -363,7 +378,7 @@ __global__ void __launch_bounds__(kBlock) k_classify(const Lattice L, const Bodi
         }
         A.relink = rl;
     }
-    if (!A.reclass) return;
+    if (!A.reclass || (int)blockIdx.x >= p.g_box) return;
     int lo[3], w[3];
     body_box(L, p, s, lo, w);
     if (blockIdx.x == 0 && threadIdx.x == 0)
@@ -373,7 +388,7 @@ __global__ void __launch_bounds__(kBlock) k_classify(const Lattice L, const Bodi
         }
     const int id = k + 1;
     long long b0, b1;
-    box_range((long long)w[0] * w[1] * w[2], blockIdx.x, gridDim.x, b0, b1);
+    box_range((long long)w[0] * w[1] * w[2], blockIdx.x, p.g_box, b0, b1);
     double mloc = DBL_MAX;
     for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
         const int bx = (int)(b % w[0]), by = (int)((b / w[0]) % w[1]), bz = (int)(b / ((long long)w[0] * w[1]));
@@ -394,7 +409,10 @@ __global__ void __launch_bounds__(kBlock) k_classify(const Lattice L, const Bodi
         } else if (old == id) {
             own[n] = 0;
         }
-        mloc = fmin(mloc, fabs(sqrt(dx * dx + dy * dy + dz * dz) - p.R));
+        // distance of the node to the surface, as a lower bound: FP32 square
+        // root (relative error < 1e-6 on values below 1e3) minus 1e-4
+        const float dist = sqrtf((float)(dx * dx + dy * dy + dz * dz));
+        mloc = fmin(mloc, (double)fmaxf(fabsf(dist - (float)p.R) - 1e-4f, 0.0f));
     }
     mloc = block_min(mloc);
     if (threadIdx.x == 0) atomicMin(&A.margin_bits, (unsigned long long)__double_as_longlong(mloc));
@@ -405,8 +423,9 @@ __global__ void __launch_bounds__(kBlock) k_convert(const Lattice L, const Bodie
                                                       const int32_t* own_prev) {
     const int k = blockIdx.y;
     BodyAcc& A = B.acc[k];
-    if (!A.relink) return;
     const BodyParams& p = B.par[k];
+    const int G = p.g_box;
+    if (!A.relink || (int)blockIdx.x >= G) return;
     const BodyState& s = B.state[1 - P][k];
     const int q = 1 - P;  // parity of the next sweep
     const int id = k + 1;
@@ -414,7 +433,7 @@ __global__ void __launch_bounds__(kBlock) k_convert(const Lattice L, const Bodie
     int lo[3], w[3];
     body_box(L, p, s, lo, w);
     long long b0, b1;
-    box_range((long long)w[0] * w[1] * w[2], blockIdx.x, gridDim.x, b0, b1);
+    box_range((long long)w[0] * w[1] * w[2], blockIdx.x, G, b0, b1);
     double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     long long lcount = 0;
     for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
@@ -491,12 +510,10 @@ __global__ void __launch_bounds__(kBlock) k_convert(const Lattice L, const Bodie
         for (int c = 0; c < 6; ++c) part[c] = acc[c];
         B.part_count[(size_t)k * B.G_box + blockIdx.x] = (int)lcount;
     }
-    if (!last_block(&A.counter_conv, gridDim.x)) return;
-    if (threadIdx.x != 0 || !conv) return;
-    const volatile double* pb = B.part_conv + (size_t)k * B.G_box * 6;
-    double tot[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int g = 0; g < (int)gridDim.x; ++g)
-        for (int c = 0; c < 6; ++c) tot[c] += pb[g * 6 + c];
+    if (!last_block(&A.counter_conv, G) || !conv) return;
+    double tot[6];
+    ordered_partial_sum<6>(B.part_conv + (size_t)k * B.G_box * 6, G, tot);
+    if (threadIdx.x != 0) return;
     for (int a = 0; a < 3; ++a) {
         A.Fc[a] += tot[a];
         A.Tc[a] += tot[3 + a];
@@ -508,32 +525,39 @@ __global__ void __launch_bounds__(kBlock) k_rebuild(const Lattice L, const Bodie
                                                       int32_t* own_prev) {
     const int k = blockIdx.y;
     BodyAcc& A = B.acc[k];
-    if (!A.relink) return;
     const BodyParams& p = B.par[k];
+    const int G = p.g_box;
+    if (!A.relink || (int)blockIdx.x >= G) return;
     const BodyState& s = B.state[1 - P][k];
     const int id = k + 1;
     int lo[3], w[3];
     body_box(L, p, s, lo, w);
+    // offset of this block's links: the counts of the blocks before it
     __shared__ long long s_base, s_total;
-    if (threadIdx.x == 0) {
-        long long base = 0, total = 0;
+    {
         const int* pc = B.part_count + (size_t)k * B.G_box;
-        for (int g = 0; g < (int)gridDim.x; ++g) {
-            if (g < (int)blockIdx.x) base += pc[g];
-            total += pc[g];
+        long long before = 0, all = 0;
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            const long long v = __ldcg(pc + g);
+            all += v;
+            if (g < (int)blockIdx.x) before += v;
         }
-        s_base = base;
-        s_total = total;
-        if (blockIdx.x == 0) {
-            if (total > p.link_cap) set_error(B.err, 8);
-            A.link_count = total < p.link_cap ? total : p.link_cap;
+        before = block_sum_ll(before);
+        all = block_sum_ll(all);
+        if (threadIdx.x == 0) {
+            s_base = before;
+            s_total = all;
+            if (blockIdx.x == 0) {
+                if (all > p.link_cap) set_error(B.err, 8);
+                A.link_count = all < p.link_cap ? all : p.link_cap;
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     long long base = s_base;
     uint32_t* links = B.links + p.link_off;
     long long b0, b1;
-    box_range((long long)w[0] * w[1] * w[2], blockIdx.x, gridDim.x, b0, b1);
+    box_range((long long)w[0] * w[1] * w[2], blockIdx.x, G, b0, b1);
     for (long long r0 = b0; r0 < b1; r0 += blockDim.x) {
         const long long b = r0 + threadIdx.x;
         uint32_t mask = 0;

@@ -95,10 +95,11 @@ __device__ __forceinline__ int64_t cell_index(const Lattice& L, int x, int y, in
 }
 
 __device__ __forceinline__ void cell_coords(const Lattice& L, int64_t n, int& x, int& y, int& z) {
-    x = (int)(n % L.nx);
-    int64_t r = n / L.nx;
-    y = (int)(r % L.ny);
-    z = (int)(r / L.ny);
+    // cell counts stay below 2^31 (enforced at creation), so 32-bit division suffices
+    const unsigned m = (unsigned)n, r = m / (unsigned)L.nx;
+    x = (int)(m - r * (unsigned)L.nx);
+    y = (int)(r % (unsigned)L.ny);
+    z = (int)(r / (unsigned)L.ny);
 }
 
 // Flat index (plane * Np + cell) of the read slot of population i of cell
@@ -156,6 +157,8 @@ struct BodyParams {
     int64_t link_off;  // first slot of this body's link segment
     int64_t link_cap;  // capacity of the segment
     int box_w[3];      // scan box extent (spheres: W = ceil(2R)+6 per axis)
+    int g_links;       // blocks of the link kernel for this body (fixed by the body alone)
+    int g_box;         // blocks of the box kernels for this body
     int pad;
 };
 

@@ -78,6 +78,7 @@ SIGNATURES = {
     "lb_get_links": (C.c_int, [_CTX, C.c_int32, _LP, C.c_int64, _LP]),
     "lb_last_error": (C.c_char_p, [_CTX]),
     "lb_kernel_launches": (C.c_int64, [_CTX]),
+    "lb_set_sweep_variant": (C.c_int, [_CTX, C.c_int32]),
     "lb_profile_begin": (C.c_int, [_CTX]),
     "lb_profile_end": (C.c_int, [_CTX, _DP, _LP]),
 }
@@ -259,6 +260,10 @@ def lb_kernel_launches(ctx) -> int:
 KERNEL_KINDS = ("sweep", "links", "classify", "convert", "rebuild")
 
 
+def lb_set_sweep_variant(ctx, variant: int):
+    _check(ctx, load().lb_set_sweep_variant(ctx, int(variant)), "lb_set_sweep_variant")
+
+
 def lb_profile_begin(ctx):
     _check(ctx, load().lb_profile_begin(ctx), "lb_profile_begin")
 
@@ -402,6 +407,9 @@ class Lattice:
 
     def links(self, oid=0):
         return lb_get_links(self.ctx, oid)
+
+    def set_sweep_variant(self, variant):
+        lb_set_sweep_variant(self.ctx, variant)
 
     def profile_begin(self):
         lb_profile_begin(self.ctx)
