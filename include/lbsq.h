@@ -224,6 +224,39 @@ lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant);
 lb_status lb_profile_begin(lb_ctx* c);
 lb_status lb_profile_end(lb_ctx* c, double total_ms[5], int64_t launches[5]);
 
+/* ---- Allocation-free entry point (the paper has no counterpart) ----------
+ * For callers that must not allocate device memory: code that runs while a
+ * host framework owns all device memory through its own pool, code inside a
+ * latency-critical loop where a cudaMalloc would synchronise the device, or a
+ * monitoring hook that must not change the memory footprint of the program
+ * it watches.  Such callers cannot create an lb_ctx either (lb_create
+ * allocates), so this call works on buffers the caller already owns.
+ *
+ * lb_fluid_totals_static sums mass (sum of f_i) and momentum (sum of
+ * f_i c_i) over the fluid cells of a population field, like lb_get_mass,
+ * and writes out[4] = {mass, jx, jy, jz}.  It calls no cudaMalloc, cudaFree
+ * or allocating library routine: its per-block partial sums live in a
+ * file-scope device array of LB_STATIC_PARTIALS x 4 doubles (32 KiB), which
+ * every GPU that loads the library holds until the process exits.
+ *   f       device, FP64 [19][n_cells] absolute populations in the velocity
+ *           order of this header, cells x-fastest (the layout of
+ *           lb_get_populations);
+ *   owner   device int32 [n_cells], 0 = fluid (the layout of lb_get_owner),
+ *           or NULL to count every cell;
+ *   out     device, 4 doubles;
+ *   stream  cudaStream_t, or NULL for the legacy default stream.
+ * Runs on the current device, stream-ordered; it does not synchronise.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU race, so
+ * issue them on one stream.  Each call writes every partial it reads, so
+ * nothing needs clearing between calls.  Errors: LB_ERR_INVALID (f or out
+ * NULL, n_cells outside [1, LB_STATIC_MAX_CELLS]), LB_ERR_CUDA. */
+#define LB_STATIC_PARTIALS 1024
+#define LB_STATIC_MAX_CELLS (1LL << 27)
+lb_status lb_fluid_totals_static(const double* f, const int32_t* owner, int64_t n_cells, double* out,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

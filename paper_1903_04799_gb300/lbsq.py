@@ -81,6 +81,7 @@ SIGNATURES = {
     "lb_set_sweep_variant": (C.c_int, [_CTX, C.c_int32]),
     "lb_profile_begin": (C.c_int, [_CTX]),
     "lb_profile_end": (C.c_int, [_CTX, _DP, _LP]),
+    "lb_fluid_totals_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -273,6 +274,14 @@ def lb_profile_end(ctx):
     n = np.zeros(5, dtype=np.int64)
     _check(ctx, load().lb_profile_end(ctx, _dp(t), n.ctypes.data_as(_LP)), "lb_profile_end")
     return {k: (float(t[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def lb_fluid_totals_static(f_ptr: int, owner_ptr: int, n_cells: int, out_ptr: int, stream_ptr: int = 0):
+    """Allocation-free fluid mass and momentum of caller-owned device buffers
+    (see include/lbsq.h); pointers are raw device addresses."""
+    _check(None, load().lb_fluid_totals_static(C.c_void_p(f_ptr), C.c_void_p(owner_ptr or None), int(n_cells),
+                                                C.c_void_p(out_ptr), C.c_void_p(stream_ptr or None)),
+           "lb_fluid_totals_static")
 
 
 # ------------------------------------------------------------ torch plumbing
