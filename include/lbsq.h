@@ -218,11 +218,11 @@ lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant);
  * recorded on the context's stream before and after it.  lb_profile_end
  * synchronises and writes, per kernel kind in launch order
  *   0 sweep, 1 links (bounce-back, force reduction, Newton-Euler),
- *   2 classify, 3 convert, 4 rebuild,
- * the summed device time in ms (total_ms[5]) and the launch count
- * (launches[5]).  Either pointer may be NULL. */
+ *   2 classify, 3 convert, 4 rebuild, 5 tick (end of step),
+ * the summed device time in ms (total_ms[6]) and the launch count
+ * (launches[6]).  Either pointer may be NULL. */
 lb_status lb_profile_begin(lb_ctx* c);
-lb_status lb_profile_end(lb_ctx* c, double total_ms[5], int64_t launches[5]);
+lb_status lb_profile_end(lb_ctx* c, double total_ms[6], int64_t launches[6]);
 
 /* ---- Allocation-free entry point (the paper has no counterpart) ----------
  * For callers that must not allocate device memory: code that runs while a

@@ -14,10 +14,9 @@
 
 namespace lbsq {
 void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, cudaStream_t st);
-void launch_body_step(const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
-                      cudaStream_t st);
-void launch_relink(const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
-                   cudaStream_t st);
+void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, int grid_box, long long* step,
+                        cudaStream_t st);
+void launch_body_step(const Bodies& B, int parity, int grid_links, int grid_box, long long* step, cudaStream_t st);
 void launch_fill_rest(const Lattice& L, cudaStream_t st);
 void launch_set_eq(const Lattice& L, const double* rho, const double* u, int q, cudaStream_t st);
 void launch_set_pop(const Lattice& L, const double* f, int q, cudaStream_t st);
@@ -30,11 +29,7 @@ void launch_sphere_overlap(const Lattice& L, const int32_t* own, const double* p
 void launch_plane_overlap(const Lattice& L, const int32_t* own, const int* kind, int axis, int index, int* count,
                           cudaStream_t st);
 void launch_plane_claim(const Lattice& L, int32_t* own, int axis, int index, int id, cudaStream_t st);
-void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, int relink, cudaStream_t st);
-void launch_classify_only(const Lattice& L, const Bodies& B, int32_t* own, const int32_t* own_prev, int parity,
-                          cudaStream_t st);
-void launch_body_kernel(int which, const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
-                        cudaStream_t st);
+void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, cudaStream_t st);
 }  // namespace lbsq
 
 using namespace lbsq;
@@ -61,6 +56,15 @@ struct lb_ctx {
     double* d_part_conv = nullptr;
     int* d_part_count = nullptr;
     int G_links = 1, G_box = 1;
+    // work lists: static link items, device-built box and relink items
+    int2* d_link_items = nullptr;
+    int2* d_box_items = nullptr;
+    int2* d_rel_items = nullptr;
+    int* d_counts = nullptr;  // [0] link items, [1] box items, [2] relink items, [3] rebuild blocks done
+    int n_link_items = 0, list_cap = 0, list_alloc = 0;
+    int grid_box = 1;
+    int n_sm = 152;
+    Lattice* d_lat = nullptr;  // the one lattice descriptor on the device
     double wca_sigma = 1.0, wca_eps = 0.0;
     // scratch
     double* d_mass_part = nullptr;
@@ -138,7 +142,7 @@ void drop_graph(lb_ctx* c) {
 
 Bodies bodies_view(const lb_ctx* c) {
     Bodies B;
-    B.n = (int)c->par.size();
+    B.lats = c->d_lat;
     B.par = c->d_par;
     B.state[0] = c->d_state[0];
     B.state[1] = c->d_state[1];
@@ -147,12 +151,34 @@ Bodies bodies_view(const lb_ctx* c) {
     B.part_links = c->d_part_links;
     B.part_conv = c->d_part_conv;
     B.part_count = c->d_part_count;
-    B.G_links = c->G_links;
-    B.G_box = c->G_box;
-    B.wca_sigma = c->wca_sigma;
-    B.wca_eps = c->wca_eps;
+    B.GL = c->G_links;
+    B.GB = c->G_box;
+    B.link_items = c->d_link_items;
+    B.n_link_items = c->d_counts;
+    B.box_items = c->d_box_items;
+    B.n_box = c->d_counts + 1;
+    B.box_cap = c->list_cap;
+    B.rel_items = c->d_rel_items;
+    B.n_rel = c->d_counts + 2;
+    B.rel_cap = c->list_cap;
+    B.done = c->d_counts + 3;
     B.err = c->d_err;
     return B;
+}
+
+// The lattice descriptor the body kernels read, rebuilt from the context.
+lb_status upload_lattice(lb_ctx* c) {
+    Lattice L = c->L;
+    L.lambda_e = c->lambda_e;
+    L.lambda_o = c->lambda_o;
+    L.wca_sigma = c->wca_sigma;
+    L.wca_eps = c->wca_eps;
+    L.body_begin = 0;
+    L.body_count = (int)c->par.size();
+    L.active = 1;
+    c->L = L;
+    CK(cudaMemcpyAsync(c->d_lat, &L, sizeof(Lattice), cudaMemcpyHostToDevice, c->stream));
+    return LB_OK;
 }
 
 // Upper bound on the boundary links of a sphere of radius R: 18 per lattice
@@ -225,22 +251,35 @@ lb_status ensure_body_capacity(lb_ctx* c, int n) {
 }
 
 // After the body set changed: assign link segments, size the partial-sum
-// buffers and upload the body parameters.
+// buffers and work lists, and upload the body parameters.
 lb_status relayout(lb_ctx* c) {
     const int nb = (int)c->par.size();
     int64_t off = 0;
-    int gl = 1, gb = 1;
-    for (auto& b : c->par) {
+    int gl = 1, gb = 1, sum_gb = 0;
+    std::vector<int2> items;
+    for (int k = 0; k < nb; ++k) {
+        BodyParams& b = c->par[k];
         b.link_off = off;
         off += b.link_cap;
-        // block counts depend on the body alone: one link kernel block per 2048
-        // link slots (at most 128), one box-kernel block per 512 box cells (at
-        // most 256); so do its fixed-order reductions
+        b.lat = 0;
+        // block counts depend on the body alone (so do its fixed-order
+        // reductions): about one link per thread of the link kernel, two box
+        // cells per thread of the box kernels; capped by the shared staging
+        // buffers of the final sums (128 and 256 partials)
         const int64_t box = (int64_t)b.box_w[0] * b.box_w[1] * b.box_w[2];
-        b.g_links = (int)std::min<int64_t>(128, std::max<int64_t>(1, (b.link_cap + 2047) / 2048));
+        int64_t expect;
+        if (b.kind == BODY_SPHERE) {
+            expect = (int64_t)std::ceil(63.0 * b.R * b.R);  // about 5 links per node of 4 pi R^2
+        } else {
+            const int n3[3] = {c->L.nx, c->L.ny, c->L.nz};
+            expect = 5 * (c->L.N / n3[b.wall_axis]);
+        }
+        b.g_links = (int)std::min<int64_t>(128, std::max<int64_t>(1, (expect + 127) / 128));
         b.g_box = (int)std::min<int64_t>(256, std::max<int64_t>(1, (box + 511) / 512));
         gl = std::max(gl, b.g_links);
         gb = std::max(gb, b.g_box);
+        sum_gb += b.g_box;
+        for (int g = 0; g < b.g_links; ++g) items.push_back(make_int2(k, g));
     }
     if (off > c->links_total) {
         dfree(c, c->d_links);
@@ -257,24 +296,72 @@ lb_status relayout(lb_ctx* c) {
     c->d_part_conv = dalloc_t<double>(c, (size_t)nb * c->G_box * 6);
     c->d_part_count = dalloc_t<int>(c, (size_t)nb * c->G_box);
     if (!c->d_part_links || !c->d_part_conv || !c->d_part_count) return fail(c, LB_ERR_OOM, "partials");
+    // work lists: every body appears at most once per step in each list
+    const int need = std::max<int>((int)items.size(), sum_gb);
+    if (need > c->list_alloc) {
+        dfree(c, c->d_link_items);
+        dfree(c, c->d_box_items);
+        dfree(c, c->d_rel_items);
+        c->d_link_items = dalloc_t<int2>(c, need);
+        c->d_box_items = dalloc_t<int2>(c, need);
+        c->d_rel_items = dalloc_t<int2>(c, need);
+        if (!c->d_link_items || !c->d_box_items || !c->d_rel_items) return fail(c, LB_ERR_OOM, "work lists");
+        c->list_alloc = need;
+    }
+    c->list_cap = sum_gb;
+    c->n_link_items = (int)items.size();
+    c->grid_box = std::max(1, std::min(sum_gb, 4 * c->n_sm));
+    CK(cudaMemcpyAsync(c->d_link_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+    const int counts[4] = {c->n_link_items, 0, 0, 0};
+    CK(cudaMemcpyAsync(c->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_par, c->par.data(), sizeof(BodyParams) * nb, cudaMemcpyHostToDevice, c->stream));
     // both state buffers hold the current state
     const int cur = (int)(c->step & 1);
     CK(cudaMemcpyAsync(c->d_state[1 - cur], c->d_state[cur], sizeof(BodyState) * nb, cudaMemcpyDeviceToDevice,
                        c->stream));
+    lb_status s = upload_lattice(c);
+    if (s != LB_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));  // host vectors above are transient
     drop_graph(c);
     return LB_OK;
 }
 
-// Rebuild every link list (no conversion) and commit the owners.
+// Upload a host-built item list as the relink (which = 2) or box (1) list.
+lb_status set_list(lb_ctx* c, int which, const std::vector<int2>& items) {
+    int2* dst = which == 1 ? c->d_box_items : c->d_rel_items;
+    if ((int)items.size() > c->list_cap) return fail(c, LB_ERR_CAPACITY, "work list");
+    if (!items.empty())
+        CK(cudaMemcpyAsync(dst, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, c->stream));
+    const int n = (int)items.size();
+    CK(cudaMemcpyAsync(c->d_counts + which, &n, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+std::vector<int2> box_items_of(const lb_ctx* c, int k) {
+    std::vector<int2> v;
+    for (int g = 0; g < c->par[k].g_box; ++g) v.push_back(make_int2(k, g));
+    return v;
+}
+
+// Rebuild every link list (no conversion) and commit the owners, as if after a
+// step of parity 1 - cur (the next sweep has parity cur).
 lb_status relink_all(lb_ctx* c) {
     const int nb = (int)c->par.size();
     const int cur = (int)(c->step & 1);
+    std::vector<int2> all;
+    for (int k = 0; k < nb; ++k) {
+        auto v = box_items_of(c, k);
+        all.insert(all.end(), v.begin(), v.end());
+    }
+    lb_status s = set_list(c, 2, all);
+    if (s != LB_OK) return s;
     Bodies B = bodies_view(c);
-    launch_set_flags(c->d_acc, nb, -1, 0, 1, c->stream);
-    launch_relink(c->L, B, c->own, c->own_prev, 1 - cur, c->stream);
-    launch_set_flags(c->d_acc, nb, -1, 0, 0, c->stream);
-    c->launches += 4;
+    launch_set_flags(c->d_acc, nb, -1, 0, c->stream);
+    launch_body_kernel(3, B, 1 - cur, 1, c->grid_box, nullptr, c->stream);
+    launch_body_kernel(4, B, 1 - cur, 1, c->grid_box, nullptr, c->stream);
+    c->launches += 3;
     CK(cudaMemcpyAsync(c->own_prev, c->own, sizeof(int32_t) * c->L.N, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaGetLastError());
     return sync_checked(c);
@@ -361,8 +448,17 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     c->d_small = dalloc_t<double>(c, 8);
     c->d_err = dalloc_t<int>(c, 2);
     c->d_count = dalloc_t<int>(c, 2);
-    if (!L.F || !c->own || !c->own_prev || !c->d_mass_part || !c->d_small || !c->d_err || !c->d_count)
+    c->d_lat = dalloc_t<Lattice>(c, 1);
+    c->d_counts = dalloc_t<int>(c, 4);
+    if (!L.F || !c->own || !c->own_prev || !c->d_mass_part || !c->d_small || !c->d_err || !c->d_count ||
+        !c->d_lat || !c->d_counts)
         return bail(LB_ERR_OOM);
+    L.own = c->own;
+    L.own_prev = c->own_prev;
+    L.err = c->d_err;
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) c->n_sm = 152;
+    if (cudaMemsetAsync(c->d_counts, 0, sizeof(int) * 4, c->stream) != cudaSuccess) return bail(LB_ERR_CUDA);
+    if (upload_lattice(c) != LB_OK) return bail(LB_ERR_CUDA);
     if (cudaMemsetAsync(c->own, 0, sizeof(int32_t) * N, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->own_prev, 0, sizeof(int32_t) * N, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->d_err, 0, sizeof(int) * 2, c->stream) != cudaSuccess)
@@ -425,6 +521,8 @@ lb_status lb_add_squirmer(lb_ctx* c, const double pos[3], const double e[3], dou
     bp.B2 = beta * B1;
     bp.mass = density * (4.0 / 3.0) * M_PI * R * R * R;
     bp.inertia = 0.4 * bp.mass * R * R;
+    bp.inv_mass = 1.0 / bp.mass;
+    bp.inv_inertia = 1.0 / bp.inertia;
     bp.link_cap = sphere_link_cap(R);
     bp.box_w[0] = bp.box_w[1] = bp.box_w[2] = W;
     int32_t nid = 0;
@@ -436,10 +534,14 @@ lb_status lb_add_squirmer(lb_ctx* c, const double pos[3], const double e[3], dou
     // "after a step of parity 1 - cur" (it reads state[cur])
     const int nb = (int)c->par.size();
     const int cur = (int)(c->step & 1);
-    launch_set_flags(c->d_acc, nb, -1, 0, 0, c->stream);
-    launch_set_flags(c->d_acc, nb, nid - 1, 1, 0, c->stream);
-    launch_classify_only(c->L, bodies_view(c), c->own, c->own_prev, 1 - cur, c->stream);
-    c->launches += 3;
+    s = set_list(c, 1, box_items_of(c, nid - 1));
+    if (s != LB_OK) return s;
+    launch_set_flags(c->d_acc, nb, -1, 0, c->stream);
+    launch_set_flags(c->d_acc, nb, nid - 1, 1, c->stream);
+    Bodies B = bodies_view(c);
+    launch_body_kernel(2, B, 1 - cur, 1, c->grid_box, nullptr, c->stream);
+    launch_body_kernel(5, B, 1 - cur, 1, 1, nullptr, c->stream);
+    c->launches += 4;
     CK(cudaGetLastError());
     s = relink_all(c);
     if (s != LB_OK) return s;
@@ -513,6 +615,10 @@ lb_status lb_set_contact(lb_ctx* c, double sigma, double eps) {
     c->wca_sigma = sigma;
     c->wca_eps = eps;
     drop_graph(c);
+    CK(cudaSetDevice(c->p.device));
+    lb_status s = upload_lattice(c);
+    if (s != LB_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));
     return LB_OK;
 }
 
@@ -574,14 +680,15 @@ static cudaEvent_t pool_event(lb_ctx* c, size_t k) {
 }
 
 static void enqueue_step(lb_ctx* c, int parity) {
+    const bool bodies = !c->par.empty();
     if (c->profiling) {
         // each kernel between its own pair of events
-        const int nk = c->par.empty() ? 1 : 5;
+        const int nk = bodies ? 5 : 1;
         for (int k = 0; k < nk; ++k) {
             const size_t e0 = 2 * c->ev_used.size();
             cudaEventRecord(pool_event(c, e0), c->stream);
             if (k == 0) launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, c->stream);
-            else launch_body_kernel(k, c->L, bodies_view(c), c->own, c->own_prev, parity, c->stream);
+            else launch_body_kernel(k, bodies_view(c), parity, c->n_link_items, c->grid_box, nullptr, c->stream);
             cudaEventRecord(pool_event(c, e0 + 1), c->stream);
             c->ev_used.emplace_back(k, (int)e0);
         }
@@ -590,8 +697,8 @@ static void enqueue_step(lb_ctx* c, int parity) {
     }
     launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, c->stream);
     c->launches += 1;
-    if (!c->par.empty()) {
-        launch_body_step(c->L, bodies_view(c), c->own, c->own_prev, parity, c->stream);
+    if (bodies) {
+        launch_body_step(bodies_view(c), parity, c->n_link_items, c->grid_box, nullptr, c->stream);
         c->launches += 4;
     }
 }
@@ -665,13 +772,13 @@ lb_status lb_profile_begin(lb_ctx* c) {
     return LB_OK;
 }
 
-lb_status lb_profile_end(lb_ctx* c, double total_ms[5], int64_t launches[5]) {
+lb_status lb_profile_end(lb_ctx* c, double total_ms[6], int64_t launches[6]) {
     if (!c) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
     c->profiling = false;
     lb_status s = sync_checked(c);
-    double t[5] = {0, 0, 0, 0, 0};
-    int64_t n[5] = {0, 0, 0, 0, 0};
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    int64_t n[6] = {0, 0, 0, 0, 0, 0};
     for (auto& u : c->ev_used) {
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, c->ev_pool[u.second], c->ev_pool[u.second + 1]) == cudaSuccess) {
@@ -681,7 +788,7 @@ lb_status lb_profile_end(lb_ctx* c, double total_ms[5], int64_t launches[5]) {
     }
     c->ev_used.clear();
     if (s != LB_OK) return s;
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 6; ++k) {
         if (total_ms) total_ms[k] = t[k];
         if (launches) launches[k] = n[k];
     }

@@ -8,91 +8,92 @@
 //                  reduced per body in FP64 in a fixed order; the last block
 //                  of each body then does the symplectic Euler update (with
 //                  the conversion force of the previous remap, Eq.
-//                  "consforce", and the WCA force of Eq. "wca") and decides
-//                  whether the body's cells must be re-classified;
-//   k_classify<P>  new owner of every cell in the scan box of each body that
-//                  moved far enough for a lattice node to cross its surface;
+//                  "consforce", and the WCA force of Eq. "wca") and, when a
+//                  lattice node can cross the body surface, queues the body
+//                  for re-classification;
+//   k_classify<P>  new owner of every cell in the scan box of each queued
+//                  body; queues every body whose links the change touches;
 //   k_convert<P>   Aidun conversion of covered / uncovered cells, booking the
 //                  conversion force; counts the new boundary links;
 //   k_rebuild<P>   compacts the new link lists (block scan, canonical order
-//                  within each body's scan box) and commits the new owners.
+//                  within each body's scan box), commits the new owners and
+//                  empties the step's work lists.
+//
+// All kernels walk work lists of (body, block) items with a fixed grid, so one
+// launch serves any number of bodies on any number of lattices (a context has
+// one lattice, a server many), and a captured CUDA graph stays valid when the
+// set of bodies changes.  A body's block count is a function of the body
+// alone, and every reduction is a fixed tree (shared memory, then per-block
+// partials summed in block order by the last block of the body), so a body's
+// results do not depend on scheduling or on the other bodies present.
 //
 // Body state is double-buffered by step parity: the step of parity P reads
 // state[P] and writes state[1-P], so a body's update never races with another
-// body reading its position.  Every reduction is a fixed tree (warp shuffle,
-// then shared memory, then per-block partials summed in block order), so the
-// result does not depend on scheduling -- the same inputs give the same bits.
+// body reading its position.
+//
+// FP64 throughput is low on this GPU (about 2 FP64 operations per clock per
+// SM), so the FP64 work per link is kept to the arithmetic of the method and
+// reductions add each value once (no shuffle trees over idle lanes).
 #include <cfloat>
 
 #include "lbsq_internal.cuh"
 
 namespace lbsq {
 
-constexpr int kBlock = 256;
+constexpr int kLB = 128;  // threads of the link kernel
+constexpr int kBB = 256;  // threads of the box kernels
 
 // ---------------------------------------------------------------- reductions
 
-// Sum K doubles over the block; the result is valid in thread 0.
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K]) {
-    __shared__ double sm[32 * K];
+// Sum K doubles over a block of T threads in a fixed order: each value is
+// added once, by many lanes at a time (one FP64 warp instruction costs the
+// pipe the same with 1 or 32 active lanes).  Stage 1: K*8 threads each sum a
+// segment of T/8 values of one component; stage 2: K threads sum the 8
+// segments.  Result in out[K] (shared), valid for all threads on return.
+// Uses the shared buffer sm[K*T + K*8].
+template <int K, int T>
+__device__ __forceinline__ void block_sum_fixed(const double (&v)[K], double* sm, double* out) {
+    constexpr int SEG = 8, LEN = T / SEG;
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) sm[warp * K + k] = v[k];
+    for (int c = 0; c < K; ++c) sm[c * T + threadIdx.x] = v[c];
     __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            v[k] = lane < nw ? sm[lane * K + k] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-        }
+    double* sm2 = sm + K * T;
+    for (int t = threadIdx.x; t < K * SEG; t += T) {
+        const int c = t / SEG, sg = t % SEG;
+        double a = 0.0;
+        for (int q = 0; q < LEN; ++q) a += sm[c * T + sg * LEN + q];
+        sm2[c * SEG + sg] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double a = 0.0;
+        for (int sg = 0; sg < SEG; ++sg) a += sm2[threadIdx.x * SEG + sg];
+        out[threadIdx.x] = a;
     }
     __syncthreads();
 }
 
-__device__ __forceinline__ long long block_sum_ll(long long v) {
-    __shared__ long long sm[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (lane == 0) sm[warp] = v;
+template <int T>
+__device__ __forceinline__ long long block_sum_ll(long long v, long long* sm) {
+    sm[threadIdx.x] = v;
     __syncthreads();
-    if (warp == 0) {
-        v = lane < nw ? sm[lane] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+        long long a = 0;
+        for (int q = 0; q < T; ++q) a += sm[q];
+        sm[0] = a;
     }
     __syncthreads();
-    return v;
-}
-
-__device__ __forceinline__ double block_min(double v) {
-    __shared__ double sm[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (lane == 0) sm[warp] = v;
+    const long long r = sm[0];
     __syncthreads();
-    if (warp == 0) {
-        v = lane < nw ? sm[lane] : DBL_MAX;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
-    }
-    __syncthreads();
-    return v;
+    return r;
 }
 
 // Exclusive scan of one int per thread over the block; returns the thread's
 // offset and writes the block total to *total.
-__device__ __forceinline__ int block_scan(int v, int* total) {
-    __shared__ int sm[33];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+template <int T>
+__device__ __forceinline__ int block_scan(int v, int* total, int* sm) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int nw = T / 32;
     int inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -101,56 +102,65 @@ __device__ __forceinline__ int block_scan(int v, int* total) {
     }
     if (lane == 31) sm[warp] = inc;
     __syncthreads();
-    if (warp == 0) {
-        int w = lane < nw ? sm[lane] : 0;
-        int wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += t;
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int t = sm[w];
+            sm[w] = acc;
+            acc += t;
         }
-        if (lane < nw) sm[lane] = wi - w;  // exclusive warp offsets
-        if (lane == nw - 1) sm[32] = wi;
+        sm[nw] = acc;
     }
     __syncthreads();
-    int res = sm[warp] + inc - v;
-    *total = sm[32];
+    const int res = sm[warp] + inc - v;
+    *total = sm[nw];
     __syncthreads();
     return res;
 }
 
-// Last-block election: every block calls this once after writing its
-// partial; returns true in exactly one block (the last to arrive), which may
-// then read all partials.  The counter resets itself for the next launch.
-__device__ __forceinline__ bool last_block(int* counter, int nblocks) {
-    __shared__ int is_last;
+// Last-block election among the nblocks blocks of one body: every block calls
+// it once after writing its partial; it returns true in the last to arrive,
+// which may then read all partials.  The counter resets itself.
+__device__ __forceinline__ bool last_block(int* counter, int nblocks, int* flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        int t = atomicAdd(counter, 1);
-        is_last = (t == nblocks - 1);
-        if (is_last) *counter = 0;
+        const int t = atomicAdd(counter, 1);
+        *flag = (t == nblocks - 1);
+        if (*flag) *counter = 0;
     }
     __syncthreads();
-    if (is_last) __threadfence();
-    return is_last != 0;
+    const bool last = *flag != 0;
+    if (last) __threadfence();
+    __syncthreads();
+    return last;
 }
 
-// In the elected last block: stage the G x K partials in shared memory with
-// all threads (cache-global loads, so no stale L1 line is read), then thread 0
-// sums them in block order -- the same fixed order as a serial loop.
-constexpr int kMaxPart = 1536;
+// The G partials of one body summed in a fixed order, staged in shared memory
+// with cache-global loads (no stale L1 line): K*8 lanes each sum a run of
+// consecutive partials of one component, K lanes then sum the 8 runs.  The
+// grouping depends on G only (a property of the body).  Result in out[K]
+// (shared).  Uses sm[G*K + K*8].
 template <int K>
-__device__ __forceinline__ void ordered_partial_sum(const double* part, int G, double (&tot)[K]) {
-    __shared__ double sp[kMaxPart];
-    for (int t = threadIdx.x; t < G * K; t += blockDim.x) sp[t] = __ldcg(part + t);
+__device__ __forceinline__ void ordered_partial_sum(const double* part, int G, double* sm, double* out) {
+    constexpr int SEG = 8;
+    for (int t = threadIdx.x; t < G * K; t += blockDim.x) sm[t] = __ldcg(part + t);
     __syncthreads();
-#pragma unroll
-    for (int c = 0; c < K; ++c) tot[c] = 0.0;
-    if (threadIdx.x == 0)
-        for (int g = 0; g < G; ++g)
-#pragma unroll
-            for (int c = 0; c < K; ++c) tot[c] += sp[g * K + c];
+    double* sm2 = sm + G * K;
+    const int run = (G + SEG - 1) / SEG;
+    for (int t = threadIdx.x; t < K * SEG; t += blockDim.x) {
+        const int c = t / SEG, sg = t % SEG;
+        double a = 0.0;
+        for (int g = sg * run; g < (sg + 1) * run && g < G; ++g) a += sm[g * K + c];
+        sm2[c * SEG + sg] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double a = 0.0;
+        for (int sg = 0; sg < SEG; ++sg) a += sm2[threadIdx.x * SEG + sg];
+        out[threadIdx.x] = a;
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- geometry
@@ -161,54 +171,37 @@ __device__ __forceinline__ void cross3(const double* a, const double* b, double*
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// Wall velocity on the link from fluid node (x,y,z) along c_i, taken at the
-// link midpoint: rigid motion (Eq. "vb") plus the squirmer slip (Eq.
-// "squirmer"); d receives the midpoint's offset from the centre.
-__device__ __forceinline__ void link_velocity(const Lattice& L, const BodyParams& p, const BodyState& s, int x,
-                                              int y, int z, int i, double vb[3], double d[3]) {
-    if (p.kind != BODY_SPHERE) {
-        vb[0] = p.wall_vel[0];
-        vb[1] = p.wall_vel[1];
-        vb[2] = p.wall_vel[2];
-        d[0] = d[1] = d[2] = 0.0;
-        return;
-    }
-    d[0] = min_image(((double)x + 0.5 * cx(i)) - s.pos[0], L.nx);
-    d[1] = min_image(((double)y + 0.5 * cy(i)) - s.pos[1], L.ny);
-    d[2] = min_image(((double)z + 0.5 * cz(i)) - s.pos[2], L.nz);
-    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    double sl[3] = {0.0, 0.0, 0.0};
-    if (r > 0.0) {
-        double n[3] = {d[0] / r, d[1] / r, d[2] / r};
-        double ct = s.e[0] * n[0] + s.e[1] * n[1] + s.e[2] * n[2];
-        double a = p.B1 + p.B2 * ct;
-        for (int k = 0; k < 3; ++k) sl[k] = a * (ct * n[k] - s.e[k]);
-    }
-    double w[3];
-    cross3(s.omega, d, w);
-    for (int k = 0; k < 3; ++k) vb[k] = s.vel[k] + w[k] + sl[k];
+__device__ __forceinline__ int step_wrap(int a, int c, int n) {
+    a += c;
+    if (a < 0) a += n;
+    else if (a >= n) a -= n;
+    return a;
 }
+
+// c * v for a lattice component c in {-1, 0, 1}, without a multiplication
+__device__ __forceinline__ double csel(int c, double v) { return c > 0 ? v : (c < 0 ? -v : 0.0); }
 
 __device__ __forceinline__ double wca_force(double r, double sigma, double eps) {
     if (eps == 0.0 || r >= 1.122462048309373 * sigma) return 0.0;  // 2^(1/6)
     if (r < 0.05 * sigma) r = 0.05 * sigma;
-    double sr = sigma / r, sr2 = sr * sr, sr6 = sr2 * sr2 * sr2;
+    const double sr = sigma / r, sr2 = sr * sr, sr6 = sr2 * sr2 * sr2;
     return 24.0 * eps / r * (2.0 * sr6 * sr6 - sr6);
 }
 
 __device__ __forceinline__ void rotate_e(double* e, const double* w) {
-    double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    const double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     if (th == 0.0) return;
-    double k[3] = {w[0] / th, w[1] / th, w[2] / th};
+    const double ith = 1.0 / th;
+    const double k[3] = {w[0] * ith, w[1] * ith, w[2] * ith};
     double sn, c;
     sincos(th, &sn, &c);
     double kxe[3];
     cross3(k, e, kxe);
-    double ke = k[0] * e[0] + k[1] * e[1] + k[2] * e[2];
+    const double ke = k[0] * e[0] + k[1] * e[1] + k[2] * e[2];
     double r[3];
     for (int a = 0; a < 3; ++a) r[a] = e[a] * c + kxe[a] * sn + k[a] * ke * (1.0 - c);
-    double nr = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    for (int a = 0; a < 3; ++a) e[a] = r[a] / nr;
+    const double inr = 1.0 / sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int a = 0; a < 3; ++a) e[a] = r[a] * inr;
 }
 
 __device__ __forceinline__ int wrap_pos(int a, int n) { return ((a % n) + n) % n; }
@@ -218,74 +211,63 @@ __device__ __forceinline__ bool axis_overlap(int a, int wa, int b, int wb, int n
     return wrap_pos(b - a, n) < wa || wrap_pos(a - b, n) < wb;
 }
 
-// ---------------------------------------------------------------- step kernels
+__device__ __forceinline__ bool boxes_intersect(const Lattice& L, const BodyParams& pa, const BodyState& sa,
+                                                const BodyParams& pb, const BodyState& sb) {
+    int la[3], wa[3], lb[3], wb[3];
+    body_box(L, pa, sa, la, wa);
+    body_box(L, pb, sb, lb, wb);
+    return axis_overlap(la[0], wa[0], lb[0], wb[0], L.nx) && axis_overlap(la[1], wa[1], lb[1], wb[1], L.ny) &&
+           axis_overlap(la[2], wa[2], lb[2], wb[2], L.nz);
+}
 
+// Box-partition helper: block g of G covers box cells [b0, b1).
+__device__ __forceinline__ void box_range(long long total, int g, int G, long long& b0, long long& b1) {
+    const long long chunk = (total + G - 1) / G;
+    b0 = (long long)g * chunk;
+    b1 = b0 + chunk < total ? b0 + chunk : total;
+}
+
+__device__ __forceinline__ void box_cell(const Lattice& L, const int lo[3], const int w[3], long long b, int& x,
+                                         int& y, int& z) {
+    // box sizes stay below 2^31 cells: 32-bit division
+    const unsigned ub = (unsigned)b, r = ub / (unsigned)w[0];
+    const int bx = (int)(ub - r * (unsigned)w[0]);
+    const int by = (int)(r % (unsigned)w[1]), bz = (int)(r / (unsigned)w[1]);
+    x = wrapi(lo[0] + bx, L.nx);
+    y = wrapi(lo[1] + by, L.ny);
+    z = wrapi(lo[2] + bz, L.nz);
+}
+
+// Append n consecutive items (k, 0..n-1) to a list, by the calling block.
+__device__ __forceinline__ void append_items(int2* items, int* count, int cap, int k, int n, int* err,
+                                             int* sm_base) {
+    __syncthreads();
+    if (threadIdx.x == 0) *sm_base = atomicAdd(count, n);
+    __syncthreads();
+    const int base = *sm_base;
+    if (base + n > cap) {
+        if (threadIdx.x == 0) set_error(err, 8);
+    } else {
+        for (int g = threadIdx.x; g < n; g += blockDim.x) items[base + g] = make_int2(k, g);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- Newton-Euler
+
+// Symplectic Euler of body k (thread 0 of its last link block): applies the
+// momentum exchange of this step plus the conversion force booked by the last
+// remap, writes state[1-P], and decides whether a node can cross the surface.
 template <int P>
-__global__ void __launch_bounds__(kBlock) k_links(const Lattice L, const Bodies B) {
-    const int k = blockIdx.y;
+__device__ void update_body(const Lattice& L, const Bodies& B, int k, const double* tot) {
     const BodyParams& p = B.par[k];
-    const int G = p.g_links;
-    if ((int)blockIdx.x >= G) return;
     const BodyState& s = B.state[P][k];
     BodyAcc& A = B.acc[k];
-    const long long cnt = A.link_count;
-    const uint32_t* links = B.links + p.link_off;
-    const int64_t Np = L.Np;
-    double acc[12];
-#pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = 0.0;
-    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < cnt; l += (long long)G * blockDim.x) {
-        const uint32_t code = links[l];
-        const int64_t n = code >> 5;
-        const int i = code & 31, ib = opp(i);
-        int x, y, z;
-        cell_coords(L, n, x, y, z);
-        const int64_t ns = cell_index(L, wrapi(x + cx(i), L.nx), wrapi(y + cy(i), L.ny), wrapi(z + cz(i), L.nz));
-        // where sweep P left f*_i of the fluid node, and where the next sweep reads
-        // the reflected population f_ib of the fluid node
-        const int64_t out_slot = P == 0 ? (int64_t)ib * Np + n : (int64_t)i * Np + ns;
-        const int64_t in_slot = P == 0 ? (int64_t)i * Np + ns : (int64_t)ib * Np + n;
-        const double fout = load_abs(L, out_slot, i);
-        double vb[3], d[3];
-        link_velocity(L, p, s, x, y, z, i, vb, d);
-        const double cv = cx(i) * vb[0] + cy(i) * vb[1] + cz(i) * vb[2];
-        const double fin = fout - 6.0 * wgt(i) * L.rho0 * cv;
-        store_abs(L, in_slot, ib, fin);
-        const double sf = fout + fin;
-        const double dF[3] = {cx(i) * sf, cy(i) * sf, cz(i) * sf};
-        double dT[3];
-        cross3(d, dF, dT);
-        const double tr = (d[0] * dF[0] + d[1] * dF[1] + d[2] * dF[2]) / 3.0;
-        acc[0] += dF[0];
-        acc[1] += dF[1];
-        acc[2] += dF[2];
-        acc[3] += dT[0];
-        acc[4] += dT[1];
-        acc[5] += dT[2];
-        acc[6] -= d[0] * dF[0] - tr;
-        acc[7] -= d[1] * dF[1] - tr;
-        acc[8] -= d[2] * dF[2] - tr;
-        acc[9] -= 0.5 * (d[0] * dF[1] + d[1] * dF[0]);
-        acc[10] -= 0.5 * (d[0] * dF[2] + d[2] * dF[0]);
-        acc[11] -= 0.5 * (d[1] * dF[2] + d[2] * dF[1]);
-    }
-    block_sum<12>(acc);
-    double* part = B.part_links + ((size_t)k * B.G_links + blockIdx.x) * 12;
-    if (threadIdx.x == 0)
-        for (int c = 0; c < 12; ++c) part[c] = acc[c];
-    if (!last_block(&A.counter_links, G)) return;
-
-    // ---- final fixed-order sum of the partials
-    double tot[12];
-    ordered_partial_sum<12>(B.part_links + (size_t)k * B.G_links * 12, G, tot);
-    if (threadIdx.x != 0) return;
     for (int a = 0; a < 3; ++a) {
         A.Fbb[a] = tot[a];
         A.Tbb[a] = tot[3 + a];
     }
     for (int a = 0; a < 6; ++a) A.Sbb[a] = tot[6 + a];
-
-    // ---- symplectic Euler (velocity first, dt = 1)
     BodyState so = s;
     for (int a = 0; a < 3; ++a) {
         A.Fapp[a] = A.Fbb[a] + A.Fc[a];
@@ -295,32 +277,31 @@ __global__ void __launch_bounds__(kBlock) k_links(const Lattice L, const Bodies 
     }
     int reclass = 0;
     if (p.kind == BODY_SPHERE && p.mobile) {
+        const int n3[3] = {L.nx, L.ny, L.nz};
         double Fw[3] = {0.0, 0.0, 0.0};
-        if (B.wca_eps != 0.0) {
-            const int n3[3] = {L.nx, L.ny, L.nz};
-            for (int j = 0; j < B.n; ++j) {
+        if (L.wca_eps != 0.0) {
+            for (int j = L.body_begin; j < L.body_begin + L.body_count; ++j) {
                 if (j == k) continue;
                 const BodyParams& q = B.par[j];
                 const BodyState& t = B.state[P][j];
                 if (q.kind == BODY_SPHERE) {
                     double dd[3];
                     for (int a = 0; a < 3; ++a) dd[a] = min_image(s.pos[a] - t.pos[a], n3[a]);
-                    double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-                    double f = wca_force(dist - p.R - q.R, B.wca_sigma, B.wca_eps);
+                    const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+                    const double f = wca_force(dist - p.R - q.R, L.wca_sigma, L.wca_eps);
                     if (f != 0.0)
                         for (int a = 0; a < 3; ++a) Fw[a] += f * dd[a] / dist;
                 } else {
                     const int ax = q.wall_axis;
-                    double dd = min_image(s.pos[ax] - (double)q.wall_index, n3[ax]);
-                    double f = wca_force(fabs(dd) - 0.5 - p.R, B.wca_sigma, B.wca_eps);
+                    const double dd = min_image(s.pos[ax] - (double)q.wall_index, n3[ax]);
+                    const double f = wca_force(fabs(dd) - 0.5 - p.R, L.wca_sigma, L.wca_eps);
                     if (f != 0.0) Fw[ax] += dd > 0.0 ? f : -f;
                 }
             }
         }
-        const int n3[3] = {L.nx, L.ny, L.nz};
         for (int a = 0; a < 3; ++a) {
-            so.vel[a] = s.vel[a] + (A.Fapp[a] + Fw[a]) / p.mass;
-            so.omega[a] = s.omega[a] + A.Tapp[a] / p.inertia;
+            so.vel[a] = s.vel[a] + (A.Fapp[a] + Fw[a]) * p.inv_mass;
+            so.omega[a] = s.omega[a] + A.Tapp[a] * p.inv_inertia;
         }
         for (int a = 0; a < 3; ++a) {
             double q = s.pos[a] + so.vel[a];
@@ -329,16 +310,16 @@ __global__ void __launch_bounds__(kBlock) k_links(const Lattice L, const Bodies 
             so.pos[a] = q;
         }
         rotate_e(so.e, so.omega);
-        double sp = so.vel[0] * so.vel[0] + so.vel[1] * so.vel[1] + so.vel[2] * so.vel[2];
-        if (!(sp < 0.25)) set_error(B.err, 5);
+        const double sp = so.vel[0] * so.vel[0] + so.vel[1] * so.vel[1] + so.vel[2] * so.vel[2];
+        if (!(sp < 0.25)) set_error(L.err, 5);
         // Node crossing test: every node of the box kept its side of the surface
         // if the centre moved less than the distance of the nearest node to the
         // surface at the last classification (less a 1e-9 guard, far above the
         // FP64 error of the inside test).
         double dd[3];
         for (int a = 0; a < 3; ++a) dd[a] = min_image(so.pos[a] - A.r_class[a], n3[a]);
-        double disp = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-        double margin = __longlong_as_double((long long)A.margin_bits);
+        const double disp = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        const double margin = __longlong_as_double((long long)A.margin_bits);
         reclass = !(disp < margin - 1e-9);
         if (reclass) A.margin_bits = (unsigned long long)__double_as_longlong(DBL_MAX);
     }
@@ -346,304 +327,544 @@ __global__ void __launch_bounds__(kBlock) k_links(const Lattice L, const Bodies 
     B.state[1 - P][k] = so;
 }
 
-// Box-partition helper: block g of G covers box cells [b0, b1).
-__device__ __forceinline__ void box_range(long long total, int g, int G, long long& b0, long long& b1) {
-    long long chunk = (total + G - 1) / G;
-    b0 = (long long)g * chunk;
-    b1 = b0 + chunk < total ? b0 + chunk : total;
-}
+// ---------------------------------------------------------------- k_links
 
-template <int P>
-__global__ void __launch_bounds__(kBlock) k_classify(const Lattice L, const Bodies B, int32_t* own,
-                                                       const int32_t* own_prev) {
-    const int k = blockIdx.y;
-    BodyAcc& A = B.acc[k];
-    const BodyParams& p = B.par[k];
-    const BodyState& s = B.state[1 - P][k];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        // a body must rebuild its links when its own cells or those of an
-        // intersecting box changed
-        int rl = A.reclass;
-        if (!rl) {
-            int lo[3], w[3];
-            body_box(L, p, s, lo, w);
-            const int n3[3] = {L.nx, L.ny, L.nz};
-            for (int j = 0; j < B.n && !rl; ++j) {
-                if (!B.acc[j].reclass) continue;
-                int loj[3], wj[3];
-                body_box(L, B.par[j], B.state[1 - P][j], loj, wj);
-                rl = axis_overlap(lo[0], w[0], loj[0], wj[0], n3[0]) && axis_overlap(lo[1], w[1], loj[1], wj[1], n3[1]) &&
-                     axis_overlap(lo[2], w[2], loj[2], wj[2], n3[2]);
-            }
-        }
-        A.relink = rl;
-    }
-    if (!A.reclass || (int)blockIdx.x >= p.g_box) return;
-    int lo[3], w[3];
-    body_box(L, p, s, lo, w);
-    if (blockIdx.x == 0 && threadIdx.x == 0)
+// One block's share of one body's links.  FP64 storage: every quantity in
+// FP64 (parity with the FP64 reference to roundoff).  Reduced storages: the
+// wall velocity and the reflected deviation in FP32 (the stored populations
+// carry FP32 or coarser precision anyway), the momentum exchange accumulated
+// in FP64 from per-thread FP32 terms.  For spheres the rest part 2 w_i rho0 of
+// each exchanged pair is dropped from the sums: over the links of a closed
+// solid it adds exactly zero to the force, the torque and the stresslet (each
+// solid-solid neighbour pair cancels).  Walls keep it (a wall's force
+// includes the rest pressure) and have no torque or stresslet.
+template <int P, bool DP>
+__device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p, const BodyState& s, long long cnt,
+                                           const uint32_t* links, int g, int G, double (&acc)[12]) {
+    const int64_t Np = L.Np;
+    const bool sphere = p.kind == BODY_SPHERE;
+    // body position split into integer and fraction, so that FP32 link
+    // offsets keep full precision far from the origin
+    int ip[3];
+    float fp[3], e32[3], v32[3], w32[3];
+    if (!DP) {
         for (int a = 0; a < 3; ++a) {
-            A.box_lo[a] = lo[a];
-            A.r_class[a] = s.pos[a];
+            ip[a] = (int)floor(s.pos[a]);
+            fp[a] = (float)(s.pos[a] - (double)ip[a]);
+            e32[a] = (float)s.e[a];
+            v32[a] = (float)s.vel[a];
+            w32[a] = (float)s.omega[a];
         }
-    const int id = k + 1;
-    long long b0, b1;
-    box_range((long long)w[0] * w[1] * w[2], blockIdx.x, p.g_box, b0, b1);
-    double mloc = DBL_MAX;
-    for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
-        const int bx = (int)(b % w[0]), by = (int)((b / w[0]) % w[1]), bz = (int)(b / ((long long)w[0] * w[1]));
-        const int x = wrapi(lo[0] + bx, L.nx), y = wrapi(lo[1] + by, L.ny), z = wrapi(lo[2] + bz, L.nz);
-        const int64_t n = cell_index(L, x, y, z);
-        const double dx = min_image((double)x - s.pos[0], L.nx);
-        const double dy = min_image((double)y - s.pos[1], L.ny);
-        const double dz = min_image((double)z - s.pos[2], L.nz);
-        const bool in = inside_sphere(dx, dy, dz, p.R);
-        const int old = own_prev[n];
-        if (in) {
-            if (old == 0) {
-                int r = atomicCAS(&own[n], 0, id);
-                if (r != 0 && r != id) set_error(B.err, 4);
-            } else if (old != id) {
-                set_error(B.err, 4);
-            }
-        } else if (old == id) {
-            own[n] = 0;
-        }
-        // distance of the node to the surface, as a lower bound: FP32 square
-        // root (relative error < 1e-6 on values below 1e3) minus 1e-4
-        const float dist = sqrtf((float)(dx * dx + dy * dy + dz * dz));
-        mloc = fmin(mloc, (double)fmaxf(fabsf(dist - (float)p.R) - 1e-4f, 0.0f));
     }
-    mloc = block_min(mloc);
-    if (threadIdx.x == 0) atomicMin(&A.margin_bits, (unsigned long long)__double_as_longlong(mloc));
-}
-
-template <int P>
-__global__ void __launch_bounds__(kBlock) k_convert(const Lattice L, const Bodies B, const int32_t* own,
-                                                      const int32_t* own_prev) {
-    const int k = blockIdx.y;
-    BodyAcc& A = B.acc[k];
-    const BodyParams& p = B.par[k];
-    const int G = p.g_box;
-    if (!A.relink || (int)blockIdx.x >= G) return;
-    const BodyState& s = B.state[1 - P][k];
-    const int q = 1 - P;  // parity of the next sweep
-    const int id = k + 1;
-    const bool conv = A.reclass != 0;
-    int lo[3], w[3];
-    body_box(L, p, s, lo, w);
-    long long b0, b1;
-    box_range((long long)w[0] * w[1] * w[2], blockIdx.x, G, b0, b1);
-    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    long long lcount = 0;
-    for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
-        const int bx = (int)(b % w[0]), by = (int)((b / w[0]) % w[1]), bz = (int)(b / ((long long)w[0] * w[1]));
-        const int x = wrapi(lo[0] + bx, L.nx), y = wrapi(lo[1] + by, L.ny), z = wrapi(lo[2] + bz, L.nz);
-        const int64_t n = cell_index(L, x, y, z);
-        const int now = own[n];
-        if (conv) {
-            const int was = own_prev[n];
-            if ((was == 0 && now == id) || (was == id && now == 0)) {
-                double d[3] = {min_image((double)x - s.pos[0], L.nx), min_image((double)y - s.pos[1], L.ny),
-                               min_image((double)z - s.pos[2], L.nz)};
-                double m[3] = {0.0, 0.0, 0.0};
-                double sign;
-                if (now == id) {
-                    // fluid -> solid: the destroyed momentum goes to the body
-                    for (int i = 0; i < Q; ++i) {
-                        double fi = load_abs(L, read_slot(L, i, x, y, z, q), i);
-                        m[0] += fi * cx(i);
-                        m[1] += fi * cy(i);
-                        m[2] += fi * cz(i);
-                    }
-                    sign = 1.0;
-                } else {
-                    // solid -> fluid: refill with the equilibrium of the mean density of
-                    // the neighbours fluid now and before, moving with the body
-                    double sum = 0.0;
-                    int cnt = 0;
-                    for (int i = 1; i < Q; ++i) {
-                        const int xn = wrapi(x + cx(i), L.nx), yn = wrapi(y + cy(i), L.ny), zn = wrapi(z + cz(i), L.nz);
-                        const int64_t nn = cell_index(L, xn, yn, zn);
-                        if (own[nn] == 0 && own_prev[nn] == 0) {
-                            double r = 0.0;
-                            for (int j = 0; j < Q; ++j) r += load_abs(L, read_slot(L, j, xn, yn, zn, q), j);
-                            sum += r;
-                            cnt++;
-                        }
-                    }
-                    const double rb = cnt > 0 ? sum / (double)cnt : L.rho0;
-                    double wd[3];
-                    cross3(s.omega, d, wd);
-                    const double u[3] = {s.vel[0] + wd[0], s.vel[1] + wd[1], s.vel[2] + wd[2]};
-                    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-                    for (int i = 0; i < Q; ++i) {
-                        const double cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
-                        const double fi = wgt(i) * rb * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-                        store_abs(L, read_slot(L, i, x, y, z, q), i, fi);
-                        m[0] += fi * cx(i);
-                        m[1] += fi * cy(i);
-                        m[2] += fi * cz(i);
-                    }
-                    sign = -1.0;
+    const float B1f = (float)p.B1, B2f = (float)p.B2, shf = (float)(6.0 * L.rho0);
+    for (long long l = (long long)g * blockDim.x + threadIdx.x; l < cnt; l += (long long)G * blockDim.x) {
+        const uint32_t code = links[l];
+        const int64_t n = code >> 5;
+        const int i = code & 31, ib = opp(i);
+        const int ci[3] = {cx(i), cy(i), cz(i)};
+        int x, y, z;
+        cell_coords(L, n, x, y, z);
+        const int64_t ns =
+            cell_index(L, step_wrap(x, ci[0], L.nx), step_wrap(y, ci[1], L.ny), step_wrap(z, ci[2], L.nz));
+        // where sweep P left f*_i of the fluid node, and where the next sweep
+        // reads the reflected population f_ib of the fluid node
+        const int64_t out_slot = P == 0 ? (int64_t)ib * Np + n : (int64_t)i * Np + ns;
+        const int64_t in_slot = P == 0 ? (int64_t)i * Np + ns : (int64_t)ib * Np + n;
+        if (DP || !sphere) {
+            const double fout = load_abs(L, out_slot, i);
+            double vb[3], d[3];
+            if (sphere) {
+                // link midpoint relative to the centre; rigid motion + slip there
+                d[0] = min_image(((double)x + 0.5 * ci[0]) - s.pos[0], L.nx);
+                d[1] = min_image(((double)y + 0.5 * ci[1]) - s.pos[1], L.ny);
+                d[2] = min_image(((double)z + 0.5 * ci[2]) - s.pos[2], L.nz);
+                const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                double sl[3] = {0.0, 0.0, 0.0};
+                if (r2 > 0.0) {
+                    const double ir = 1.0 / sqrt(r2);
+                    const double n0 = d[0] * ir, n1 = d[1] * ir, n2 = d[2] * ir;
+                    const double ct = s.e[0] * n0 + s.e[1] * n1 + s.e[2] * n2;
+                    const double a = p.B1 + p.B2 * ct;
+                    sl[0] = a * (ct * n0 - s.e[0]);
+                    sl[1] = a * (ct * n1 - s.e[1]);
+                    sl[2] = a * (ct * n2 - s.e[2]);
                 }
-                double t[3];
-                cross3(d, m, t);
-                for (int a = 0; a < 3; ++a) {
-                    acc[a] += sign * m[a];
-                    acc[3 + a] += sign * t[a];
-                }
+                double w[3];
+                cross3(s.omega, d, w);
+                for (int a = 0; a < 3; ++a) vb[a] = s.vel[a] + w[a] + sl[a];
+            } else {
+                for (int a = 0; a < 3; ++a) vb[a] = p.wall_vel[a];
             }
-        }
-        if (now == 0) {
-            for (int i = 1; i < Q; ++i) {
-                const int64_t nn =
-                    cell_index(L, wrapi(x + cx(i), L.nx), wrapi(y + cy(i), L.ny), wrapi(z + cz(i), L.nz));
-                lcount += own[nn] == id;
+            const double cv = csel(ci[0], vb[0]) + csel(ci[1], vb[1]) + csel(ci[2], vb[2]);
+            const double fin = fout - 6.0 * L.rho0 * wgt(i) * cv;
+            store_abs(L, in_slot, ib, fin);
+            // momentum given to the body, c_i (f_out + f_in); torque, stresslet
+            const double sf = fout + fin;
+            const double dF[3] = {csel(ci[0], sf), csel(ci[1], sf), csel(ci[2], sf)};
+            acc[0] += dF[0];
+            acc[1] += dF[1];
+            acc[2] += dF[2];
+            if (sphere) {
+                acc[3] += d[1] * dF[2] - d[2] * dF[1];
+                acc[4] += d[2] * dF[0] - d[0] * dF[2];
+                acc[5] += d[0] * dF[1] - d[1] * dF[0];
+                const double tr = (d[0] * dF[0] + d[1] * dF[1] + d[2] * dF[2]) * (1.0 / 3.0);
+                acc[6] -= d[0] * dF[0] - tr;
+                acc[7] -= d[1] * dF[1] - tr;
+                acc[8] -= d[2] * dF[2] - tr;
+                acc[9] -= 0.5 * (d[0] * dF[1] + d[1] * dF[0]);
+                acc[10] -= 0.5 * (d[0] * dF[2] + d[2] * dF[0]);
+                acc[11] -= 0.5 * (d[1] * dF[2] + d[2] * dF[1]);
             }
+        } else {
+            // FP32 path (reduced storage, sphere): deviations g = f - w rho0
+            const float gout = load_dev(L, out_slot);
+            float d[3];
+            const int xi[3] = {x, y, z};
+            const int n3[3] = {L.nx, L.ny, L.nz};
+            for (int a = 0; a < 3; ++a) {
+                float t = (float)(xi[a] - ip[a]) + (0.5f * (float)ci[a] - fp[a]);
+                const float h = 0.5f * (float)n3[a];
+                if (t > h) t -= (float)n3[a];
+                else if (t <= -h) t += (float)n3[a];
+                d[a] = t;
+            }
+            const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            float sl[3] = {0.0f, 0.0f, 0.0f};
+            if (r2 > 0.0f) {
+                const float ir = rsqrtf(r2);
+                const float n0 = d[0] * ir, n1 = d[1] * ir, n2 = d[2] * ir;
+                const float ct = e32[0] * n0 + e32[1] * n1 + e32[2] * n2;
+                const float a = B1f + B2f * ct;
+                sl[0] = a * (ct * n0 - e32[0]);
+                sl[1] = a * (ct * n1 - e32[1]);
+                sl[2] = a * (ct * n2 - e32[2]);
+            }
+            const float vb0 = v32[0] + (w32[1] * d[2] - w32[2] * d[1]) + sl[0];
+            const float vb1 = v32[1] + (w32[2] * d[0] - w32[0] * d[2]) + sl[1];
+            const float vb2 = v32[2] + (w32[0] * d[1] - w32[1] * d[0]) + sl[2];
+            const float cv = (ci[0] > 0 ? vb0 : (ci[0] < 0 ? -vb0 : 0.0f)) +
+                             (ci[1] > 0 ? vb1 : (ci[1] < 0 ? -vb1 : 0.0f)) +
+                             (ci[2] > 0 ? vb2 : (ci[2] < 0 ? -vb2 : 0.0f));
+            const float gin = gout - shf * (float)wgt(i) * cv;
+            store_dev(L, in_slot, gin);
+            const float sf = gout + gin;
+            const float dF[3] = {ci[0] > 0 ? sf : (ci[0] < 0 ? -sf : 0.0f), ci[1] > 0 ? sf : (ci[1] < 0 ? -sf : 0.0f),
+                                 ci[2] > 0 ? sf : (ci[2] < 0 ? -sf : 0.0f)};
+            const float tr = (d[0] * dF[0] + d[1] * dF[1] + d[2] * dF[2]) * (1.0f / 3.0f);
+            const float t12[12] = {dF[0],
+                                   dF[1],
+                                   dF[2],
+                                   d[1] * dF[2] - d[2] * dF[1],
+                                   d[2] * dF[0] - d[0] * dF[2],
+                                   d[0] * dF[1] - d[1] * dF[0],
+                                   -(d[0] * dF[0] - tr),
+                                   -(d[1] * dF[1] - tr),
+                                   -(d[2] * dF[2] - tr),
+                                   -0.5f * (d[0] * dF[1] + d[1] * dF[0]),
+                                   -0.5f * (d[0] * dF[2] + d[2] * dF[0]),
+                                   -0.5f * (d[1] * dF[2] + d[2] * dF[1])};
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[c] += (double)t12[c];
         }
-    }
-    block_sum<6>(acc);
-    lcount = block_sum_ll(lcount);
-    if (threadIdx.x == 0) {
-        double* part = B.part_conv + ((size_t)k * B.G_box + blockIdx.x) * 6;
-        for (int c = 0; c < 6; ++c) part[c] = acc[c];
-        B.part_count[(size_t)k * B.G_box + blockIdx.x] = (int)lcount;
-    }
-    if (!last_block(&A.counter_conv, G) || !conv) return;
-    double tot[6];
-    ordered_partial_sum<6>(B.part_conv + (size_t)k * B.G_box * 6, G, tot);
-    if (threadIdx.x != 0) return;
-    for (int a = 0; a < 3; ++a) {
-        A.Fc[a] += tot[a];
-        A.Tc[a] += tot[3 + a];
     }
 }
 
 template <int P>
-__global__ void __launch_bounds__(kBlock) k_rebuild(const Lattice L, const Bodies B, const int32_t* own,
-                                                      int32_t* own_prev) {
-    const int k = blockIdx.y;
-    BodyAcc& A = B.acc[k];
-    const BodyParams& p = B.par[k];
-    const int G = p.g_box;
-    if (!A.relink || (int)blockIdx.x >= G) return;
-    const BodyState& s = B.state[1 - P][k];
-    const int id = k + 1;
-    int lo[3], w[3];
-    body_box(L, p, s, lo, w);
-    // offset of this block's links: the counts of the blocks before it
-    __shared__ long long s_base, s_total;
-    {
-        const int* pc = B.part_count + (size_t)k * B.G_box;
-        long long before = 0, all = 0;
-        for (int g = threadIdx.x; g < G; g += blockDim.x) {
-            const long long v = __ldcg(pc + g);
-            all += v;
-            if (g < (int)blockIdx.x) before += v;
-        }
-        before = block_sum_ll(before);
-        all = block_sum_ll(all);
+__global__ void __launch_bounds__(kLB) k_links(const Bodies B) {
+    __shared__ double sm[12 * kLB + 12 * 8];
+    __shared__ double s_tot[12];
+    __shared__ int s_flag;
+    const int nitems = *B.n_link_items;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 item = B.link_items[it];
+        const int k = item.x, g = item.y;
+        const BodyParams& p = B.par[k];
+        const Lattice& L = B.lats[p.lat];
+        if (!L.active) continue;
+        const int G = p.g_links;
+        BodyAcc& A = B.acc[k];
+        double acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = 0.0;
+        if (L.storage == ST_F64)
+            link_terms<P, true>(L, p, B.state[P][k], A.link_count, B.links + p.link_off, g, G, acc);
+        else
+            link_terms<P, false>(L, p, B.state[P][k], A.link_count, B.links + p.link_off, g, G, acc);
+        block_sum_fixed<12, kLB>(acc, sm, s_tot);
+        double* part = B.part_links + ((size_t)k * B.GL + g) * 12;
+        if (threadIdx.x < 12) part[threadIdx.x] = s_tot[threadIdx.x];
+        if (!last_block(&A.counter_links, G, &s_flag)) continue;
+        ordered_partial_sum<12>(B.part_links + (size_t)k * B.GL * 12, G, sm, s_tot);
         if (threadIdx.x == 0) {
-            s_base = before;
-            s_total = all;
-            if (blockIdx.x == 0) {
-                if (all > p.link_cap) set_error(B.err, 8);
-                A.link_count = all < p.link_cap ? all : p.link_cap;
+            update_body<P>(L, B, k, s_tot);
+            s_flag = A.reclass;
+        }
+        __syncthreads();
+        if (s_flag) append_items(B.box_items, B.n_box, B.box_cap, k, p.g_box, B.err, (int*)sm);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- k_classify
+
+template <int P>
+__global__ void __launch_bounds__(kBB) k_classify(const Bodies B) {
+    __shared__ double smd[kBB / 32];
+    __shared__ int s_base, s_scan[kBB / 32 + 1];
+    const int nitems = *B.n_box;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 item = B.box_items[it];
+        const int k = item.x, g = item.y;
+        const BodyParams& p = B.par[k];
+        const Lattice& L = B.lats[p.lat];
+        BodyAcc& A = B.acc[k];
+        const BodyState& s = B.state[1 - P][k];
+        if (g == 0) {
+            // queue every body of this lattice whose links the change can touch:
+            // this body and every body whose scan box meets this body's box
+            // (one thread per candidate body, in rounds of the block size)
+            for (int j0 = L.body_begin; j0 < L.body_begin + L.body_count; j0 += kBB) {
+                const int j = j0 + threadIdx.x;
+                int take = 0, nb = 0;
+                if (j < L.body_begin + L.body_count &&
+                    (j == k || boxes_intersect(L, p, s, B.par[j], B.state[1 - P][j]))) {
+                    take = atomicExch(&B.acc[j].rel_flag, 1) == 0;
+                    nb = take ? B.par[j].g_box : 0;
+                }
+                int total;
+                const int off = block_scan<kBB>(nb, &total, s_scan);
+                if (threadIdx.x == 0 && total > 0) s_base = atomicAdd(B.n_rel, total);
+                __syncthreads();
+                if (take) {
+                    if (s_base + off + nb > B.rel_cap) set_error(B.err, 8);
+                    else
+                        for (int gg = 0; gg < nb; ++gg) B.rel_items[s_base + off + gg] = make_int2(j, gg);
+                }
+                __syncthreads();
             }
+        }
+        int lo[3], w[3];
+        body_box(L, p, s, lo, w);
+        if (g == 0 && threadIdx.x == 0)
+            for (int a = 0; a < 3; ++a) {
+                A.box_lo[a] = lo[a];
+                A.r_class[a] = s.pos[a];
+            }
+        const int id = k + 1;
+        long long b0, b1;
+        box_range((long long)w[0] * w[1] * w[2], g, p.g_box, b0, b1);
+        float mloc = FLT_MAX;
+        for (long long b = b0 + threadIdx.x; b < b1; b += kBB) {
+            int x, y, z;
+            box_cell(L, lo, w, b, x, y, z);
+            const int64_t n = cell_index(L, x, y, z);
+            const double dx = min_image((double)x - s.pos[0], L.nx);
+            const double dy = min_image((double)y - s.pos[1], L.ny);
+            const double dz = min_image((double)z - s.pos[2], L.nz);
+            const bool in = inside_sphere(dx, dy, dz, p.R);
+            const int old = L.own_prev[n];
+            if (in) {
+                if (old == 0) {
+                    const int r = atomicCAS(&L.own[n], 0, id);
+                    if (r != 0 && r != id) set_error(L.err, 4);
+                } else if (old != id) {
+                    set_error(L.err, 4);
+                }
+            } else if (old == id) {
+                L.own[n] = 0;
+            }
+            // distance of the node to the surface, as a lower bound: FP32 square
+            // root (relative error < 1e-6 on values below 1e3) minus 1e-4
+            const float dist = sqrtf((float)(dx * dx + dy * dy + dz * dz));
+            mloc = fminf(mloc, fmaxf(fabsf(dist - (float)p.R) - 1e-4f, 0.0f));
+        }
+        // block minimum (FP32 values, exact)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mloc = fminf(mloc, __shfl_down_sync(0xffffffffu, mloc, o));
+        if ((threadIdx.x & 31) == 0) smd[threadIdx.x >> 5] = (double)mloc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = DBL_MAX;
+            for (int q = 0; q < kBB / 32; ++q) m = fmin(m, smd[q]);
+            atomicMin(&A.margin_bits, (unsigned long long)__double_as_longlong(m));
         }
         __syncthreads();
     }
-    long long base = s_base;
-    uint32_t* links = B.links + p.link_off;
-    long long b0, b1;
-    box_range((long long)w[0] * w[1] * w[2], blockIdx.x, G, b0, b1);
-    for (long long r0 = b0; r0 < b1; r0 += blockDim.x) {
-        const long long b = r0 + threadIdx.x;
-        uint32_t mask = 0;
-        int64_t n = 0;
-        if (b < b1) {
-            const int bx = (int)(b % w[0]), by = (int)((b / w[0]) % w[1]), bz = (int)(b / ((long long)w[0] * w[1]));
-            const int x = wrapi(lo[0] + bx, L.nx), y = wrapi(lo[1] + by, L.ny), z = wrapi(lo[2] + bz, L.nz);
-            n = cell_index(L, x, y, z);
-            if (own[n] == 0) {
-                for (int i = 1; i < Q; ++i) {
-                    const int64_t nn =
-                        cell_index(L, wrapi(x + cx(i), L.nx), wrapi(y + cy(i), L.ny), wrapi(z + cz(i), L.nz));
-                    if (own[nn] == id) mask |= 1u << i;
+}
+
+// ---------------------------------------------------------------- k_convert
+
+// Refill of one uncovered cell by one warp: lane l = 1..18 reads the density of
+// neighbour l (if fluid now and before), the neighbour densities are summed in
+// lane order; lanes 0..18 write the equilibrium of population l.  The created
+// momentum (taken from the body) is added to acc of lane 0.
+__device__ __forceinline__ void refill_cell(const Lattice& L, const BodyState& s, int x, int y, int z, int q,
+                                            double* acc) {
+    const int lane = threadIdx.x & 31;
+    double r = 0.0;
+    int valid = 0;
+    if (lane >= 1 && lane < Q) {
+        const int xn = step_wrap(x, cx(lane), L.nx), yn = step_wrap(y, cy(lane), L.ny),
+                  zn = step_wrap(z, cz(lane), L.nz);
+        const int64_t nn = cell_index(L, xn, yn, zn);
+        if (L.own[nn] == 0 && L.own_prev[nn] == 0) {
+            valid = 1;
+            for (int j = 0; j < Q; ++j) r += load_abs(L, read_slot(L, j, xn, yn, zn, q), j);
+        }
+    }
+    double sum = 0.0;
+    int cnt = 0;
+    for (int l = 1; l < Q; ++l) {
+        const double rl = __shfl_sync(0xffffffffu, r, l);
+        const int vl = __shfl_sync(0xffffffffu, valid, l);
+        if (vl) {
+            sum += rl;
+            cnt++;
+        }
+    }
+    const double rb = cnt > 0 ? sum / (double)cnt : L.rho0;
+    const double d[3] = {min_image((double)x - s.pos[0], L.nx), min_image((double)y - s.pos[1], L.ny),
+                         min_image((double)z - s.pos[2], L.nz)};
+    double wd[3];
+    cross3(s.omega, d, wd);
+    const double u[3] = {s.vel[0] + wd[0], s.vel[1] + wd[1], s.vel[2] + wd[2]};
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double fi = 0.0;
+    if (lane < Q) {
+        const double cu = cx(lane) * u[0] + cy(lane) * u[1] + cz(lane) * u[2];
+        fi = wgt(lane) * rb * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        store_abs(L, read_slot(L, lane, x, y, z, q), lane, fi);
+    }
+    double m[3] = {0.0, 0.0, 0.0};
+    for (int l = 0; l < Q; ++l) {
+        const double fl = __shfl_sync(0xffffffffu, fi, l);
+        m[0] += fl * cx(l);
+        m[1] += fl * cy(l);
+        m[2] += fl * cz(l);
+    }
+    if (lane == 0) {
+        double t[3];
+        cross3(d, m, t);
+        for (int a = 0; a < 3; ++a) {
+            acc[a] -= m[a];
+            acc[3 + a] -= t[a];
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kBB) k_convert(const Bodies B) {
+    __shared__ double sm[6 * kBB + 6 * 8];
+    __shared__ double s_tot[6];
+    __shared__ long long sml[kBB];
+    __shared__ int s_list[kBB], s_scan[kBB / 32 + 1], s_flag;
+    const int nitems = *B.n_rel;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 item = B.rel_items[it];
+        const int k = item.x, g = item.y;
+        const BodyParams& p = B.par[k];
+        const Lattice& L = B.lats[p.lat];
+        BodyAcc& A = B.acc[k];
+        const int G = p.g_box;
+        const BodyState& s = B.state[1 - P][k];
+        const int q = 1 - P;  // parity of the next sweep
+        const int id = k + 1;
+        const bool conv = A.reclass != 0;
+        int lo[3], w[3];
+        body_box(L, p, s, lo, w);
+        long long b0, b1;
+        box_range((long long)w[0] * w[1] * w[2], g, G, b0, b1);
+        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        long long lcount = 0;
+        for (long long r0 = b0; r0 < b1; r0 += kBB) {
+            const long long b = r0 + threadIdx.x;
+            int uncover = 0, x = 0, y = 0, z = 0;
+            if (b < b1) {
+                box_cell(L, lo, w, b, x, y, z);
+                const int64_t n = cell_index(L, x, y, z);
+                const int now = L.own[n];
+                if (conv) {
+                    const int was = L.own_prev[n];
+                    if (was == 0 && now == id) {
+                        // fluid -> solid: the destroyed momentum goes to the body
+                        double m[3] = {0.0, 0.0, 0.0};
+                        for (int i = 0; i < Q; ++i) {
+                            const double fi = load_abs(L, read_slot(L, i, x, y, z, q), i);
+                            m[0] += fi * cx(i);
+                            m[1] += fi * cy(i);
+                            m[2] += fi * cz(i);
+                        }
+                        const double d[3] = {min_image((double)x - s.pos[0], L.nx),
+                                             min_image((double)y - s.pos[1], L.ny),
+                                             min_image((double)z - s.pos[2], L.nz)};
+                        double t[3];
+                        cross3(d, m, t);
+                        for (int a = 0; a < 3; ++a) {
+                            acc[a] += m[a];
+                            acc[3 + a] += t[a];
+                        }
+                    } else if (was == id && now == 0) {
+                        uncover = 1;
+                    }
+                }
+                if (now == 0)
+                    for (int i = 1; i < Q; ++i) {
+                        const int64_t nn = cell_index(L, step_wrap(x, cx(i), L.nx), step_wrap(y, cy(i), L.ny),
+                                                      step_wrap(z, cz(i), L.nz));
+                        lcount += L.own[nn] == id;
+                    }
+            }
+            // solid -> fluid cells of this round, in thread order, refilled by warps
+            int nu;
+            const int pos = block_scan<kBB>(uncover, &nu, s_scan);
+            if (uncover) s_list[pos] = (int)(b - b0);
+            __syncthreads();
+            for (int u = threadIdx.x >> 5; u < nu; u += kBB / 32) {
+                int ux, uy, uz;
+                box_cell(L, lo, w, b0 + s_list[u], ux, uy, uz);
+                refill_cell(L, s, ux, uy, uz, q, acc);
+            }
+            __syncthreads();
+        }
+        block_sum_fixed<6, kBB>(acc, sm, s_tot);
+        lcount = block_sum_ll<kBB>(lcount, sml);
+        if (threadIdx.x < 6) B.part_conv[((size_t)k * B.GB + g) * 6 + threadIdx.x] = s_tot[threadIdx.x];
+        if (threadIdx.x == 0) B.part_count[(size_t)k * B.GB + g] = (int)lcount;
+        if (!last_block(&A.counter_conv, G, &s_flag)) continue;
+        if (!conv) continue;
+        ordered_partial_sum<6>(B.part_conv + (size_t)k * B.GB * 6, G, sm, s_tot);
+        if (threadIdx.x < 3) {
+            A.Fc[threadIdx.x] += s_tot[threadIdx.x];
+            A.Tc[threadIdx.x] += s_tot[3 + threadIdx.x];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- k_rebuild
+
+template <int P>
+__global__ void __launch_bounds__(kBB) k_rebuild(const Bodies B) {
+    __shared__ long long sml[kBB];
+    __shared__ int s_scan[kBB / 32 + 1], s_flag;
+    __shared__ long long s_base;
+    const int nitems = *B.n_rel;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 item = B.rel_items[it];
+        const int k = item.x, g = item.y;
+        const BodyParams& p = B.par[k];
+        const Lattice& L = B.lats[p.lat];
+        BodyAcc& A = B.acc[k];
+        const int G = p.g_box;
+        const BodyState& s = B.state[1 - P][k];
+        const int id = k + 1;
+        int lo[3], w[3];
+        body_box(L, p, s, lo, w);
+        // offset of this block's links: the counts of the blocks before it
+        {
+            const int* pc = B.part_count + (size_t)k * B.GB;
+            long long before = 0, all = 0;
+            for (int gg = threadIdx.x; gg < G; gg += kBB) {
+                const long long v = __ldcg(pc + gg);
+                all += v;
+                if (gg < g) before += v;
+            }
+            before = block_sum_ll<kBB>(before, sml);
+            all = block_sum_ll<kBB>(all, sml);
+            if (threadIdx.x == 0) {
+                s_base = before;
+                if (g == 0) {
+                    if (all > p.link_cap) set_error(L.err, 8);
+                    A.link_count = all < p.link_cap ? all : p.link_cap;
                 }
             }
-            if (A.reclass) own_prev[n] = own[n];
+            __syncthreads();
         }
-        int tot;
-        int off = block_scan(__popc(mask), &tot);
-        long long pos = base + off;
-        while (mask) {
-            const int i = __ffs(mask) - 1;
-            mask &= mask - 1;
-            if (pos < p.link_cap) links[pos] = (uint32_t)(n * 32 + i);
-            pos++;
+        long long base = s_base;
+        uint32_t* links = B.links + p.link_off;
+        const bool commit = A.reclass != 0;
+        long long b0, b1;
+        box_range((long long)w[0] * w[1] * w[2], g, G, b0, b1);
+        for (long long r0 = b0; r0 < b1; r0 += kBB) {
+            const long long b = r0 + threadIdx.x;
+            uint32_t mask = 0;
+            int64_t n = 0;
+            if (b < b1) {
+                int x, y, z;
+                box_cell(L, lo, w, b, x, y, z);
+                n = cell_index(L, x, y, z);
+                if (L.own[n] == 0) {
+                    for (int i = 1; i < Q; ++i) {
+                        const int64_t nn = cell_index(L, step_wrap(x, cx(i), L.nx), step_wrap(y, cy(i), L.ny),
+                                                      step_wrap(z, cz(i), L.nz));
+                        if (L.own[nn] == id) mask |= 1u << i;
+                    }
+                }
+                if (commit) L.own_prev[n] = L.own[n];
+            }
+            int tot;
+            const int off = block_scan<kBB>(__popc(mask), &tot, s_scan);
+            long long pos = base + off;
+            while (mask) {
+                const int i = __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (pos < p.link_cap) links[pos] = (uint32_t)(n * 32 + i);
+                pos++;
+            }
+            base += tot;
         }
-        base += tot;
+        if (!last_block(&A.counter_rebuild, G, &s_flag)) continue;
+        if (threadIdx.x == 0) A.rel_flag = 0;
+        __syncthreads();
     }
+    // the last block of the launch empties the step's work lists (every block
+    // has read the counts by now)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(B.done, 1) == (int)gridDim.x - 1) {
+            *B.n_box = 0;
+            *B.n_rel = 0;
+            *B.done = 0;
+        }
+    }
+}
+
+__global__ void k_tick(int* n_box, int* n_rel, long long* step) {
+    *n_box = 0;
+    *n_rel = 0;
+    if (step) *step += 1;
 }
 
 // ---------------------------------------------------------------- launchers
 
-void launch_body_step(const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
-                      cudaStream_t st) {
-    dim3 gl(B.G_links, B.n), gb(B.G_box, B.n);
-    if (parity == 0) {
-        k_links<0><<<gl, kBlock, 0, st>>>(L, B);
-        k_classify<0><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-        k_convert<0><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-        k_rebuild<0><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-    } else {
-        k_links<1><<<gl, kBlock, 0, st>>>(L, B);
-        k_classify<1><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-        k_convert<1><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-        k_rebuild<1><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-    }
-}
-
-// One body kernel of a step by kind (1 links, 2 classify, 3 convert, 4 rebuild),
-// for the traced launch path.
-void launch_body_kernel(int which, const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
+// which: 1 links, 2 classify, 3 convert, 4 rebuild, 5 tick.  The link kernel
+// gets grid_links blocks over its static item list; the box kernels walk their
+// device-built lists with grid_box blocks.
+void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, int grid_box, long long* step,
                         cudaStream_t st) {
-    dim3 gl(B.G_links, B.n), gb(B.G_box, B.n);
-    if (parity == 0) {
-        if (which == 1) k_links<0><<<gl, kBlock, 0, st>>>(L, B);
-        else if (which == 2) k_classify<0><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-        else if (which == 3) k_convert<0><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-        else k_rebuild<0><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
+    if (which == 1) {
+        if (parity == 0) k_links<0><<<grid_links, kLB, 0, st>>>(B);
+        else k_links<1><<<grid_links, kLB, 0, st>>>(B);
+    } else if (which == 2) {
+        if (parity == 0) k_classify<0><<<grid_box, kBB, 0, st>>>(B);
+        else k_classify<1><<<grid_box, kBB, 0, st>>>(B);
+    } else if (which == 3) {
+        if (parity == 0) k_convert<0><<<grid_box, kBB, 0, st>>>(B);
+        else k_convert<1><<<grid_box, kBB, 0, st>>>(B);
+    } else if (which == 4) {
+        if (parity == 0) k_rebuild<0><<<grid_box, kBB, 0, st>>>(B);
+        else k_rebuild<1><<<grid_box, kBB, 0, st>>>(B);
     } else {
-        if (which == 1) k_links<1><<<gl, kBlock, 0, st>>>(L, B);
-        else if (which == 2) k_classify<1><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-        else if (which == 3) k_convert<1><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-        else k_rebuild<1><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
+        k_tick<<<1, 1, 0, st>>>(B.n_box, B.n_rel, step);
     }
 }
 
-// Classification pass alone (used when a body is added).
-void launch_classify_only(const Lattice& L, const Bodies& B, int32_t* own, const int32_t* own_prev, int parity,
-                          cudaStream_t st) {
-    dim3 gb(B.G_box, B.n);
-    if (parity == 0) k_classify<0><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-    else k_classify<1><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-}
-
-// Rebuild the link lists of every body whose relink flag the host set, as if
-// after a step of parity `parity` (the next sweep has parity 1 - parity).
-void launch_relink(const Lattice& L, const Bodies& B, int32_t* own, int32_t* own_prev, int parity,
-                   cudaStream_t st) {
-    dim3 gb(B.G_box, B.n);
-    if (parity == 0) {
-        k_convert<0><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-        k_rebuild<0><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-    } else {
-        k_convert<1><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-        k_rebuild<1><<<gb, kBlock, 0, st>>>(L, B, own, own_prev);
-    }
+// A step's body kernels: links, classify, convert, rebuild (whose last block
+// empties the work lists).
+void launch_body_step(const Bodies& B, int parity, int grid_links, int grid_box, long long* step, cudaStream_t st) {
+    for (int which = 1; which <= 4; ++which) launch_body_kernel(which, B, parity, grid_links, grid_box, step, st);
 }
 
 }  // namespace lbsq

@@ -75,7 +75,8 @@ template <> struct StoreT<ST_BF16> {
 
 inline int storage_bytes(int s) { return s == ST_F64 ? 8 : (s == ST_F32 ? 4 : 2); }
 
-// Lattice geometry and population array, as seen by kernels.
+// One lattice as seen by kernels (an array of these lives in device memory;
+// a context has one, a server one per resident request).
 struct Lattice {
     void* F;          // populations, storage-typed
     int nx, ny, nz;
@@ -83,6 +84,14 @@ struct Lattice {
     int storage;
     double rho0;
     float scale, inv_scale;  // FP16 deviation scale (1 for other storages)
+    int32_t* own;       // cell owners, 0 = fluid
+    int32_t* own_prev;  // owners committed at the last re-classification
+    int* err;           // device error word of this lattice
+    double lambda_e, lambda_o;
+    double wca_sigma, wca_eps;
+    int body_begin, body_count;  // this lattice's bodies in the body table
+    int active;                  // 0: not stepped (a free or finished server slot)
+    int pad;
 };
 
 __device__ __forceinline__ int wrapi(int a, int n) {
@@ -130,6 +139,23 @@ __device__ __forceinline__ void store_abs(const Lattice& L, int64_t slot, int i,
     }
 }
 
+// Deviation g_i = f_i - w_i rho0 of a reduced-storage slot, in FP32 (no FP64
+// arithmetic), and its store.  Not for FP64 storage.
+__device__ __forceinline__ float load_dev(const Lattice& L, int64_t slot) {
+    switch (L.storage) {
+        case ST_F32: return ((const float*)L.F)[slot];
+        case ST_F16: return __half2float(((const __half*)L.F)[slot]) * L.inv_scale;
+        default: return __bfloat162float(((const __nv_bfloat16*)L.F)[slot]) * L.inv_scale;
+    }
+}
+__device__ __forceinline__ void store_dev(const Lattice& L, int64_t slot, float g) {
+    switch (L.storage) {
+        case ST_F32: ((float*)L.F)[slot] = g; break;
+        case ST_F16: ((__half*)L.F)[slot] = __float2half_rn(g * L.scale); break;
+        default: ((__nv_bfloat16*)L.F)[slot] = __float2bfloat16_rn(g * L.scale); break;
+    }
+}
+
 // Minimum image of a coordinate difference into (-n/2, n/2].
 __device__ __forceinline__ double min_image(double d, int n) {
     double h = 0.5 * (double)n;
@@ -159,7 +185,8 @@ struct BodyParams {
     int box_w[3];      // scan box extent (spheres: W = ceil(2R)+6 per axis)
     int g_links;       // blocks of the link kernel for this body (fixed by the body alone)
     int g_box;         // blocks of the box kernels for this body
-    int pad;
+    int lat;           // index of the body's lattice
+    double inv_mass, inv_inertia;
 };
 
 struct BodyState {  // ping-pong by step parity
@@ -173,23 +200,37 @@ struct BodyAcc {
     double r_class[3];                // centre at the last classification
     unsigned long long margin_bits;   // min | |x - r| - R | over the box at that time
     int box_lo[3];                    // scan box origin of the current classification
-    int reclass, relink;              // work flags of the current step
+    int reclass;                      // re-classify this step (set by the update)
+    int rel_flag;                     // queued for relinking this step
     long long link_count;
-    int counter_links, counter_conv;  // last-block counters (self-resetting)
+    int counter_links, counter_conv, counter_rebuild;  // last-block counters (self-resetting)
+    int pad;
 };
 
+// Body table and the work lists of a step.  An item (body, block) is one
+// block's share of a body; per-step lists are appended on the device:
+// the update appends the box items of bodies that must re-classify, the
+// classification appends the items of every body whose links must be rebuilt.
 struct Bodies {
-    int n;
+    const Lattice* lats;
     const BodyParams* par;
     BodyState* state[2];
     BodyAcc* acc;
     uint32_t* links;       // code = cell * 32 + i
-    double* part_links;    // [n][G_links][12]
-    double* part_conv;     // [n][G_box][6]
-    int* part_count;       // [n][G_box]
-    int G_links, G_box;
-    double wca_sigma, wca_eps;
-    int* err;
+    double* part_links;    // [body][GL][12]
+    double* part_conv;     // [body][GB][6]
+    int* part_count;       // [body][GB]
+    int GL, GB;            // strides of the partial arrays
+    const int2* link_items;
+    const int* n_link_items;
+    int2* box_items;
+    int* n_box;
+    int box_cap;
+    int2* rel_items;
+    int* n_rel;
+    int rel_cap;
+    int* done;             // blocks of the rebuild kernel that finished (self-resetting)
+    int* err;              // error word for list overflow (shared)
 };
 
 // Scan box of a body: origin and extent.

@@ -156,12 +156,12 @@ __global__ void k_plane_claim(const Lattice L, int32_t* own, int axis, int index
     if (c[axis] == index && own[n] == 0) own[n] = id;
 }
 
-// Work flags for set-up passes: body k (or all if k < 0).
-__global__ void k_set_flags(BodyAcc* acc, int nb, int k, int reclass, int relink) {
+// Work flag for set-up passes: body k (or all if k < 0) re-classifies (and
+// its node margin restarts) or not.
+__global__ void k_set_flags(BodyAcc* acc, int nb, int k, int reclass) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nb || (k >= 0 && j != k)) return;
     acc[j].reclass = reclass;
-    acc[j].relink = relink;
     if (reclass) acc[j].margin_bits = (unsigned long long)__double_as_longlong(DBL_MAX);
 }
 
@@ -198,8 +198,8 @@ void launch_plane_overlap(const Lattice& L, const int32_t* own, const int* kind,
 void launch_plane_claim(const Lattice& L, int32_t* own, int axis, int index, int id, cudaStream_t st) {
     k_plane_claim<<<grid_for(L.N), kB, 0, st>>>(L, own, axis, index, id);
 }
-void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, int relink, cudaStream_t st) {
-    k_set_flags<<<(nb + kB - 1) / kB, kB, 0, st>>>(acc, nb, k, reclass, relink);
+void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, cudaStream_t st) {
+    k_set_flags<<<(nb + kB - 1) / kB, kB, 0, st>>>(acc, nb, k, reclass);
 }
 
 }  // namespace lbsq

@@ -258,7 +258,7 @@ def lb_kernel_launches(ctx) -> int:
     return int(load().lb_kernel_launches(ctx))
 
 
-KERNEL_KINDS = ("sweep", "links", "classify", "convert", "rebuild")
+KERNEL_KINDS = ("sweep", "links", "classify", "convert", "rebuild", "tick")
 
 
 def lb_set_sweep_variant(ctx, variant: int):
@@ -270,8 +270,8 @@ def lb_profile_begin(ctx):
 
 
 def lb_profile_end(ctx):
-    t = np.zeros(5)
-    n = np.zeros(5, dtype=np.int64)
+    t = np.zeros(6)
+    n = np.zeros(6, dtype=np.int64)
     _check(ctx, load().lb_profile_end(ctx, _dp(t), n.ctypes.data_as(_LP)), "lb_profile_end")
     return {k: (float(t[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
 
