@@ -13,7 +13,8 @@
 #include "lbsq_internal.cuh"
 
 namespace lbsq {
-void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, cudaStream_t st);
+void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, int zmode,
+                  const int* win, int gz, cudaStream_t st);
 void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, int grid_box, long long* step,
                         cudaStream_t st);
 void launch_body_step(const Bodies& B, int parity, int grid_links, int grid_box, long long* step, cudaStream_t st);
@@ -81,7 +82,16 @@ struct lb_ctx {
     std::vector<std::pair<void*, size_t>> allocs;
     // graph of two steps (even then odd)
     cudaGraphExec_t graph = nullptr;
+    int64_t graph_launches = 0;  // kernel launches in one replay
     int sweep_variant = 0;
+    // overlap of the body kernels of step t with the far sweep of step t+1:
+    // the far sweep on `side`, the body kernels on `hi` (highest priority, so
+    // that SM slots freed by sweep blocks go to the short body kernels first)
+    cudaStream_t side = nullptr, hi = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+    int* d_win = nullptr;  // [2][2] near-body z-windows by step parity
+    bool split = false;    // whether steps are split into far and near sweeps
+    int win_max = 0;       // upper bound of the window length (planes)
     // kernel tracing
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -163,6 +173,7 @@ Bodies bodies_view(const lb_ctx* c) {
     B.rel_cap = c->list_cap;
     B.done = c->d_counts + 3;
     B.err = c->d_err;
+    B.win = c->split ? c->d_win : nullptr;
     return B;
 }
 
@@ -322,6 +333,19 @@ lb_status relayout(lb_ctx* c) {
                        c->stream));
     lb_status s = upload_lattice(c);
     if (s != LB_OK) return s;
+    // near-body window: an upper bound of its length from the box heights; the
+    // split pays only when the window leaves most of the lattice outside
+    int wmax = 0;
+    bool across = false;
+    for (auto& b : c->par) {
+        if (b.kind == BODY_SPHERE) wmax += b.box_w[2] + 5;
+        else if (b.wall_axis == 2) wmax += 3 + 5;
+        else across = true;
+    }
+    c->win_max = std::min(wmax, c->L.nz);
+    c->split = !across && nb > 0 && wmax * 5 < 3 * c->L.nz;
+    const int win_init[4] = {0, c->L.nz, 0, c->L.nz};  // whole lattice until the first rebuild
+    CK(cudaMemcpyAsync(c->d_win, win_init, sizeof(win_init), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));  // host vectors above are transient
     drop_graph(c);
     return LB_OK;
@@ -450,8 +474,17 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     c->d_count = dalloc_t<int>(c, 2);
     c->d_lat = dalloc_t<Lattice>(c, 1);
     c->d_counts = dalloc_t<int>(c, 4);
+    c->d_win = dalloc_t<int>(c, 4);
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) return bail(LB_ERR_CUDA);
+    if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess)
+        return bail(LB_ERR_CUDA);
     if (!L.F || !c->own || !c->own_prev || !c->d_mass_part || !c->d_small || !c->d_err || !c->d_count ||
-        !c->d_lat || !c->d_counts)
+        !c->d_lat || !c->d_counts || !c->d_win)
         return bail(LB_ERR_OOM);
     L.own = c->own;
     L.own_prev = c->own_prev;
@@ -475,6 +508,14 @@ lb_status lb_destroy(lb_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graph(c);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_join2) cudaEventDestroy(c->ev_join2);
+    for (cudaStream_t st : {c->side, c->hi})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
     while (!c->allocs.empty()) dfree(c, c->allocs.back().first);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -679,38 +720,80 @@ static cudaEvent_t pool_event(lb_ctx* c, size_t k) {
     return c->ev_pool[k];
 }
 
-static void enqueue_step(lb_ctx* c, int parity) {
-    const bool bodies = !c->par.empty();
-    if (c->profiling) {
-        // each kernel between its own pair of events
-        const int nk = bodies ? 5 : 1;
-        for (int k = 0; k < nk; ++k) {
-            const size_t e0 = 2 * c->ev_used.size();
-            cudaEventRecord(pool_event(c, e0), c->stream);
-            if (k == 0) launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, c->stream);
-            else launch_body_kernel(k, bodies_view(c), parity, c->n_link_items, c->grid_box, nullptr, c->stream);
-            cudaEventRecord(pool_event(c, e0 + 1), c->stream);
-            c->ev_used.emplace_back(k, (int)e0);
-        }
-        c->launches += nk;
-        return;
+static void sweep_all(lb_ctx* c, int parity, cudaStream_t st) {
+    launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, 0, nullptr, c->L.nz, st);
+}
+
+// Traced step: each kernel between its own pair of events, no overlap.
+static void enqueue_traced_step(lb_ctx* c) {
+    const int parity = (int)(c->step & 1);
+    const int nk = c->par.empty() ? 1 : 5;
+    for (int k = 0; k < nk; ++k) {
+        const size_t e0 = 2 * c->ev_used.size();
+        cudaEventRecord(pool_event(c, e0), c->stream);
+        if (k == 0) sweep_all(c, parity, c->stream);
+        else launch_body_kernel(k, bodies_view(c), parity, c->n_link_items, c->grid_box, nullptr, c->stream);
+        cudaEventRecord(pool_event(c, e0 + 1), c->stream);
+        c->ev_used.emplace_back(k, (int)e0);
     }
-    launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, c->stream);
-    c->launches += 1;
-    if (bodies) {
-        launch_body_step(bodies_view(c), parity, c->n_link_items, c->grid_box, nullptr, c->stream);
-        c->launches += 4;
+    c->launches += nk;
+    c->step++;
+}
+
+// n steps on the context's stream.  When the bodies occupy a thin slab of
+// planes, the sweep of step t+1 is split: the planes outside the near-body
+// window (none of whose slots the body kernels touch) run on a side stream
+// while the body kernels of step t run, the planes inside it after them.
+static void enqueue_steps(lb_ctx* c, int64_t n) {
+    const bool bodies = !c->par.empty();
+    const Bodies B = bodies_view(c);
+    bool swept = false;  // sweep of the current step already issued
+    for (int64_t k = 0; k < n; ++k) {
+        const int parity = (int)(c->step & 1);
+        if (!swept) {
+            sweep_all(c, parity, c->stream);
+            c->launches += 1;
+        }
+        swept = false;
+        if (!bodies) {
+            c->step++;
+            continue;
+        }
+        if (c->split && k + 1 < n) {
+            const int q = 1 - parity;
+            const int* win = c->d_win + 2 * q;
+            cudaEventRecord(c->ev_fork, c->stream);
+            cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+            cudaStreamWaitEvent(c->hi, c->ev_fork, 0);
+            launch_body_step(B, parity, c->n_link_items, c->grid_box, nullptr, c->hi);
+            launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 1, win, c->L.nz, c->side);
+            cudaEventRecord(c->ev_join, c->side);
+            cudaEventRecord(c->ev_join2, c->hi);
+            cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+            cudaStreamWaitEvent(c->stream, c->ev_join2, 0);
+            launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 2, win, c->win_max, c->stream);
+            c->launches += 6;
+            swept = true;
+        } else {
+            launch_body_step(B, parity, c->n_link_items, c->grid_box, nullptr, c->stream);
+            c->launches += 4;
+        }
+        c->step++;
     }
 }
 
+constexpr int kGraphSteps = 8;
+
 static lb_status build_graph(lb_ctx* c) {
     cudaGraph_t g = nullptr;
+    const int64_t saved_launches = c->launches, saved_step = c->step;
+    c->step = 0;  // the graph starts on an even step
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    const int64_t saved = c->launches;
-    enqueue_step(c, 0);
-    enqueue_step(c, 1);
-    c->launches = saved;
+    enqueue_steps(c, kGraphSteps);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->graph_launches = c->launches - saved_launches;
+    c->launches = saved_launches;
+    c->step = saved_step;
     if (e != cudaSuccess) return cuda_fail(c, e, "capture");
     e = cudaGraphInstantiate(&c->graph, g, 0);
     cudaGraphDestroy(g);
@@ -725,35 +808,29 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
     if (!c || nsteps < 0) return LB_ERR_INVALID;
     if (c->sticky) return fail(c, LB_ERR_STATE, "context holds a device error");
     CK(cudaSetDevice(c->p.device));
-    const int per_step = 1 + (c->par.empty() ? 0 : 4);
+    if (c->profiling) {
+        for (int64_t k = 0; k < nsteps; ++k) enqueue_traced_step(c);
+        CK(cudaGetLastError());
+        return LB_OK;
+    }
     int64_t left = nsteps;
-    if (left > 0 && (c->step & 1)) {
-        enqueue_step(c, 1);
-        c->step++;
+    if (left > 0 && (c->step & 1)) {  // graphs start on even steps
+        enqueue_steps(c, 1);
         left--;
     }
-    if (c->profiling) {
-        for (; left > 0; --left) {
-            enqueue_step(c, (int)(c->step & 1));
-            c->step++;
-        }
-    }
-    if (left >= 2) {
+    if (left >= kGraphSteps) {
         if (!c->graph) {
             lb_status s = build_graph(c);
             if (s != LB_OK) return s;
         }
-        while (left >= 2) {
+        while (left >= kGraphSteps) {
             CK(cudaGraphLaunch(c->graph, c->stream));
-            c->launches += 2 * per_step;
-            c->step += 2;
-            left -= 2;
+            c->launches += c->graph_launches;
+            c->step += kGraphSteps;
+            left -= kGraphSteps;
         }
     }
-    if (left == 1) {
-        enqueue_step(c, 0);
-        c->step++;
-    }
+    if (left > 0) enqueue_steps(c, left);
     CK(cudaGetLastError());
     return LB_OK;
 }

@@ -554,15 +554,43 @@ __global__ void __launch_bounds__(kBB) k_classify(const Bodies B) {
         const int id = k + 1;
         long long b0, b1;
         box_range((long long)w[0] * w[1] * w[2], g, p.g_box, b0, b1);
+        // centre split into integer and fraction for exact-enough FP32 offsets
+        int ip[3];
+        float fp[3];
+        for (int a = 0; a < 3; ++a) {
+            ip[a] = (int)floor(s.pos[a]);
+            fp[a] = (float)(s.pos[a] - (double)ip[a]);
+        }
+        const int n3[3] = {L.nx, L.ny, L.nz};
+        const float R2f = (float)(p.R * p.R);
+        // |FP32 |d|^2 - exact| < 2e-3 for every node of a box in a lattice
+        // below 2^15 per axis; nodes farther than this band from the surface
+        // are decided in FP32, the rest by the exact FP64 test
+        const float band = 1e-3f * R2f + 1e-2f;
         float mloc = FLT_MAX;
         for (long long b = b0 + threadIdx.x; b < b1; b += kBB) {
             int x, y, z;
             box_cell(L, lo, w, b, x, y, z);
             const int64_t n = cell_index(L, x, y, z);
-            const double dx = min_image((double)x - s.pos[0], L.nx);
-            const double dy = min_image((double)y - s.pos[1], L.ny);
-            const double dz = min_image((double)z - s.pos[2], L.nz);
-            const bool in = inside_sphere(dx, dy, dz, p.R);
+            const int xi[3] = {x, y, z};
+            float df[3];
+            for (int a = 0; a < 3; ++a) {
+                float t = (float)(xi[a] - ip[a]) - fp[a];
+                const float h = 0.5f * (float)n3[a];
+                if (t > h) t -= (float)n3[a];
+                else if (t <= -h) t += (float)n3[a];
+                df[a] = t;
+            }
+            const float s32 = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+            bool in;
+            if (fabsf(s32 - R2f) > band) {
+                in = s32 < R2f;
+            } else {
+                const double dx = min_image((double)x - s.pos[0], L.nx);
+                const double dy = min_image((double)y - s.pos[1], L.ny);
+                const double dz = min_image((double)z - s.pos[2], L.nz);
+                in = inside_sphere(dx, dy, dz, p.R);
+            }
             const int old = L.own_prev[n];
             if (in) {
                 if (old == 0) {
@@ -574,10 +602,10 @@ __global__ void __launch_bounds__(kBB) k_classify(const Bodies B) {
             } else if (old == id) {
                 L.own[n] = 0;
             }
-            // distance of the node to the surface, as a lower bound: FP32 square
-            // root (relative error < 1e-6 on values below 1e3) minus 1e-4
-            const float dist = sqrtf((float)(dx * dx + dy * dy + dz * dz));
-            mloc = fminf(mloc, fmaxf(fabsf(dist - (float)p.R) - 1e-4f, 0.0f));
+            // distance of the node to the surface, as a lower bound: FP32 offsets
+            // and square root (absolute error below 1e-4 for |d| < 2^10) minus 1e-3
+            const float dist = sqrtf(s32);
+            mloc = fminf(mloc, fmaxf(fabsf(dist - (float)p.R) - 1e-3f, 0.0f));
         }
         // block minimum (FP32 values, exact)
 #pragma unroll
@@ -727,7 +755,14 @@ __global__ void __launch_bounds__(kBB) k_convert(const Bodies B) {
             }
             __syncthreads();
         }
-        block_sum_fixed<6, kBB>(acc, sm, s_tot);
+        // conversions are rare: blocks without one skip the FP64 block sum
+        const int had = acc[0] != 0.0 || acc[1] != 0.0 || acc[2] != 0.0 || acc[3] != 0.0 || acc[4] != 0.0 ||
+                        acc[5] != 0.0;
+        if (__syncthreads_or(had)) {
+            block_sum_fixed<6, kBB>(acc, sm, s_tot);
+        } else if (threadIdx.x < 6) {
+            s_tot[threadIdx.x] = 0.0;
+        }
         lcount = block_sum_ll<kBB>(lcount, sml);
         if (threadIdx.x < 6) B.part_conv[((size_t)k * B.GB + g) * 6 + threadIdx.x] = s_tot[threadIdx.x];
         if (threadIdx.x == 0) B.part_count[(size_t)k * B.GB + g] = (int)lcount;
@@ -743,6 +778,54 @@ __global__ void __launch_bounds__(kBB) k_convert(const Bodies B) {
 }
 
 // ---------------------------------------------------------------- k_rebuild
+
+// z-window of lattice 0 that holds every cell the body kernels of the next
+// step can touch: the z-extent of every body's scan box at the new positions,
+// two more planes on each side (a body moves less than half a cell per
+// step).  Stored in win[P] for the sweeps two steps later (see api.cu); the
+// whole lattice when the bodies spread over more than 3/5 of it.
+template <int P>
+__device__ void near_window(const Bodies& B) {
+    const Lattice& L = B.lats[0];
+    const int n = L.nz;
+    int lo_min = 0, hi_max = 0, ref = 0;
+    bool first = true, full = L.body_count == 0;
+    for (int j = L.body_begin; j < L.body_begin + L.body_count && !full; ++j) {
+        const BodyParams& q = B.par[j];
+        int lo, w;
+        if (q.kind == BODY_SPHERE) {
+            lo = (int)floor(B.state[1 - P][j].pos[2] - q.R) - 2;
+            w = q.box_w[2];
+        } else if (q.wall_axis == 2) {
+            lo = q.wall_index - 1;
+            w = 3;
+        } else {
+            full = true;  // a wall across every plane
+            break;
+        }
+        // unwrap the box centre to within half a lattice of the first body's
+        int c = lo + w / 2;
+        if (first) ref = c;
+        while (c - ref > n / 2) {
+            lo -= n;
+            c -= n;
+        }
+        while (c - ref < -n / 2) {
+            lo += n;
+            c += n;
+        }
+        if (first || lo - 2 < lo_min) lo_min = lo - 2;
+        if (first || lo + w + 2 > hi_max) hi_max = lo + w + 2;
+        first = false;
+    }
+    int z0 = 0, len = n;
+    if (!full && (hi_max - lo_min) * 5 < 3 * n) {
+        z0 = ((lo_min % n) + n) % n;
+        len = hi_max - lo_min;
+    }
+    B.win[2 * P] = z0;
+    B.win[2 * P + 1] = len;
+}
 
 template <int P>
 __global__ void __launch_bounds__(kBB) k_rebuild(const Bodies B) {
@@ -827,6 +910,7 @@ __global__ void __launch_bounds__(kBB) k_rebuild(const Bodies B) {
             *B.n_box = 0;
             *B.n_rel = 0;
             *B.done = 0;
+            if (B.win) near_window<P>(B);
         }
     }
 }

@@ -231,6 +231,7 @@ struct Bodies {
     int rel_cap;
     int* done;             // blocks of the rebuild kernel that finished (self-resetting)
     int* err;              // error word for list overflow (shared)
+    int* win;              // near-body z-windows [2][2] of lattice 0 (z0, length) by step parity, or null
 };
 
 // Scan box of a body: origin and extent.

@@ -24,7 +24,26 @@ struct SweepArgs {
     int64_t Np;
     double lambda_e, lambda_o, rho0;
     float scale, inv_scale;
+    // z-window split: mode 0 sweeps every plane; mode 1 ("far") the planes
+    // outside the window win[0..1] = (z0, length); mode 2 ("near") the planes
+    // inside it, blockIdx.z counting from z0
+    int zmode;
+    const int* win;
 };
+
+// Plane swept by this block, or -1 if none.
+__device__ __forceinline__ int sweep_plane(const SweepArgs& a) {
+    const int bz = blockIdx.z;
+    if (a.zmode == 0) return bz;
+    const int z0 = __ldg(a.win), len = __ldg(a.win + 1);
+    if (a.zmode == 2) {
+        if (bz >= len) return -1;
+        const int z = z0 + bz;
+        return z >= a.nz ? z - a.nz : z;
+    }
+    const int rel = bz - z0 < 0 ? bz - z0 + a.nz : bz - z0;
+    return rel < len ? -1 : bz;
+}
 
 template <class R, bool DEV>
 __device__ __forceinline__ void collide_trt(R g[Q], R le, R lo, R rho0) {
@@ -81,8 +100,9 @@ __global__ void __launch_bounds__(256) k_sweep(const SweepArgs a) {
     using T = typename ST::T;
     using R = typename ST::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= a.nx) return;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int z = sweep_plane(a);
+    if (x >= a.nx || z < 0) return;
+    const int y = blockIdx.y;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
     const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
@@ -149,8 +169,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep2(const SweepArgs a) {
     using V = typename PV::V;
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x0 >= a.nx || y >= a.ny) return;
-    const int z = blockIdx.z;
+    const int z = sweep_plane(a);
+    if (x0 >= a.nx || y >= a.ny || z < 0) return;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
     const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
@@ -206,14 +226,14 @@ __global__ void __launch_bounds__(256, 2) k_sweep2(const SweepArgs a) {
 }
 
 template <int S>
-static void launch_s(const SweepArgs& a, int parity, int variant, cudaStream_t st) {
+static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaStream_t st) {
     if constexpr (S != ST_F64) {
         if (variant != 1 && a.nx % 2 == 0) {
             const int pairs = a.nx / 2;
             int bx = ((pairs + 31) / 32) * 32;
             if (bx > 128) bx = 128;
             const int by = 256 / bx;
-            dim3 block(bx, by), grid((pairs + bx - 1) / bx, (a.ny + by - 1) / by, a.nz);
+            dim3 block(bx, by), grid((pairs + bx - 1) / bx, (a.ny + by - 1) / by, gz);
             if (parity == 0) k_sweep2<S, 0><<<grid, block, 0, st>>>(a);
             else k_sweep2<S, 1><<<grid, block, 0, st>>>(a);
             return;
@@ -221,14 +241,17 @@ static void launch_s(const SweepArgs& a, int parity, int variant, cudaStream_t s
     }
     int bx = ((a.nx + 31) / 32) * 32;
     if (bx > 256) bx = 256;
-    dim3 grid((a.nx + bx - 1) / bx, a.ny, a.nz);
+    dim3 grid((a.nx + bx - 1) / bx, a.ny, gz);
     if (parity == 0) k_sweep<S, 0><<<grid, bx, 0, st>>>(a);
     else k_sweep<S, 1><<<grid, bx, 0, st>>>(a);
 }
 
 // variant: 0 = default (two cells per thread where nx is even, FP64 one cell),
 // 1 = one cell per thread, 2 = two cells per thread where possible.
-void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, cudaStream_t st) {
+// zmode / win / gz: plane selection (see SweepArgs); gz = grid planes (nz for
+// modes 0 and 1, an upper bound of the window length for mode 2).
+void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, int zmode,
+                  const int* win, int gz, cudaStream_t st) {
     SweepArgs a;
     a.F = L.F;
     a.nx = L.nx;
@@ -240,11 +263,14 @@ void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity
     a.rho0 = L.rho0;
     a.scale = L.scale;
     a.inv_scale = L.inv_scale;
+    a.zmode = zmode;
+    a.win = win;
+    if (gz <= 0) return;
     switch (L.storage) {
-        case ST_F64: launch_s<ST_F64>(a, parity, variant, st); break;
-        case ST_F32: launch_s<ST_F32>(a, parity, variant, st); break;
-        case ST_F16: launch_s<ST_F16>(a, parity, variant, st); break;
-        default: launch_s<ST_BF16>(a, parity, variant, st); break;
+        case ST_F64: launch_s<ST_F64>(a, parity, variant, gz, st); break;
+        case ST_F32: launch_s<ST_F32>(a, parity, variant, gz, st); break;
+        case ST_F16: launch_s<ST_F16>(a, parity, variant, gz, st); break;
+        default: launch_s<ST_BF16>(a, parity, variant, gz, st); break;
     }
 }
 
