@@ -223,6 +223,71 @@ def e2e_run(wl, storage, steps, device, torch):
             "steps": steps, "wall_s": t}
 
 
+def serve_run(torch, device=0, n=256, budget=24 << 30, load=0.8):
+    """The serving mix (256 Poisson arrivals; periodic box / square tube /
+    obstacle geometries; R ~ U[3, 12]; steps ~ U[2000, 20000]; FP16-deviation
+    or FP32 storage) through lb_server: requests are submitted when their
+    arrival time has passed (host wall clock) and admitted as slots and HBM
+    budget free up.  The arrival rate is set to `load` times a capacity
+    measured first on the leading requests of the mix.  Latency = finish
+    (end of the round in which the request completed, host clock) - arrival."""
+    from paper_1903_04799_gb300 import lbsq
+    from paper_1903_04799_gb300 import workloads as W
+
+    def req_of(m):
+        return lbsq.make_request(m.geometry, m.shape, m.storage, pos=m.pos, e=m.e, R=m.R, B1=m.B1, beta=m.beta,
+                                 obstacle=m.obstacle, wca=m.wca, steps=m.steps)
+
+    srv = lbsq.Server(budget_bytes=budget, max_resident=64, round_steps=64, device=device)
+    info0 = srv.info()
+    # capacity: the first 24 requests all resident, 6 rounds
+    probe = W.serving_mix(n=24, rate=1.0)
+    for m in probe:
+        srv.submit(req_of(m))
+    srv.advance()
+    c0, t0 = srv.info()["cell_updates"], time.perf_counter()
+    for _ in range(6):
+        srv.advance()
+    cap = (srv.info()["cell_updates"] - c0) / (time.perf_counter() - t0)
+    srv.close()
+    mix = W.serving_mix(n=n, rate=1.0)
+    work = np.mean([m.cells * m.steps for m in mix])
+    rate = load * cap / work
+    mix = W.serving_mix(n=n, rate=rate)
+    srv = lbsq.Server(budget_bytes=budget, max_resident=64, round_steps=64, tile_planes=info0["tile_planes"],
+                      device=device)
+    tickets, finish, pending = {}, {}, list(range(n))
+    t_start = time.perf_counter()
+    max_res = 0
+    while len(finish) < n:
+        now = time.perf_counter() - t_start
+        while pending and mix[pending[0]].arrival <= now:
+            i = pending.pop(0)
+            tickets[i] = srv.submit(req_of(mix[i]))
+        running, queued = srv.advance()
+        max_res = max(max_res, running)
+        now = time.perf_counter() - t_start
+        for i, t in tickets.items():
+            if i in finish:
+                continue
+            res = srv.poll(t)
+            if res.state in (lbsq.LB_REQ_DONE, lbsq.LB_REQ_FAILED):
+                finish[i] = (now, res.state)
+        if running == 0 and queued == 0 and pending:
+            time.sleep(max(0.0, mix[pending[0]].arrival - (time.perf_counter() - t_start)))
+    info = srv.info()
+    srv.close()
+    lat = np.array([finish[i][0] - mix[i].arrival for i in range(n)])
+    span = max(f[0] for f in finish.values()) - mix[0].arrival
+    failed = sum(1 for f in finish.values() if f[1] != lbsq.LB_REQ_DONE)
+    return {"requests": n, "failed": failed, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+            "aggregate_mlups": info["cell_updates"] / span / 1e6, "busy_span_s": span,
+            "offered_load": load, "capacity_mlups_probe": cap / 1e6, "arrival_rate_per_s": rate,
+            "max_resident": max_res, "tile_planes": info["tile_planes"], "blocks_per_sm": info["blocks_per_sm"],
+            "round_steps": 64, "hbm_budget_gb": budget / 2**30}
+
+
 def cpu_baseline(wl, budget_s=15.0):
     """The oracle as it stands, on the host cores, a bounded sample of the workload."""
     from oracle import oracle as O
@@ -354,6 +419,8 @@ def ours(args):
                                                  "kernels_ms_per_step": r["kernels_ms"],
                                                  "steps_per_timed_iteration": r["steps_per_timed_iteration"]}
             res["extra"] = extra
+        if not args.skip_serve:
+            res["serving_c5"] = serve_run(torch, local)
         res["e2e"] = e2e_run(wl, head, min(args.steps, 1000), local, torch)
         if not args.skip_cpu:
             res["cpu_baseline"] = cpu_baseline(wl)
@@ -408,6 +475,7 @@ def main():
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

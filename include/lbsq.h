@@ -224,6 +224,83 @@ lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant);
 lb_status lb_profile_begin(lb_ctx* c);
 lb_status lb_profile_end(lb_ctx* c, double total_ms[6], int64_t launches[6]);
 
+/* ---- Serving: many independent simulations resident at once ------------
+ * A server keeps many squirmer simulations (requests) resident on one GPU and
+ * advances them together: each step is one launch of a persistent sweep over
+ * a packed list of tiles (z-slabs) of every resident lattice, whatever their
+ * sizes and storages, followed by the body kernels of all their bodies; the
+ * steps of a round are replayed from one CUDA graph.  Requests are admitted in
+ * arrival order as lattice slots and device memory (a fixed HBM budget,
+ * allocated once and carved per request) free up; later requests that fit
+ * may start before an earlier one that does not (at most 4 times).  A
+ * request stops after its own number of steps; its results stay until
+ * polled.  Every request evolves exactly as it would alone: kernels never mix
+ * data of two lattices and every reduction has a fixed order per body. */
+typedef struct lb_server lb_server;
+
+typedef struct {
+    int32_t device;
+    void* stream;            /* cudaStream_t, or NULL: the server creates one */
+    size_t hbm_budget_bytes; /* device memory for resident lattices (populations,
+                                owners, boundary links); allocated at creation */
+    int32_t max_resident;    /* lattice slots, 1..256 */
+    int32_t round_steps;     /* steps per scheduling round (even, >= 2) */
+    int32_t tile_planes;     /* z-planes per sweep tile; 0 = pick by timing at creation */
+    const lb_allocator* allocator; /* NULL = cudaMalloc / cudaFree */
+} lb_server_params;
+
+/* One simulation (a configuration of the paper's Secs. II-III):
+ *   geometry 0: periodic box with one squirmer;
+ *   geometry 1: square tube along z (plane walls at x, y = 0 and n-1, as
+ *               lb_add_wall kind 1) with one squirmer;
+ *   geometry 2: periodic box with one squirmer and a fixed obstacle sphere
+ *               (obstacle = x, y, z, radius; as lb_add_wall kind 2). */
+typedef struct {
+    int32_t geometry;
+    int32_t nx, ny, nz;
+    int32_t storage;           /* lb_storage */
+    int32_t collision;         /* lb_collision */
+    double lambda_e, magic, rho0;
+    double pos[3], e[3];       /* squirmer centre and orientation */
+    double R, B1, beta;        /* squirmer radius and modes (mobile, density rho0) */
+    double obstacle[4];
+    double wca_sigma, wca_eps; /* contact force (Eq. "wca"), eps = 0: none */
+    int64_t steps;
+} lb_request;
+
+typedef enum { LB_REQ_QUEUED = 0, LB_REQ_RUNNING = 1, LB_REQ_DONE = 2, LB_REQ_FAILED = 3 } lb_request_state;
+
+typedef struct {
+    int32_t state;       /* lb_request_state */
+    int32_t status;      /* lb_status of a failed request */
+    int64_t steps_done;
+    double pos[3], vel[3], e[3], omega[3]; /* squirmer state at the end */
+    double F[3], T[3];   /* as lb_get_force_torque, last step */
+    double mean_speed;   /* mean of v.e over the updates after the half-way round */
+    double mean_vel[3];  /* mean velocity over all updates */
+} lb_result;
+
+void lb_server_params_default(lb_server_params* p);
+/* Errors: LB_ERR_INVALID, LB_ERR_OOM (budget not allocatable), LB_ERR_CUDA. */
+lb_status lb_server_create(const lb_server_params* p, lb_server** out);
+lb_status lb_server_destroy(lb_server* s);
+/* Queue a request; *ticket identifies it.  Errors: LB_ERR_INVALID (sizes,
+ * radius, storage, a request larger than the whole budget). */
+lb_status lb_server_submit(lb_server* s, const lb_request* r, int64_t* ticket);
+/* One scheduling round: retire finished requests, admit queued ones that
+ * fit, advance every resident request by round_steps steps (or fewer, to its
+ * end), wait for the GPU.  *running and *queued receive the counts after the
+ * round (either may be NULL). */
+lb_status lb_server_advance(lb_server* s, int32_t* running, int32_t* queued);
+/* State and (when done) results of a request; a done request is forgotten
+ * after it has been polled once.  LB_ERR_INVALID for an unknown ticket. */
+lb_status lb_server_poll(lb_server* s, int64_t ticket, lb_result* out);
+/* Sweep tile shape in use (picked by timing when tile_planes = 0), device
+ * memory in use and total cell updates done. */
+lb_status lb_server_info(const lb_server* s, int32_t* tile_planes, int32_t* blocks_per_sm, size_t* bytes_used,
+                         double* cell_updates);
+const char* lb_server_last_error(const lb_server* s);
+
 /* ---- Allocation-free entry point (the paper has no counterpart) ----------
  * For callers that must not allocate device memory: code that runs while a
  * host framework owns all device memory through its own pool, code inside a

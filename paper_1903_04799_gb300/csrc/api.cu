@@ -174,6 +174,7 @@ Bodies bodies_view(const lb_ctx* c) {
     B.done = c->d_counts + 3;
     B.err = c->d_err;
     B.win = c->split ? c->d_win : nullptr;
+    B.gstep = nullptr;
     return B;
 }
 
@@ -187,6 +188,8 @@ lb_status upload_lattice(lb_ctx* c) {
     L.body_begin = 0;
     L.body_count = (int)c->par.size();
     L.active = 1;
+    L.gstep = nullptr;
+    L.stop_step = 0;
     c->L = L;
     CK(cudaMemcpyAsync(c->d_lat, &L, sizeof(Lattice), cudaMemcpyHostToDevice, c->stream));
     return LB_OK;

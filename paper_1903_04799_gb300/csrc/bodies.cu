@@ -310,6 +310,9 @@ __device__ void update_body(const Lattice& L, const Bodies& B, int k, const doub
             so.pos[a] = q;
         }
         rotate_e(so.e, so.omega);
+        for (int a = 0; a < 3; ++a) A.vsum[a] += so.vel[a];
+        A.vesum += so.vel[0] * so.e[0] + so.vel[1] * so.e[1] + so.vel[2] * so.e[2];
+        A.nsum += 1;
         const double sp = so.vel[0] * so.vel[0] + so.vel[1] * so.vel[1] + so.vel[2] * so.vel[2];
         if (!(sp < 0.25)) set_error(L.err, 5);
         // Node crossing test: every node of the box kept its side of the surface
@@ -481,7 +484,7 @@ __global__ void __launch_bounds__(kLB) k_links(const Bodies B) {
         const int k = item.x, g = item.y;
         const BodyParams& p = B.par[k];
         const Lattice& L = B.lats[p.lat];
-        if (!L.active) continue;
+        if (!lattice_active(L)) continue;
         const int G = p.g_links;
         BodyAcc& A = B.acc[k];
         double acc[12];
@@ -911,6 +914,7 @@ __global__ void __launch_bounds__(kBB) k_rebuild(const Bodies B) {
             *B.n_rel = 0;
             *B.done = 0;
             if (B.win) near_window<P>(B);
+            if (B.gstep) *B.gstep += 1;
         }
     }
 }

@@ -90,9 +90,16 @@ struct Lattice {
     double lambda_e, lambda_o;
     double wca_sigma, wca_eps;
     int body_begin, body_count;  // this lattice's bodies in the body table
-    int active;                  // 0: not stepped (a free or finished server slot)
+    int active;                  // 0: not stepped (a free server slot, or being set up)
     int pad;
+    const long long* gstep;      // server: global step counter (null for a context)
+    long long stop_step;         // server: the lattice is stepped while *gstep < stop_step
 };
+
+// Whether a lattice takes part in the current step.
+__device__ __forceinline__ bool lattice_active(const Lattice& L) {
+    return L.active && (L.gstep == nullptr || *L.gstep < L.stop_step);
+}
 
 __device__ __forceinline__ int wrapi(int a, int n) {
     a %= n;
@@ -200,6 +207,8 @@ struct BodyAcc {
     double r_class[3];                // centre at the last classification
     unsigned long long margin_bits;   // min | |x - r| - R | over the box at that time
     int box_lo[3];                    // scan box origin of the current classification
+    double vsum[3], vesum;            // sums over the updates of v and of v.e (mobile spheres)
+    long long nsum;                   // number of updates summed
     int reclass;                      // re-classify this step (set by the update)
     int rel_flag;                     // queued for relinking this step
     long long link_count;
@@ -232,6 +241,7 @@ struct Bodies {
     int* done;             // blocks of the rebuild kernel that finished (self-resetting)
     int* err;              // error word for list overflow (shared)
     int* win;              // near-body z-windows [2][2] of lattice 0 (z0, length) by step parity, or null
+    long long* gstep;      // server: global step counter, advanced by the rebuild kernel (or null)
 };
 
 // Scan box of a body: origin and extent.

@@ -42,6 +42,30 @@ class lb_params(C.Structure):
                 ("allocator", C.POINTER(lb_allocator))]
 
 
+class lb_server_params(C.Structure):
+    _fields_ = [("device", C.c_int32), ("stream", C.c_void_p), ("hbm_budget_bytes", C.c_size_t),
+                ("max_resident", C.c_int32), ("round_steps", C.c_int32), ("tile_planes", C.c_int32),
+                ("allocator", C.POINTER(lb_allocator))]
+
+
+class lb_request(C.Structure):
+    _fields_ = [("geometry", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("storage", C.c_int32), ("collision", C.c_int32), ("lambda_e", C.c_double),
+                ("magic", C.c_double), ("rho0", C.c_double), ("pos", C.c_double * 3), ("e", C.c_double * 3),
+                ("R", C.c_double), ("B1", C.c_double), ("beta", C.c_double), ("obstacle", C.c_double * 4),
+                ("wca_sigma", C.c_double), ("wca_eps", C.c_double), ("steps", C.c_int64)]
+
+
+class lb_result(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("steps_done", C.c_int64),
+                ("pos", C.c_double * 3), ("vel", C.c_double * 3), ("e", C.c_double * 3),
+                ("omega", C.c_double * 3), ("F", C.c_double * 3), ("T", C.c_double * 3),
+                ("mean_speed", C.c_double), ("mean_vel", C.c_double * 3)]
+
+
+LB_REQ_QUEUED, LB_REQ_RUNNING, LB_REQ_DONE, LB_REQ_FAILED = 0, 1, 2, 3
+
+
 class LBError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str = ""):
         self.status = status
@@ -82,6 +106,14 @@ SIGNATURES = {
     "lb_profile_begin": (C.c_int, [_CTX]),
     "lb_profile_end": (C.c_int, [_CTX, _DP, _LP]),
     "lb_fluid_totals_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "lb_server_params_default": (None, [C.POINTER(lb_server_params)]),
+    "lb_server_create": (C.c_int, [C.POINTER(lb_server_params), C.POINTER(C.c_void_p)]),
+    "lb_server_destroy": (C.c_int, [C.c_void_p]),
+    "lb_server_submit": (C.c_int, [C.c_void_p, C.POINTER(lb_request), _LP]),
+    "lb_server_advance": (C.c_int, [C.c_void_p, _IP, _IP]),
+    "lb_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(lb_result)]),
+    "lb_server_info": (C.c_int, [C.c_void_p, _IP, _IP, C.POINTER(C.c_size_t), _DP]),
+    "lb_server_last_error": (C.c_char_p, [C.c_void_p]),
 }
 
 _lib = None
@@ -282,6 +314,123 @@ def lb_fluid_totals_static(f_ptr: int, owner_ptr: int, n_cells: int, out_ptr: in
     _check(None, load().lb_fluid_totals_static(C.c_void_p(f_ptr), C.c_void_p(owner_ptr or None), int(n_cells),
                                                 C.c_void_p(out_ptr), C.c_void_p(stream_ptr or None)),
            "lb_fluid_totals_static")
+
+
+# ------------------------------------------------------------ serving
+
+def _scheck(srv, status, where):
+    if status != LB_OK:
+        raw = load().lb_server_last_error(srv) if srv else b""
+        raise LBError(status, where, raw.decode() if raw else "")
+
+
+def lb_server_params_default() -> lb_server_params:
+    p = lb_server_params()
+    load().lb_server_params_default(C.byref(p))
+    return p
+
+
+def lb_server_create(p: lb_server_params):
+    srv = C.c_void_p()
+    _scheck(None, load().lb_server_create(C.byref(p), C.byref(srv)), "lb_server_create")
+    return srv
+
+
+def lb_server_destroy(srv):
+    _scheck(None, load().lb_server_destroy(srv), "lb_server_destroy")
+
+
+def lb_server_submit(srv, req: lb_request) -> int:
+    t = C.c_int64()
+    _scheck(srv, load().lb_server_submit(srv, C.byref(req), C.byref(t)), "lb_server_submit")
+    return t.value
+
+
+def lb_server_advance(srv):
+    r, q = C.c_int32(), C.c_int32()
+    _scheck(srv, load().lb_server_advance(srv, C.byref(r), C.byref(q)), "lb_server_advance")
+    return r.value, q.value
+
+
+def lb_server_poll(srv, ticket: int) -> lb_result:
+    out = lb_result()
+    _scheck(srv, load().lb_server_poll(srv, int(ticket), C.byref(out)), "lb_server_poll")
+    return out
+
+
+def lb_server_info(srv):
+    tz, bps, used, cu = C.c_int32(), C.c_int32(), C.c_size_t(), C.c_double()
+    _scheck(srv, load().lb_server_info(srv, C.byref(tz), C.byref(bps), C.byref(used), C.byref(cu)),
+            "lb_server_info")
+    return {"tile_planes": tz.value, "blocks_per_sm": bps.value, "bytes_used": used.value,
+            "cell_updates": cu.value}
+
+
+def make_request(geometry=0, shape=(32, 32, 32), storage="f32", collision="trt", lambda_e=1.0,
+                 magic=3.0 / 16.0, rho0=1.0, pos=None, e=(0.0, 0.0, 1.0), R=4.0, B1=0.005, beta=0.0,
+                 obstacle=(0.0, 0.0, 0.0, 0.0), wca=(1.0, 0.0), steps=100) -> lb_request:
+    r = lb_request()
+    r.geometry = int(geometry)
+    r.nx, r.ny, r.nz = (int(v) for v in shape)
+    r.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    r.collision = LB_TRT if collision == "trt" else LB_BGK
+    r.lambda_e, r.magic, r.rho0 = float(lambda_e), float(magic), float(rho0)
+    pos = pos if pos is not None else tuple(v / 2.0 for v in shape)
+    for a in range(3):
+        r.pos[a] = float(pos[a])
+        r.e[a] = float(e[a])
+    r.R, r.B1, r.beta = float(R), float(B1), float(beta)
+    for a in range(4):
+        r.obstacle[a] = float(obstacle[a])
+    r.wca_sigma, r.wca_eps = float(wca[0]), float(wca[1])
+    r.steps = int(steps)
+    return r
+
+
+class Server:
+    """Many squirmer simulations resident on one GPU, advanced together."""
+
+    def __init__(self, budget_bytes=8 << 30, max_resident=64, round_steps=64, tile_planes=0, device=0,
+                 use_torch=True):
+        p = lb_server_params_default()
+        p.device = int(device)
+        p.hbm_budget_bytes = int(budget_bytes)
+        p.max_resident = int(max_resident)
+        p.round_steps = int(round_steps)
+        p.tile_planes = int(tile_planes)
+        self._stream = None
+        self._alloc = None
+        if use_torch:
+            import torch
+            self._stream = torch.cuda.Stream(device=device)
+            p.stream = C.c_void_p(self._stream.cuda_stream)
+            self._alloc = TorchAllocator(device, self._stream.cuda_stream)
+            p.allocator = C.pointer(self._alloc.struct)
+        self.params = p
+        self.srv = lb_server_create(p)
+
+    def close(self):
+        if getattr(self, "srv", None):
+            lb_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def submit(self, req: lb_request) -> int:
+        return lb_server_submit(self.srv, req)
+
+    def advance(self):
+        return lb_server_advance(self.srv)
+
+    def poll(self, ticket: int) -> lb_result:
+        return lb_server_poll(self.srv, ticket)
+
+    def info(self):
+        return lb_server_info(self.srv)
 
 
 # ------------------------------------------------------------ torch plumbing

@@ -120,3 +120,80 @@ def random_populations(N: int, seed: int, base, spread: float = 0.1):
     rng = np.random.default_rng(seed)
     base = np.asarray(base, dtype=np.float64).reshape(19, 1)
     return base * (1.0 + spread * rng.uniform(-1, 1, (19, N)))
+
+
+@dataclass
+class ServeRequest:
+    """One request of the serving mix (a dict of lb_request fields)."""
+    arrival: float
+    geometry: int
+    shape: tuple
+    storage: str
+    R: float
+    beta: float
+    B1: float
+    steps: int
+    pos: tuple
+    e: tuple
+    obstacle: tuple = (0.0, 0.0, 0.0, 0.0)
+    wca: tuple = (1.0, 0.0)
+
+    @property
+    def cells(self) -> int:
+        return int(np.prod(self.shape))
+
+
+def serving_mix(n: int = 256, seed: int = 190304799, rate: float = 4.0, steps_range=(2000, 20000),
+                edge_range=(32, 160)) -> list:
+    """The serving mix: n requests with exponential inter-arrival times (mean
+    1/rate s); geometry uniform over {periodic box, square tube, box with a
+    fixed obstacle}; squirmer R ~ U[3, 12], beta ~ U[-5, 5], B1 = 0.004,
+    steps ~ U[steps_range]; storage FP16-deviation or FP32 by a fair coin.
+      box:      cubic, edge ~ U[edge_range] (raised to 2R + 8 if smaller),
+                squirmer at the centre, random orientation;
+      tube:     (4R + 2)^2 cross-section (walls at 0 and 4R + 1), length 16R,
+                squirmer on the axis tilted by at most 0.2 rad;
+      obstacle: cubic box of edge max(8R + 8, U[edge_range]), obstacle of
+                radius 2R at the centre, squirmer 2R + R + 4 away on a random
+                axis, aimed at the obstacle with a small offset angle; WCA
+                contact force (sigma 1, eps 0.01) on."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        geo = int(rng.integers(0, 3))
+        R = float(rng.uniform(3.0, 12.0))
+        beta = float(rng.uniform(-5.0, 5.0))
+        steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
+        steps += steps % 2
+        storage = "f16dev" if rng.random() < 0.5 else "f32"
+        if geo == 0:
+            L = max(int(rng.integers(edge_range[0], edge_range[1] + 1)), int(math.ceil(2 * R)) + 8)
+            shape = (L, L, L)
+            pos = (L / 2 + 0.25, L / 2 - 0.15, L / 2 + 0.05)
+            out.append(ServeRequest(t, 0, shape, storage, R, beta, 0.004, steps, pos, random_unit(rng)))
+        elif geo == 1:
+            w = int(math.ceil(4 * R)) + 2
+            length = int(math.ceil(16 * R))
+            tilt = float(rng.uniform(0.0, 0.2))
+            phi = float(rng.uniform(0.0, 2 * math.pi))
+            e = (math.sin(tilt) * math.cos(phi), math.sin(tilt) * math.sin(phi), math.cos(tilt))
+            pos = (w / 2 - 0.5 + 0.1, w / 2 - 0.5 - 0.1, length / 2)
+            out.append(ServeRequest(t, 1, (w, w, length), storage, R, beta, 0.004, steps, pos, e,
+                                    wca=(1.0, 0.01)))
+        else:
+            A = 2 * R
+            L = max(int(math.ceil(8 * R)) + 8, int(rng.integers(edge_range[0], edge_range[1] + 1)))
+            c = L / 2
+            axis = int(rng.integers(0, 3))
+            gap = A + R + 4.0
+            pos = [c, c, c]
+            pos[axis] -= gap
+            off = float(rng.uniform(0.02, 0.1))
+            e = [0.0, 0.0, 0.0]
+            e[axis] = 1.0
+            e[(axis + 1) % 3] = off
+            out.append(ServeRequest(t, 2, (L, L, L), storage, R, beta, 0.004, steps, tuple(pos), tuple(e),
+                                    obstacle=(c, c, c, A), wca=(1.0, 0.01)))
+    return out
