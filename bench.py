@@ -254,7 +254,7 @@ def serve_run(torch, device=0, n=256, budget=24 << 30, load=0.8):
     work = np.mean([m.cells * m.steps for m in mix])
     rate = load * cap / work
     mix = W.serving_mix(n=n, rate=rate)
-    srv = lbsq.Server(budget_bytes=budget, max_resident=64, round_steps=64, tile_planes=info0["tile_planes"],
+    srv = lbsq.Server(budget_bytes=budget, max_resident=64, round_steps=64, tile_units=info0["tile_units"],
                       device=device)
     tickets, finish, pending = {}, {}, list(range(n))
     t_start = time.perf_counter()
@@ -284,7 +284,7 @@ def serve_run(torch, device=0, n=256, budget=24 << 30, load=0.8):
             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
             "aggregate_mlups": info["cell_updates"] / span / 1e6, "busy_span_s": span,
             "offered_load": load, "capacity_mlups_probe": cap / 1e6, "arrival_rate_per_s": rate,
-            "max_resident": max_res, "tile_planes": info["tile_planes"], "blocks_per_sm": info["blocks_per_sm"],
+            "max_resident": max_res, "tile_units": info["tile_units"], "blocks_per_sm": info["blocks_per_sm"],
             "round_steps": 64, "hbm_budget_gb": budget / 2**30}
 
 

@@ -93,7 +93,9 @@ typedef struct {
                             3/16 in the paper; ignored for BGK (lo = le) */
     double rho0;         /* rest density, > 0 */
     int32_t storage;     /* lb_storage */
-    int32_t dev_scale_log2; /* FP16 deviation scale exponent; -1 = default (20) */
+    int32_t dev_scale_log2; /* FP16 deviation scale exponent k (store d * 2^k);
+                               -1 = default 14: deviations up to 4 fit, and the
+                               usual 1e-5..1e-2 stay in FP16's normal range */
     int32_t device;      /* CUDA device ordinal */
     void* stream;        /* cudaStream_t to run on; NULL = a stream the context creates */
     const lb_allocator* allocator; /* NULL = cudaMalloc / cudaFree */
@@ -226,8 +228,9 @@ lb_status lb_profile_end(lb_ctx* c, double total_ms[6], int64_t launches[6]);
 
 /* ---- Serving: many independent simulations resident at once ------------
  * A server keeps many squirmer simulations (requests) resident on one GPU and
- * advances them together: each step is one launch of a persistent sweep over
- * a packed list of tiles (z-slabs) of every resident lattice, whatever their
+ * advances them together: each step is one launch per storage type of a
+ * persistent sweep over a packed list of tiles (fixed-size chunks of cells)
+ * of every resident lattice, whatever their
  * sizes and storages, followed by the body kernels of all their bodies; the
  * steps of a round are replayed from one CUDA graph.  Requests are admitted in
  * arrival order as lattice slots and device memory (a fixed HBM budget,
@@ -245,7 +248,7 @@ typedef struct {
                                 owners, boundary links); allocated at creation */
     int32_t max_resident;    /* lattice slots, 1..256 */
     int32_t round_steps;     /* steps per scheduling round (even, >= 2) */
-    int32_t tile_planes;     /* z-planes per sweep tile; 0 = pick by timing at creation */
+    int32_t tile_units;      /* cells (or cell pairs) per sweep tile; 0 = pick by timing at creation */
     const lb_allocator* allocator; /* NULL = cudaMalloc / cudaFree */
 } lb_server_params;
 
@@ -295,9 +298,9 @@ lb_status lb_server_advance(lb_server* s, int32_t* running, int32_t* queued);
 /* State and (when done) results of a request; a done request is forgotten
  * after it has been polled once.  LB_ERR_INVALID for an unknown ticket. */
 lb_status lb_server_poll(lb_server* s, int64_t ticket, lb_result* out);
-/* Sweep tile shape in use (picked by timing when tile_planes = 0), device
- * memory in use and total cell updates done. */
-lb_status lb_server_info(const lb_server* s, int32_t* tile_planes, int32_t* blocks_per_sm, size_t* bytes_used,
+/* Sweep tile size in use (picked by timing when tile_units = 0), persistent
+ * blocks per SM, device memory in use and total cell updates done. */
+lb_status lb_server_info(const lb_server* s, int32_t* tile_units, int32_t* blocks_per_sm, size_t* bytes_used,
                          double* cell_updates);
 const char* lb_server_last_error(const lb_server* s);
 

@@ -465,7 +465,9 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     L.Np = (N + 63) / 64 * 64;
     L.storage = p->storage;
     L.rho0 = p->rho0;
-    const int k = p->dev_scale_log2 < 0 ? 20 : p->dev_scale_log2;
+    // FP16 deviation scale: 2^14 keeps deviations up to 4 representable and
+    // the usual 1e-5 .. 1e-2 in FP16's normal range
+    const int k = p->dev_scale_log2 < 0 ? 14 : p->dev_scale_log2;
     L.scale = p->storage == LB_F16DEV ? std::ldexp(1.0f, k) : 1.0f;
     L.inv_scale = 1.0f / L.scale;
     L.F = dalloc(c, (size_t)Q * L.Np * storage_bytes(p->storage));
@@ -581,7 +583,7 @@ lb_status lb_add_squirmer(lb_ctx* c, const double pos[3], const double e[3], dou
     s = set_list(c, 1, box_items_of(c, nid - 1));
     if (s != LB_OK) return s;
     launch_set_flags(c->d_acc, nb, -1, 0, c->stream);
-    launch_set_flags(c->d_acc, nb, nid - 1, 1, c->stream);
+    launch_set_flags(c->d_acc, nb, nid - 1, 2, c->stream);  // whole box
     Bodies B = bodies_view(c);
     launch_body_kernel(2, B, 1 - cur, 1, c->grid_box, nullptr, c->stream);
     launch_body_kernel(5, B, 1 - cur, 1, 1, nullptr, c->stream);

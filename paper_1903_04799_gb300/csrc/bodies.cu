@@ -73,14 +73,19 @@ __device__ __forceinline__ void block_sum_fixed(const double (&v)[K], double* sm
     __syncthreads();
 }
 
+// Integer block sum (exact, so any order gives the same result): warp
+// shuffles, then one warp over the warp totals.
 template <int T>
 __device__ __forceinline__ long long block_sum_ll(long long v, long long* sm) {
-    sm[threadIdx.x] = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long a = 0;
-        for (int q = 0; q < T; ++q) a += sm[q];
-        sm[0] = a;
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < T / 32 ? sm[threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) sm[0] = v;
     }
     __syncthreads();
     const long long r = sm[0];
@@ -236,6 +241,48 @@ __device__ __forceinline__ void box_cell(const Lattice& L, const int lo[3], cons
     x = wrapi(lo[0] + bx, L.nx);
     y = wrapi(lo[1] + by, L.ny);
     z = wrapi(lo[2] + bz, L.nz);
+}
+
+// FP32 view of a sphere's centre relative to nodes: integer part and fraction
+// of each coordinate, so that node offsets keep full precision.
+struct CentreF {
+    int ip[3];
+    float fp[3];
+};
+
+__device__ __forceinline__ CentreF centre_f(const BodyState& s) {
+    CentreF c;
+    for (int a = 0; a < 3; ++a) {
+        c.ip[a] = (int)floor(s.pos[a]);
+        c.fp[a] = (float)(s.pos[a] - (double)c.ip[a]);
+    }
+    return c;
+}
+
+// |d|^2 of node (x,y,z) from the centre in FP32 (minimum image); absolute
+// error below 2e-3 for |d| < 2^10.
+__device__ __forceinline__ float dist2_f(const Lattice& L, const CentreF& c, int x, int y, int z) {
+    const int xi[3] = {x, y, z}, n3[3] = {L.nx, L.ny, L.nz};
+    float s2 = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        float t = (float)(xi[a] - c.ip[a]) - c.fp[a];
+        const float h = 0.5f * (float)n3[a];
+        if (t > h) t -= (float)n3[a];
+        else if (t <= -h) t += (float)n3[a];
+        s2 += t * t;
+    }
+    return s2;
+}
+
+// Whether a node of a sphere's box can hold a boundary link of the sphere or
+// change owner in one step: only nodes with R - 1.5 < |d| < R + 2 can (a
+// link joins a fluid node to a solid neighbour at most sqrt(2) away; a body
+// moves less than half a node per step).  Generous bounds cover the FP32
+// error of dist2_f.
+__device__ __forceinline__ bool in_shell(float d2, float R) {
+    const float lo = R > 1.5f ? (R - 1.5f) * (R - 1.5f) - 0.25f : -1.0f;
+    const float hi = (R + 2.0f) * (R + 2.0f) + 0.25f;
+    return d2 > lo && d2 < hi;
 }
 
 // Append n consecutive items (k, 0..n-1) to a list, by the calling block.
@@ -473,6 +520,28 @@ __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p
     }
 }
 
+// Links of a still body with no force readout: out slot copied to in slot in
+// the storage format (f_in = f_out when the wall velocity is zero).
+template <int P>
+__device__ __forceinline__ void copy_links(const Lattice& L, long long cnt, const uint32_t* links, int g, int G) {
+    const int64_t Np = L.Np;
+    const int bytes = L.storage == ST_F64 ? 8 : (L.storage == ST_F32 ? 4 : 2);
+    for (long long l = (long long)g * blockDim.x + threadIdx.x; l < cnt; l += (long long)G * blockDim.x) {
+        const uint32_t code = links[l];
+        const int64_t n = code >> 5;
+        const int i = code & 31, ib = opp(i);
+        int x, y, z;
+        cell_coords(L, n, x, y, z);
+        const int64_t ns =
+            cell_index(L, step_wrap(x, cx(i), L.nx), step_wrap(y, cy(i), L.ny), step_wrap(z, cz(i), L.nz));
+        const int64_t out_slot = P == 0 ? (int64_t)ib * Np + n : (int64_t)i * Np + ns;
+        const int64_t in_slot = P == 0 ? (int64_t)i * Np + ns : (int64_t)ib * Np + n;
+        if (bytes == 8) ((double*)L.F)[in_slot] = ((const double*)L.F)[out_slot];
+        else if (bytes == 4) ((float*)L.F)[in_slot] = ((const float*)L.F)[out_slot];
+        else ((unsigned short*)L.F)[in_slot] = ((const unsigned short*)L.F)[out_slot];
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(kLB) k_links(const Bodies B) {
     __shared__ double sm[12 * kLB + 12 * 8];
@@ -487,6 +556,12 @@ __global__ void __launch_bounds__(kLB) k_links(const Bodies B) {
         if (!lattice_active(L)) continue;
         const int G = p.g_links;
         BodyAcc& A = B.acc[k];
+        if (p.copy_only) {
+            // still wall or obstacle (v_b = 0): the reflected population equals the
+            // outgoing one bit for bit; no momentum is summed and nothing moves
+            copy_links<P>(L, A.link_count, B.links + p.link_off, g, G);
+            continue;
+        }
         double acc[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) acc[c] = 0.0;
@@ -557,15 +632,9 @@ __global__ void __launch_bounds__(kBB) k_classify(const Bodies B) {
         const int id = k + 1;
         long long b0, b1;
         box_range((long long)w[0] * w[1] * w[2], g, p.g_box, b0, b1);
-        // centre split into integer and fraction for exact-enough FP32 offsets
-        int ip[3];
-        float fp[3];
-        for (int a = 0; a < 3; ++a) {
-            ip[a] = (int)floor(s.pos[a]);
-            fp[a] = (float)(s.pos[a] - (double)ip[a]);
-        }
-        const int n3[3] = {L.nx, L.ny, L.nz};
-        const float R2f = (float)(p.R * p.R);
+        const CentreF cf = centre_f(s);
+        const float R2f = (float)(p.R * p.R), Rf = (float)p.R;
+        const bool full = A.reclass == 2;  // first classification of a new body
         // |FP32 |d|^2 - exact| < 2e-3 for every node of a box in a lattice
         // below 2^15 per axis; nodes farther than this band from the surface
         // are decided in FP32, the rest by the exact FP64 test
@@ -574,17 +643,11 @@ __global__ void __launch_bounds__(kBB) k_classify(const Bodies B) {
         for (long long b = b0 + threadIdx.x; b < b1; b += kBB) {
             int x, y, z;
             box_cell(L, lo, w, b, x, y, z);
+            const float s32 = dist2_f(L, cf, x, y, z);
+            // nodes well inside or well outside kept their side since the last
+            // classification (a body moves less than half a node per step)
+            if (!full && !in_shell(s32, Rf)) continue;
             const int64_t n = cell_index(L, x, y, z);
-            const int xi[3] = {x, y, z};
-            float df[3];
-            for (int a = 0; a < 3; ++a) {
-                float t = (float)(xi[a] - ip[a]) - fp[a];
-                const float h = 0.5f * (float)n3[a];
-                if (t > h) t -= (float)n3[a];
-                else if (t <= -h) t += (float)n3[a];
-                df[a] = t;
-            }
-            const float s32 = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
             bool in;
             if (fabsf(s32 - R2f) > band) {
                 in = s32 < R2f;
@@ -708,11 +771,18 @@ __global__ void __launch_bounds__(kBB) k_convert(const Bodies B) {
         box_range((long long)w[0] * w[1] * w[2], g, G, b0, b1);
         double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         long long lcount = 0;
+        const bool sphere = p.kind == BODY_SPHERE;
+        const CentreF cf = centre_f(s);
+        const float Rf = (float)p.R;
         for (long long r0 = b0; r0 < b1; r0 += kBB) {
             const long long b = r0 + threadIdx.x;
             int uncover = 0, x = 0, y = 0, z = 0;
-            if (b < b1) {
+            bool take = b < b1;
+            if (take) {
                 box_cell(L, lo, w, b, x, y, z);
+                if (sphere) take = in_shell(dist2_f(L, cf, x, y, z), Rf);
+            }
+            if (take) {
                 const int64_t n = cell_index(L, x, y, z);
                 const int now = L.own[n];
                 if (conv) {
@@ -870,24 +940,34 @@ __global__ void __launch_bounds__(kBB) k_rebuild(const Bodies B) {
         long long base = s_base;
         uint32_t* links = B.links + p.link_off;
         const bool commit = A.reclass != 0;
+        const bool sphere = p.kind == BODY_SPHERE;
+        const CentreF cf = centre_f(s);
+        const float Rf = (float)p.R;
         long long b0, b1;
         box_range((long long)w[0] * w[1] * w[2], g, G, b0, b1);
         for (long long r0 = b0; r0 < b1; r0 += kBB) {
             const long long b = r0 + threadIdx.x;
             uint32_t mask = 0;
             int64_t n = 0;
-            if (b < b1) {
-                int x, y, z;
+            int x = 0, y = 0, z = 0;
+            bool take = b < b1;
+            if (take) {
                 box_cell(L, lo, w, b, x, y, z);
+                // same predicate as the count in k_convert (only shell nodes can
+                // hold links; only they changed owner)
+                if (sphere) take = in_shell(dist2_f(L, cf, x, y, z), Rf);
+            }
+            if (take) {
                 n = cell_index(L, x, y, z);
-                if (L.own[n] == 0) {
+                const int now = L.own[n];
+                if (now == 0) {
                     for (int i = 1; i < Q; ++i) {
                         const int64_t nn = cell_index(L, step_wrap(x, cx(i), L.nx), step_wrap(y, cy(i), L.ny),
                                                       step_wrap(z, cz(i), L.nz));
                         if (L.own[nn] == id) mask |= 1u << i;
                     }
                 }
-                if (commit) L.own_prev[n] = L.own[n];
+                if (commit) L.own_prev[n] = now;
             }
             int tot;
             const int off = block_scan<kBB>(__popc(mask), &tot, s_scan);

@@ -193,6 +193,7 @@ struct BodyParams {
     int g_links;       // blocks of the link kernel for this body (fixed by the body alone)
     int g_box;         // blocks of the box kernels for this body
     int lat;           // index of the body's lattice
+    int copy_only;     // a still body whose force nobody reads: bounce-back is a plain copy
     double inv_mass, inv_inertia;
 };
 
@@ -209,7 +210,8 @@ struct BodyAcc {
     int box_lo[3];                    // scan box origin of the current classification
     double vsum[3], vesum;            // sums over the updates of v and of v.e (mobile spheres)
     long long nsum;                   // number of updates summed
-    int reclass;                      // re-classify this step (set by the update)
+    int reclass;                      // 1: re-classify the shell this step (set by the update);
+                                      // 2: classify the whole box (a body being added)
     int rel_flag;                     // queued for relinking this step
     long long link_count;
     int counter_links, counter_conv, counter_rebuild;  // last-block counters (self-resetting)

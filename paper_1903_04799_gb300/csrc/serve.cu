@@ -38,20 +38,20 @@ void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, cudaStream_t st)
 
 struct TileArgs {
     const Lattice* lats;
-    const int4* tiles;  // (lattice, z0, z1, paired)
-    const int* n_tiles;
+    const int4* tiles;  // (lattice, first unit, end unit, paired), sorted by storage
+    const int* n_tiles; // [5]: tiles of storage S are [n_tiles[S], n_tiles[S+1])
 };
 
+// A tile is the unit range [tile.y, tile.z) of one lattice, a unit being a cell
+// pair (paired tiles, nx even) or a cell, numbered x-fastest over the lattice.
 template <int P, int S>
 __device__ __forceinline__ void sweep_tile(const Lattice& L, const int4 tile) {
     const SweepArgs a = sweep_args(L, L.lambda_e, L.lambda_o);
-    const int per_row = tile.w ? L.nx / 2 : L.nx;
-    const unsigned rows = (unsigned)L.ny * (unsigned)(tile.z - tile.y);
-    const unsigned units = (unsigned)per_row * rows;
-    for (unsigned u = threadIdx.x; u < units; u += blockDim.x) {
-        const unsigned r = u / (unsigned)per_row;
-        const int xi = (int)(u - r * (unsigned)per_row);
-        const int y = (int)(r % (unsigned)L.ny), z = tile.y + (int)(r / (unsigned)L.ny);
+    const unsigned per_row = tile.w ? (unsigned)L.nx / 2 : (unsigned)L.nx;
+    for (unsigned u = (unsigned)tile.y + threadIdx.x; u < (unsigned)tile.z; u += blockDim.x) {
+        const unsigned r = u / per_row;
+        const int xi = (int)(u - r * per_row);
+        const int y = (int)(r % (unsigned)L.ny), z = (int)(r / (unsigned)L.ny);
         if constexpr (S != ST_F64) {
             if (tile.w) {
                 sweep_two<S, P>(a, 2 * xi, y, z);
@@ -62,25 +62,29 @@ __device__ __forceinline__ void sweep_tile(const Lattice& L, const int4 tile) {
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(256, 2) k_sweep_tiles(const TileArgs T) {
-    const int nt = *T.n_tiles;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+// One kernel per storage, so that none pays for another's registers; the
+// tile list is sorted by storage and n_tiles[S .. S+1] bounds storage S.
+template <int P, int S>
+__global__ void __launch_bounds__(256, S == ST_F64 ? 1 : 2) k_sweep_tiles(const TileArgs T) {
+    const int t0 = T.n_tiles[S], t1 = T.n_tiles[S + 1];
+    for (int t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
         const int4 tile = T.tiles[t];
         const Lattice& L = T.lats[tile.x];
-        if (!lattice_active(L)) continue;
-        switch (L.storage) {
-            case ST_F64: sweep_tile<P, ST_F64>(L, tile); break;
-            case ST_F32: sweep_tile<P, ST_F32>(L, tile); break;
-            case ST_F16: sweep_tile<P, ST_F16>(L, tile); break;
-            default: sweep_tile<P, ST_BF16>(L, tile); break;
-        }
+        if (lattice_active(L)) sweep_tile<P, S>(L, tile);
     }
 }
 
+template <int P>
+static void launch_tiles_p(const TileArgs& T, int grid, cudaStream_t st) {
+    k_sweep_tiles<P, ST_F64><<<grid, 256, 0, st>>>(T);
+    k_sweep_tiles<P, ST_F32><<<grid, 256, 0, st>>>(T);
+    k_sweep_tiles<P, ST_F16><<<grid, 256, 0, st>>>(T);
+    k_sweep_tiles<P, ST_BF16><<<grid, 256, 0, st>>>(T);
+}
+
 static void launch_tiles(const TileArgs& T, int parity, int grid, cudaStream_t st) {
-    if (parity == 0) k_sweep_tiles<0><<<grid, 256, 0, st>>>(T);
-    else k_sweep_tiles<1><<<grid, 256, 0, st>>>(T);
+    if (parity == 0) launch_tiles_p<0>(T, grid, st);
+    else launch_tiles_p<1>(T, grid, st);
 }
 
 }  // namespace lbsq
@@ -203,7 +207,7 @@ struct lb_server {
     int64_t next_ticket = 1;
     int64_t gstep = 0;
     double cell_updates = 0.0;
-    int tile_planes = 4, blocks_per_sm = 2;
+    int tile_units = 2048, blocks_per_sm = 2;
     cudaGraphExec_t graph = nullptr;
     std::string msg;
 };
@@ -259,7 +263,7 @@ std::vector<TableSpec> tables(lb_server* s) {
         {(void**)&s->d_rel_items, sizeof(int2) * s->list_cap},
         {(void**)&s->d_counts, sizeof(int) * 4},
         {(void**)&s->d_tiles, sizeof(int4) * s->tile_cap},
-        {(void**)&s->d_ntiles, sizeof(int) * 2},
+        {(void**)&s->d_ntiles, sizeof(int) * 5},
         {(void**)&s->d_gstep, sizeof(long long)},
         {(void**)&s->d_errs, sizeof(int) * s->cap_slots},
     };
@@ -353,6 +357,8 @@ std::vector<BodyParams> request_bodies(const lb_request& r, std::vector<BodyStat
         const double e0[3] = {0.0, 0.0, 1.0};
         sphere(r.obstacle, e0, r.obstacle[3], 0.0, 0.0, 0);
     }
+    // the walls and the obstacle are still and their forces are not reported
+    for (auto& b : v) b.copy_only = 1;
     sphere(r.pos, r.e, r.R, r.B1, r.beta, 1);
     for (auto& b : v) {
         const int64_t box = (int64_t)b.box_w[0] * b.box_w[1] * b.box_w[2];
@@ -415,7 +421,7 @@ lb_status admit(lb_server* s, int l, const Queued& q) {
     L.Np = (N + 63) / 64 * 64;
     L.storage = r.storage;
     L.rho0 = r.rho0;
-    L.scale = r.storage == LB_F16DEV ? std::ldexp(1.0f, 20) : 1.0f;
+    L.scale = r.storage == LB_F16DEV ? std::ldexp(1.0f, 14) : 1.0f;
     L.inv_scale = 1.0f / L.scale;
     L.own = (int32_t*)(s->arena.base + blocks[1].first);
     L.own_prev = (int32_t*)(s->arena.base + blocks[2].first);
@@ -465,7 +471,7 @@ lb_status admit(lb_server* s, int l, const Queued& q) {
                                 str));
             const int cnt[3] = {0, (int)items.size(), 0};
             SCK(cudaMemcpyAsync(s->d_counts + 1, cnt + 1, sizeof(int) * 2, cudaMemcpyHostToDevice, str));
-            launch_set_flags(s->d_acc, s->cap_bodies, k, 1, str);
+            launch_set_flags(s->d_acc, s->cap_bodies, k, 2, str);  // whole box
             launch_body_kernel(2, B, P, 1, std::max(1, std::min((int)items.size(), 4 * s->n_sm)), nullptr, str);
             SCK(cudaStreamSynchronize(str));  // item vector is transient
         }
@@ -544,6 +550,7 @@ lb_status fill_result(lb_server* s, int l, lb_result* out) {
 lb_status upload_mix(lb_server* s) {
     std::vector<int2> items;
     std::vector<int4> tiles;
+    int bounds[5] = {0, 0, 0, 0, 0};
     for (int l = 0; l < s->cap_slots; ++l) {
         const Slot& sl = s->slots[l];
         if (!sl.used) continue;
@@ -551,10 +558,19 @@ lb_status upload_mix(lb_server* s) {
             const int k = sl.L.body_begin + j;
             for (int g = 0; g < s->par[k].g_links; ++g) items.push_back(make_int2(k, g));
         }
-        const int paired = (sl.L.nx % 2 == 0 && sl.L.storage != LB_F64) ? 1 : 0;
-        for (int z0 = 0; z0 < sl.L.nz; z0 += s->tile_planes)
-            tiles.push_back(make_int4(l, z0, std::min(sl.L.nz, z0 + s->tile_planes), paired));
     }
+    for (int st = 0; st < 4; ++st) {  // tiles sorted by storage
+        bounds[st] = (int)tiles.size();
+        for (int l = 0; l < s->cap_slots; ++l) {
+            const Slot& sl = s->slots[l];
+            if (!sl.used || sl.L.storage != st) continue;
+            const int paired = (sl.L.nx % 2 == 0 && st != LB_F64) ? 1 : 0;
+            const int64_t units = paired ? sl.L.N / 2 : sl.L.N;
+            for (int64_t u0 = 0; u0 < units; u0 += s->tile_units)
+                tiles.push_back(make_int4(l, (int)u0, (int)std::min<int64_t>(units, u0 + s->tile_units), paired));
+        }
+    }
+    bounds[4] = (int)tiles.size();
     if ((int)items.size() > s->list_cap || (int)tiles.size() > s->tile_cap)
         return sfail(s, LB_ERR_CAPACITY, "work lists of the resident mix");
     if (!items.empty())
@@ -562,9 +578,9 @@ lb_status upload_mix(lb_server* s) {
                             s->stream));
     if (!tiles.empty())
         SCK(cudaMemcpyAsync(s->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s->stream));
-    const int ni = (int)items.size(), nt = (int)tiles.size();
+    const int ni = (int)items.size();
     SCK(cudaMemcpyAsync(s->d_counts, &ni, sizeof(int), cudaMemcpyHostToDevice, s->stream));
-    SCK(cudaMemcpyAsync(s->d_ntiles, &nt, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    SCK(cudaMemcpyAsync(s->d_ntiles, bounds, sizeof(bounds), cudaMemcpyHostToDevice, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
     return LB_OK;
 }
@@ -573,11 +589,11 @@ void enqueue_round(lb_server* s, cudaStream_t st) {
     const Bodies B = bodies_view(s, true);
     const TileArgs T = tile_args(s);
     const int grid = s->blocks_per_sm * s->n_sm;
-    const int gbox = 4 * s->n_sm;
+    const int glinks = 8 * s->n_sm, gbox = 4 * s->n_sm;  // latency-bound: many blocks
     for (int k = 0; k < s->p.round_steps; ++k) {
         const int P = k & 1;  // rounds start on even steps
         launch_tiles(T, P, grid, st);
-        for (int w = 1; w <= 4; ++w) launch_body_kernel(w, B, P, grid, gbox, nullptr, st);
+        for (int w = 1; w <= 4; ++w) launch_body_kernel(w, B, P, glinks, gbox, nullptr, st);
     }
 }
 
@@ -620,7 +636,7 @@ lb_status autotune(lb_server* s) {
         L.Np = Np;
         L.storage = storages[i];
         L.rho0 = 1.0;
-        L.scale = storages[i] == LB_F16DEV ? std::ldexp(1.0f, 20) : 1.0f;
+        L.scale = storages[i] == LB_F16DEV ? std::ldexp(1.0f, 14) : 1.0f;
         L.inv_scale = 1.0f / L.scale;
         L.lambda_e = 1.0;
         L.lambda_o = 8.0 / 7.0;
@@ -633,17 +649,20 @@ lb_status autotune(lb_server* s) {
     SCK(cudaEventCreate(&e0));
     SCK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_tz = s->tile_planes, best_b = s->blocks_per_sm;
-    const int tz_cand[4] = {1, 2, 4, 8}, b_cand[2] = {2, 4};
-    for (int tz : tz_cand)
+    int best_tu = s->tile_units, best_b = s->blocks_per_sm;
+    const int tu_cand[4] = {512, 1024, 2048, 4096}, b_cand[2] = {2, 4};
+    for (int tu : tu_cand)
         for (int bps : b_cand) {
+            // lattice 0 is FP32, lattice 1 FP16: tiles [0, m) and [m, 2m)
             std::vector<int4> tiles;
+            const int units = n * n * n / 2;
             for (int i = 0; i < 2; ++i)
-                for (int z0 = 0; z0 < n; z0 += tz) tiles.push_back(make_int4(i, z0, std::min(n, z0 + tz), 1));
+                for (int u0 = 0; u0 < units; u0 += tu) tiles.push_back(make_int4(i, u0, std::min(units, u0 + tu), 1));
+            const int m = (int)tiles.size() / 2;
+            const int bounds[5] = {0, 0, m, 2 * m, 2 * m};
             SCK(cudaMemcpyAsync(s->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice,
                                 s->stream));
-            const int nt = (int)tiles.size();
-            SCK(cudaMemcpyAsync(s->d_ntiles, &nt, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+            SCK(cudaMemcpyAsync(s->d_ntiles, bounds, sizeof(bounds), cudaMemcpyHostToDevice, s->stream));
             const TileArgs T = tile_args(s);
             for (int w = 0; w < 2; ++w) launch_tiles(T, w & 1, bps * s->n_sm, s->stream);
             SCK(cudaEventRecord(e0, s->stream));
@@ -654,7 +673,7 @@ lb_status autotune(lb_server* s) {
             SCK(cudaEventElapsedTime(&ms, e0, e1));
             if (ms < best) {
                 best = ms;
-                best_tz = tz;
+                best_tu = tu;
                 best_b = bps;
             }
         }
@@ -663,10 +682,10 @@ lb_status autotune(lb_server* s) {
     for (auto& b : blocks) s->arena.release(b.first, b.second);
     Lattice zero[2] = {};
     SCK(cudaMemcpyAsync(s->d_lats, zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream));
-    const int nt0 = 0;
-    SCK(cudaMemcpyAsync(s->d_ntiles, &nt0, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    const int nt0[5] = {0, 0, 0, 0, 0};
+    SCK(cudaMemcpyAsync(s->d_ntiles, nt0, sizeof(nt0), cudaMemcpyHostToDevice, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
-    s->tile_planes = best_tz;
+    s->tile_units = best_tu;
     s->blocks_per_sm = best_b;
     return LB_OK;
 }
@@ -682,13 +701,13 @@ void lb_server_params_default(lb_server_params* p) {
     p->hbm_budget_bytes = (size_t)8 << 30;
     p->max_resident = 64;
     p->round_steps = 64;
-    p->tile_planes = 0;
+    p->tile_units = 0;
 }
 
 lb_status lb_server_create(const lb_server_params* p, lb_server** out) {
     if (!p || !out) return LB_ERR_INVALID;
     if (p->max_resident < 1 || p->max_resident > 256 || p->round_steps < 2 || (p->round_steps & 1) ||
-        p->hbm_budget_bytes < ((size_t)1 << 20) || p->tile_planes < 0)
+        p->hbm_budget_bytes < ((size_t)1 << 20) || p->tile_units < 0)
         return LB_ERR_INVALID;
     lb_server* s = new (std::nothrow) lb_server();
     if (!s) return LB_ERR_OOM;
@@ -718,7 +737,7 @@ lb_status lb_server_create(const lb_server_params* p, lb_server** out) {
     }
     s->slots.resize(s->cap_slots);
     s->par.resize(s->cap_bodies);
-    if (p->tile_planes > 0) s->tile_planes = p->tile_planes;
+    if (p->tile_units > 0) s->tile_units = p->tile_units;
     else if (autotune(s) != LB_OK) return bail(LB_ERR_CUDA);
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return bail(LB_ERR_CUDA);
     *out = s;
@@ -855,10 +874,10 @@ lb_status lb_server_poll(lb_server* s, int64_t ticket, lb_result* out) {
     return sfail(s, LB_ERR_INVALID, "unknown ticket");
 }
 
-lb_status lb_server_info(const lb_server* s, int32_t* tile_planes, int32_t* blocks_per_sm, size_t* bytes_used,
+lb_status lb_server_info(const lb_server* s, int32_t* tile_units, int32_t* blocks_per_sm, size_t* bytes_used,
                          double* cell_updates) {
     if (!s) return LB_ERR_INVALID;
-    if (tile_planes) *tile_planes = s->tile_planes;
+    if (tile_units) *tile_units = s->tile_units;
     if (blocks_per_sm) *blocks_per_sm = s->blocks_per_sm;
     if (bytes_used) *bytes_used = s->arena.used;
     if (cell_updates) *cell_updates = s->cell_updates;

@@ -44,7 +44,7 @@ class lb_params(C.Structure):
 
 class lb_server_params(C.Structure):
     _fields_ = [("device", C.c_int32), ("stream", C.c_void_p), ("hbm_budget_bytes", C.c_size_t),
-                ("max_resident", C.c_int32), ("round_steps", C.c_int32), ("tile_planes", C.c_int32),
+                ("max_resident", C.c_int32), ("round_steps", C.c_int32), ("tile_units", C.c_int32),
                 ("allocator", C.POINTER(lb_allocator))]
 
 
@@ -362,7 +362,7 @@ def lb_server_info(srv):
     tz, bps, used, cu = C.c_int32(), C.c_int32(), C.c_size_t(), C.c_double()
     _scheck(srv, load().lb_server_info(srv, C.byref(tz), C.byref(bps), C.byref(used), C.byref(cu)),
             "lb_server_info")
-    return {"tile_planes": tz.value, "blocks_per_sm": bps.value, "bytes_used": used.value,
+    return {"tile_units": tz.value, "blocks_per_sm": bps.value, "bytes_used": used.value,
             "cell_updates": cu.value}
 
 
@@ -390,14 +390,14 @@ def make_request(geometry=0, shape=(32, 32, 32), storage="f32", collision="trt",
 class Server:
     """Many squirmer simulations resident on one GPU, advanced together."""
 
-    def __init__(self, budget_bytes=8 << 30, max_resident=64, round_steps=64, tile_planes=0, device=0,
+    def __init__(self, budget_bytes=8 << 30, max_resident=64, round_steps=64, tile_units=0, device=0,
                  use_torch=True):
         p = lb_server_params_default()
         p.device = int(device)
         p.hbm_budget_bytes = int(budget_bytes)
         p.max_resident = int(max_resident)
         p.round_steps = int(round_steps)
-        p.tile_planes = int(tile_planes)
+        p.tile_units = int(tile_units)
         self._stream = None
         self._alloc = None
         if use_torch:

@@ -37,7 +37,7 @@ def requests():
 
 
 def run_server(reqs, arrive_at_round, budget=1 << 30, max_resident=8, round_steps=16):
-    srv = Server(budget_bytes=budget, max_resident=max_resident, round_steps=round_steps, tile_planes=3)
+    srv = Server(budget_bytes=budget, max_resident=max_resident, round_steps=round_steps, tile_units=700)
     tickets = {}
     results = {}
     rnd = 0
@@ -98,7 +98,7 @@ def test_admission_waits_for_memory():
     start as memory frees up; all finish with their own results."""
     reqs = [make_request(0, (40, 40, 40), "f16dev", pos=(20.2, 19.9, 20.1), e=(0, 0, 1), R=4.0, B1=0.02,
                          beta=b, steps=40) for b in (-3.0, 0.0, 3.0)]
-    srv = Server(budget_bytes=int(5.5e6), max_resident=4, round_steps=16, tile_planes=2)
+    srv = Server(budget_bytes=int(5.5e6), max_resident=4, round_steps=16, tile_units=1024)
     tickets = [srv.submit(r) for r in reqs]
     running, queued = srv.advance()
     assert running == 1 and queued == 2
