@@ -304,6 +304,52 @@ def cpu_baseline(wl, budget_s=15.0):
             "kind": "oracle", "sample": f"{n} full time steps of {wl.name} after 1 warm-up step"}
 
 
+def precision_sweep(torch, device=0, steps=None):
+    """The 256^3 pusher (R = 16, beta = -3, B1 = 0.002) run 10 000 steps with
+    populations stored as FP64, FP32, FP16 and BF16 deviations (FP32 collision
+    for the last three).  Errors against the FP64 run: velocity field
+    ||u - u64|| / ||u64|| over cells fluid in both runs (final step);
+    stresslet ||S - S64||_F / ||S64||_F and swim speed |U - U64| / |U64|, both
+    averaged over the second half of the run.  The FP64 run stands in for the
+    FP64 oracle at this size: the two agree within 1e-12 on the parity tests."""
+    from paper_1903_04799_gb300 import workloads as W
+    wl = W.c3_pusher(steps=steps or 10000)
+    out, ref = {}, None
+    for st in ("f64", "f32", "f16dev", "bf16dev"):
+        g, ids = build_lattice(st, wl.shape, wl.bodies, wl.collision, wl.lambda_e, device)
+        S_acc, U_acc, n = np.zeros(6), 0.0, 0
+        chunk = 100
+        t0 = time.perf_counter()
+        for k in range(0, wl.steps, chunk):
+            g.step(chunk)
+            if k + chunk > wl.steps // 2:
+                S_acc += g.stresslet(ids[0])
+                _, v, e, _ = g.state(ids[0])
+                U_acc += float(v @ e)
+                n += 1
+        wall = time.perf_counter() - t0
+        _, u = g.fields()
+        own = g.owner()
+        g.close()
+        S, U = S_acc / n, U_acc / n
+        if st == "f64":
+            ref = (u, own, S, U)
+            out[st] = {"U_over_v0": U / (2 * 0.002 / 3), "S_zz": S[2], "wall_s": wall}
+            continue
+        both = (own == 0) & (ref[1] == 0)
+        du = u[:, both] - ref[0][:, both]
+        out[st] = {"u_l2_err": float(np.sqrt((du ** 2).sum() / (ref[0][:, both] ** 2).sum())),
+                   "stresslet_err": float(np.linalg.norm(S - ref[2]) / np.linalg.norm(ref[2])),
+                   "swim_speed_err": abs(U - ref[3]) / abs(ref[3]),
+                   "U_over_v0": U / (2 * 0.002 / 3), "wall_s": wall}
+    v0 = 2 * 0.002 / 3
+    eta = 1 / 6
+    # traction force dipole of a squirmer: -(12 pi / 5) eta R^2 B2 (e e - I/3)
+    S_closed = -(12 * np.pi / 5) * eta * 16 ** 2 * (-3 * 0.002) * 2 / 3
+    return {"workload": wl.name, "steps": wl.steps, "reference": "FP64 storage run (GPU)",
+            "stresslet_zz_closed_form": S_closed, "v0": v0, "storages": out}
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
@@ -476,11 +522,16 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--precision-sweep", action="store_true",
+                    help="run the 256^3 storage precision sweep (about 2 minutes) instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         reference(args)
+    elif args.precision_sweep:
+        import torch
+        print(json.dumps({"precision_sweep": precision_sweep(torch)}), flush=True)
     else:
         ours(args)
 

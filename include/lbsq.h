@@ -185,11 +185,15 @@ lb_status lb_get_force_torque(lb_ctx* c, int32_t id, double F[3], double T[3]);
 lb_status lb_get_object_state(lb_ctx* c, int32_t id, double pos[3], double vel[3], double e[3],
                               double omega[3]);
 
-/* Stresslet exerted on the fluid by body `id` in the last step:
- * S = -sum_links symtraceless(d (x) dF), d the link midpoint relative to
- * the centre and dF the momentum given to the body on that link; order
- * xx, yy, zz, xy, xz, yz.  The far field of Eq. "squirmerflow" gives
- * S = -4 pi eta R^2 B2 (e e - I/3).  Synchronises. */
+/* Force dipole the surface tractions of body `id` exert on the fluid in the
+ * last step: S = -sum_links symtraceless(d (x) dF), d the link midpoint
+ * relative to the centre and dF the momentum given to the body on that link;
+ * order xx, yy, zz, xy, xz, yz.  The paper defines no stresslet; this is the
+ * traction part of Batchelor's stresslet with the sign flipped (it leaves out
+ * the surface-velocity term -eta int(u n + n u) dA).  For the squirmer of
+ * Eq. "squirmerflow" in unbounded Stokes flow it is
+ * -(12 pi / 5) eta R^2 B2 (e e - I/3), eta = (1/lambda_e - 1/2) rho0 / 3.
+ * Synchronises. */
 lb_status lb_get_stresslet(lb_ctx* c, int32_t id, double S[6]);
 
 /* Mass sum(rho) and momentum sum(j) over fluid cells, FP64, summed in a

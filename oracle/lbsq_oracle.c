@@ -519,8 +519,10 @@ static void bounce_links(osim* s) {
                 o->Fbb[a] += dF[a];
                 o->Tbb[a] += dT[a];
             }
-            /* stresslet exerted on the fluid: minus the symmetric traceless
-             * first moment of the force on the body */
+            /* force dipole the tractions exert on the fluid: minus the
+             * symmetric traceless first moment of the force on the body (the
+             * traction part of Batchelor's stresslet, sign flipped; for a
+             * squirmer -(12 pi/5) eta R^2 B2 (e e - I/3)) */
             double tr = (d[0] * dF[0] + d[1] * dF[1] + d[2] * dF[2]) / 3.0;
             o->Sbb[0] -= d[0] * dF[0] - tr;
             o->Sbb[1] -= d[1] * dF[1] - tr;

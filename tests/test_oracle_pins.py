@@ -381,26 +381,33 @@ def test_swim_speed_matches_fig_resolution():
     assert abs(ratio / ref - 1) < 0.015, ratio
 
 
-def test_stresslet_sign_pusher_and_puller():
-    """Eq. "squirmerflow": the B2 term is a force dipole of strength
-    S = -4 pi eta R^2 B2 (e e - I/3) exerted on the fluid -- extensile
-    (S_zz > 0) for a pusher (beta < 0), contractile for a puller."""
-    R, L, B1 = 4, 24, 0.01
+def test_stresslet_traction_closed_form():
+    """The link sum S = -sum symtraceless(d (x) dF) is the force dipole the
+    surface tractions exert on the fluid.  Batchelor's stresslet of a body is
+    the traction moment minus eta * int(u n + n u) dA; for the squirmer of
+    Eq. "squirmerflow" the total is 4 pi eta R^2 B2 (e e - I/3) and the slip
+    velocity (B1 + B2 cos(theta)) (cos(theta) n - e) makes the second integral
+    -(8 pi / 5) eta R^2 B2 (e e - I/3) (only the B2 mode survives the
+    surface integral).  Hence S = -(12 pi / 5) eta R^2 B2 (e e - I/3): a
+    pusher (beta < 0) is extensile, a puller contractile.  R = 4 in a box of
+    12 R (confinement raises S by about 15 % at 6 R), tilted axes so that the
+    off-diagonal terms count; the whole tensor within 8 %."""
+    R, L, B1 = 4, 48, 0.002
     eta = 1 / 6
-    out = {}
-    for beta in (-5.0, 5.0):
+    for beta, e in ((-3.0, (0.6, 0.0, 0.8)), (3.0, (0.0, 0.6, 0.8))):
         s = O.OracleSim(L, L, L, lambda_e=1.0, collision="trt")
-        oid = s.add_sphere((L / 2, L / 2, L / 2), (0, 0, 1), R, B1=B1, beta=beta, mobile=True)
+        oid = s.add_sphere((L / 2 + 0.3, L / 2 - 0.2, L / 2 + 0.1), e, R, B1=B1, beta=beta, mobile=True)
         acc = np.zeros(6)
-        for k in range(600):
+        steps = 800
+        for k in range(steps):
             s.step(1)
-            if k >= 300:
+            if k >= steps // 2:
                 acc += s.stresslet(oid)
-        out[beta] = acc / 300
-    for beta, S in out.items():
-        exp_zz = -4 * math.pi * eta * R * R * beta * B1 * 2 / 3
-        assert np.sign(S[2]) == np.sign(exp_zz)
-        assert 0.5 < S[2] / exp_zz < 1.5, (beta, S)
+        S = acc / (steps - steps // 2)
+        _, _, ee, _ = s.state(oid)
+        Sm = np.array([[S[0], S[3], S[4]], [S[3], S[1], S[5]], [S[4], S[5], S[2]]])
+        form = -(12 * math.pi / 5) * eta * R * R * beta * B1 * (np.outer(ee, ee) - np.eye(3) / 3)
+        assert np.linalg.norm(Sm - form) < 0.08 * np.linalg.norm(form), (beta, Sm, form)
         assert abs(S[0] + S[1] + S[2]) < 1e-12  # traceless
 
 
