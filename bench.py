@@ -50,7 +50,7 @@ def peaks():
 
 def sweep_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("sweep.cu", "lbsq_internal.cuh"):
+    for f in ("sweep.cu", "sweep_body.cuh", "lbsq_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1903_04799_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/lbsq.h: context life cycle, validation,
 // device memory, body set-up and the per-step launch sequence (replayed from
-// a CUDA graph of two steps, even + odd, once the body set is fixed).
+// a CUDA graph of eight steps, starting on an even step, once the body set is
+// fixed).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -18,6 +19,8 @@ void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity
 void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, int grid_box, long long* step,
                         cudaStream_t st);
 void launch_body_step(const Bodies& B, int parity, int grid_links, int grid_box, long long* step, cudaStream_t st);
+void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st);
+cudaError_t prepare_body_kernels();
 void launch_fill_rest(const Lattice& L, cudaStream_t st);
 void launch_set_eq(const Lattice& L, const double* rho, const double* u, int q, cudaStream_t st);
 void launch_set_pop(const Lattice& L, const double* f, int q, cudaStream_t st);
@@ -61,8 +64,14 @@ struct lb_ctx {
     int2* d_link_items = nullptr;
     int2* d_box_items = nullptr;
     int2* d_rel_items = nullptr;
-    int* d_counts = nullptr;  // [0] link items, [1] box items, [2] relink items, [3] rebuild blocks done
+    int* d_counts = nullptr;  // [0] link items, [1] box items, [2] relink items, [3] rebuild blocks done,
+                              // [4..6] fused spheres per class, [7..9] first fused item per class
     int n_link_items = 0, list_cap = 0, list_alloc = 0;
+    // spheres advanced by the fused cluster kernel, and their shell stencils
+    int2* d_fused_items = nullptr;
+    uint32_t* d_stencil = nullptr;
+    int n_fused = 0, fused_cls = 0, fused_alloc = 0;
+    int64_t stencil_alloc = 0;
     int grid_box = 1;
     int n_sm = 152;
     Lattice* d_lat = nullptr;  // the one lattice descriptor on the device
@@ -175,6 +184,10 @@ Bodies bodies_view(const lb_ctx* c) {
     B.err = c->d_err;
     B.win = c->split ? c->d_win : nullptr;
     B.gstep = nullptr;
+    B.fused_items = c->d_fused_items;
+    B.n_fused = c->d_counts + 4;
+    B.fused_first = c->d_counts + 7;
+    B.stencil = c->d_stencil;
     return B;
 }
 
@@ -271,11 +284,22 @@ lb_status relayout(lb_ctx* c) {
     int64_t off = 0;
     int gl = 1, gb = 1, sum_gb = 0;
     std::vector<int2> items;
+    std::vector<int2> fused;
+    std::vector<uint32_t> stencil;
     for (int k = 0; k < nb; ++k) {
         BodyParams& b = c->par[k];
         b.link_off = off;
         off += b.link_cap;
         b.lat = 0;
+        b.st_off = 0;
+        b.st_count = 0;
+        if (fused_body(b)) {
+            const std::vector<uint32_t> v = shell_stencil(b.R);
+            b.st_off = (int64_t)stencil.size();
+            b.st_count = (int)v.size();
+            stencil.insert(stencil.end(), v.begin(), v.end());
+            fused.push_back(make_int2(k, 0));
+        }
         // block counts depend on the body alone (so do its fixed-order
         // reductions): about one link per thread of the link kernel, two box
         // cells per thread of the box kernels; capped by the shared staging
@@ -293,7 +317,28 @@ lb_status relayout(lb_ctx* c) {
         gl = std::max(gl, b.g_links);
         gb = std::max(gb, b.g_box);
         sum_gb += b.g_box;
-        for (int g = 0; g < b.g_links; ++g) items.push_back(make_int2(k, g));
+        if (!fused_body(b))
+            for (int g = 0; g < b.g_links; ++g) items.push_back(make_int2(k, g));
+    }
+    if ((int)fused.size() > c->fused_alloc) {
+        dfree(c, c->d_fused_items);
+        c->d_fused_items = dalloc_t<int2>(c, fused.size());
+        if (!c->d_fused_items) return fail(c, LB_ERR_OOM, "fused body list");
+        c->fused_alloc = (int)fused.size();
+    }
+    if ((int64_t)stencil.size() > c->stencil_alloc) {
+        dfree(c, c->d_stencil);
+        c->d_stencil = dalloc_t<uint32_t>(c, stencil.size());
+        if (!c->d_stencil) return fail(c, LB_ERR_OOM, "shell stencils");
+        c->stencil_alloc = (int64_t)stencil.size();
+    }
+    c->n_fused = (int)fused.size();
+    c->fused_cls = fused_class(c->n_fused);
+    if (!fused.empty()) {
+        CK(cudaMemcpyAsync(c->d_fused_items, fused.data(), sizeof(int2) * fused.size(), cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->d_stencil, stencil.data(), sizeof(uint32_t) * stencil.size(), cudaMemcpyHostToDevice,
+                           c->stream));
     }
     if (off > c->links_total) {
         dfree(c, c->d_links);
@@ -327,7 +372,8 @@ lb_status relayout(lb_ctx* c) {
     c->grid_box = std::max(1, std::min(sum_gb, 4 * c->n_sm));
     CK(cudaMemcpyAsync(c->d_link_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
                        c->stream));
-    const int counts[4] = {c->n_link_items, 0, 0, 0};
+    int counts[10] = {c->n_link_items, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    counts[4 + c->fused_cls] = c->n_fused;  // one lattice: one class, starting at item 0
     CK(cudaMemcpyAsync(c->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_par, c->par.data(), sizeof(BodyParams) * nb, cudaMemcpyHostToDevice, c->stream));
     // both state buffers hold the current state
@@ -448,6 +494,10 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
         cudaGetLastError();
         return bail(LB_ERR_CUDA);
     }
+    if (prepare_body_kernels() != cudaSuccess) {
+        cudaGetLastError();
+        return bail(LB_ERR_CUDA);
+    }
     if (p->stream) {
         c->stream = (cudaStream_t)p->stream;
     } else {
@@ -478,7 +528,7 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     c->d_err = dalloc_t<int>(c, 2);
     c->d_count = dalloc_t<int>(c, 2);
     c->d_lat = dalloc_t<Lattice>(c, 1);
-    c->d_counts = dalloc_t<int>(c, 4);
+    c->d_counts = dalloc_t<int>(c, 10);
     c->d_win = dalloc_t<int>(c, 4);
     int prio_lo = 0, prio_hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) return bail(LB_ERR_CUDA);
@@ -729,6 +779,24 @@ static void sweep_all(lb_ctx* c, int parity, cudaStream_t st) {
     launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, 0, nullptr, c->L.nz, st);
 }
 
+// The body kernels of one step on stream st: the fused kernel (spheres), the
+// link kernel (walls and still obstacles, if any), then classify, convert and
+// rebuild, which re-classify the spheres queued by the other two (bodies near
+// another body) and end the step.  Returns the launch count.
+static int body_step(lb_ctx* c, const Bodies& B, int parity, cudaStream_t st) {
+    int n = 0;
+    if (c->n_fused > 0) {
+        launch_body_fused(B, parity, c->fused_cls, c->n_fused, st);
+        n++;
+    }
+    if (c->n_link_items > 0) {
+        launch_body_kernel(1, B, parity, c->n_link_items, c->grid_box, nullptr, st);
+        n++;
+    }
+    for (int which = 2; which <= 4; ++which) launch_body_kernel(which, B, parity, c->n_link_items, c->grid_box, nullptr, st);
+    return n + 3;
+}
+
 // Traced step: each kernel between its own pair of events, no overlap.
 static void enqueue_traced_step(lb_ctx* c) {
     const int parity = (int)(c->step & 1);
@@ -736,12 +804,26 @@ static void enqueue_traced_step(lb_ctx* c) {
     for (int k = 0; k < nk; ++k) {
         const size_t e0 = 2 * c->ev_used.size();
         cudaEventRecord(pool_event(c, e0), c->stream);
-        if (k == 0) sweep_all(c, parity, c->stream);
-        else launch_body_kernel(k, bodies_view(c), parity, c->n_link_items, c->grid_box, nullptr, c->stream);
+        if (k == 0) {
+            sweep_all(c, parity, c->stream);
+            c->launches += 1;
+        } else if (k == 1) {
+            const Bodies B = bodies_view(c);
+            if (c->n_fused > 0) {
+                launch_body_fused(B, parity, c->fused_cls, c->n_fused, c->stream);
+                c->launches += 1;
+            }
+            if (c->n_link_items > 0) {
+                launch_body_kernel(1, B, parity, c->n_link_items, c->grid_box, nullptr, c->stream);
+                c->launches += 1;
+            }
+        } else {
+            launch_body_kernel(k, bodies_view(c), parity, c->n_link_items, c->grid_box, nullptr, c->stream);
+            c->launches += 1;
+        }
         cudaEventRecord(pool_event(c, e0 + 1), c->stream);
         c->ev_used.emplace_back(k, (int)e0);
     }
-    c->launches += nk;
     c->step++;
 }
 
@@ -770,18 +852,17 @@ static void enqueue_steps(lb_ctx* c, int64_t n) {
             cudaEventRecord(c->ev_fork, c->stream);
             cudaStreamWaitEvent(c->side, c->ev_fork, 0);
             cudaStreamWaitEvent(c->hi, c->ev_fork, 0);
-            launch_body_step(B, parity, c->n_link_items, c->grid_box, nullptr, c->hi);
+            c->launches += body_step(c, B, parity, c->hi);
             launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 1, win, c->L.nz, c->side);
             cudaEventRecord(c->ev_join, c->side);
             cudaEventRecord(c->ev_join2, c->hi);
             cudaStreamWaitEvent(c->stream, c->ev_join, 0);
             cudaStreamWaitEvent(c->stream, c->ev_join2, 0);
             launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 2, win, c->win_max, c->stream);
-            c->launches += 6;
+            c->launches += 2;
             swept = true;
         } else {
-            launch_body_step(B, parity, c->n_link_items, c->grid_box, nullptr, c->stream);
-            c->launches += 4;
+            c->launches += body_step(c, B, parity, c->stream);
         }
         c->step++;
     }

@@ -36,6 +36,8 @@
 // reductions add each value once (no shuffle trees over idle lanes).
 #include <cfloat>
 
+#include <cooperative_groups.h>
+
 #include "lbsq_internal.cuh"
 
 namespace lbsq {
@@ -193,22 +195,6 @@ __device__ __forceinline__ double wca_force(double r, double sigma, double eps) 
     return 24.0 * eps / r * (2.0 * sr6 * sr6 - sr6);
 }
 
-__device__ __forceinline__ void rotate_e(double* e, const double* w) {
-    const double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-    if (th == 0.0) return;
-    const double ith = 1.0 / th;
-    const double k[3] = {w[0] * ith, w[1] * ith, w[2] * ith};
-    double sn, c;
-    sincos(th, &sn, &c);
-    double kxe[3];
-    cross3(k, e, kxe);
-    const double ke = k[0] * e[0] + k[1] * e[1] + k[2] * e[2];
-    double r[3];
-    for (int a = 0; a < 3; ++a) r[a] = e[a] * c + kxe[a] * sn + k[a] * ke * (1.0 - c);
-    const double inr = 1.0 / sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    for (int a = 0; a < 3; ++a) e[a] = r[a] * inr;
-}
-
 __device__ __forceinline__ int wrap_pos(int a, int n) { return ((a % n) + n) % n; }
 
 __device__ __forceinline__ bool axis_overlap(int a, int wa, int b, int wb, int n) {
@@ -259,16 +245,20 @@ __device__ __forceinline__ CentreF centre_f(const BodyState& s) {
     return c;
 }
 
-// |d|^2 of node (x,y,z) from the centre in FP32 (minimum image); absolute
-// error below 2e-3 for |d| < 2^10.
+// |d|^2 of node (x,y,z) from the centre in FP32 (minimum image).  The node
+// offset k = x - floor(r) is wrapped as an integer first, so t = k - frac(r)
+// carries only the rounding of frac(r) to FP32 (2^-25) and of the difference
+// (|t| 2^-24): for nodes with every |t| <= T the error of |d|^2 is below
+// (15 T^2 + 3 T) 2^-24 (two roundings per square and sum, FMA or not).
 __device__ __forceinline__ float dist2_f(const Lattice& L, const CentreF& c, int x, int y, int z) {
     const int xi[3] = {x, y, z}, n3[3] = {L.nx, L.ny, L.nz};
     float s2 = 0.0f;
     for (int a = 0; a < 3; ++a) {
-        float t = (float)(xi[a] - c.ip[a]) - c.fp[a];
-        const float h = 0.5f * (float)n3[a];
-        if (t > h) t -= (float)n3[a];
-        else if (t <= -h) t += (float)n3[a];
+        int k = xi[a] - c.ip[a];
+        if (2 * k > n3[a]) k -= n3[a];
+        else if (2 * k <= -n3[a]) k += n3[a];
+        float t = (float)k - c.fp[a];
+        if (2.0f * t <= -(float)n3[a]) t += (float)n3[a];
         s2 += t * t;
     }
     return s2;
@@ -302,79 +292,165 @@ __device__ __forceinline__ void append_items(int2* items, int* count, int cap, i
 
 // ---------------------------------------------------------------- Newton-Euler
 
-// Symplectic Euler of body k (thread 0 of its last link block): applies the
-// momentum exchange of this step plus the conversion force booked by the last
-// remap, writes state[1-P], and decides whether a node can cross the surface.
+// Rare or long paths of the update, kept out of line so that the code a step
+// runs stays short (it is fetched cold every step).
+__device__ __noinline__ void rot_coeffs(double t2, double& sa, double& c1, double& c) {
+    const double th = sqrt(t2);
+    double sn;
+    sincos(th, &sn, &c);
+    sa = sn / th;
+    c1 = (1.0 - c) / t2;
+}
+
+__device__ __noinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+
+// WCA force on sphere k from the other bodies of its lattice (Eq. "wca").
 template <int P>
-__device__ void update_body(const Lattice& L, const Bodies& B, int k, const double* tot) {
-    const BodyParams& p = B.par[k];
-    const BodyState& s = B.state[P][k];
+__device__ __noinline__ void wca_sum(const Lattice& L, const Bodies& B, int k, const BodyParams& p,
+                                     const BodyState& s, double* fw) {
+    const int n3[3] = {L.nx, L.ny, L.nz};
+    for (int j = L.body_begin; j < L.body_begin + L.body_count; ++j) {
+        if (j == k) continue;
+        const BodyParams& q = B.par[j];
+        const BodyState& t = B.state[P][j];
+        if (q.kind == BODY_SPHERE) {
+            double dd[3];
+            for (int b = 0; b < 3; ++b) dd[b] = min_image(s.pos[b] - t.pos[b], n3[b]);
+            const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+            const double f = wca_force(dist - p.R - q.R, L.wca_sigma, L.wca_eps);
+            if (f != 0.0)
+                for (int b = 0; b < 3; ++b) fw[b] += f * dd[b] / dist;
+        } else {
+            const int ax = q.wall_axis;
+            const double dd = min_image(s.pos[ax] - (double)q.wall_index, n3[ax]);
+            const double f = wca_force(fabs(dd) - 0.5 - p.R, L.wca_sigma, L.wca_eps);
+            if (f != 0.0) fw[ax] += dd > 0.0 ? f : -f;
+        }
+    }
+}
+
+// Sum over lanes 0..2 of a value held per lane, as (x0 + x1) + x2 on every
+// lane (the same bits everywhere).
+__device__ __forceinline__ double sum3(double v) {
+    const double v0 = __shfl_sync(0xffffffffu, v, 0), v1 = __shfl_sync(0xffffffffu, v, 1),
+                 v2 = __shfl_sync(0xffffffffu, v, 2);
+    return (v0 + v1) + v2;
+}
+
+// Component b of a vector held as one component per lane 0..2.
+__device__ __forceinline__ double comp(double v, int b) { return __shfl_sync(0xffffffffu, v, b); }
+
+// Symplectic Euler of body k, by one whole warp (lane a < 3 holds vector
+// component a): applies the momentum exchange of this step plus the
+// conversion force booked by the last remap, writes state[1-P], and decides
+// whether a node can cross the surface.  Splitting the vectors over lanes
+// shortens the serial FP64 chain, which this GPU issues at a low rate.
+// p, s, Ai: the body's parameters, state of this step and accumulators (the
+// tables of B or copies of them); the results go to the tables of B.
+// If `out` is given, the new state and the re-classification flag are also
+// written there (lane a < 3: components a; lane 0: *out_reclass).
+template <int P>
+__device__ __noinline__ void update_body(const Lattice& L, const Bodies& B, int k, const BodyParams& p,
+                                         const BodyState& s, const BodyAcc& Ai, const double* tot,
+                                         BodyState* out = nullptr, int* out_reclass = nullptr) {
+    const int lane = threadIdx.x & 31;
+    const int a = lane < 3 ? lane : 0;  // lanes >= 3 shadow component 0 and store nothing
+    const bool own = lane < 3;
     BodyAcc& A = B.acc[k];
-    for (int a = 0; a < 3; ++a) {
+    const double Fa = tot[a] + Ai.Fc[a], Ta = tot[3 + a] + Ai.Tc[a];
+    const double rc = Ai.r_class[a], vs = Ai.vsum[a], ves = Ai.vesum;
+    const long long ns = Ai.nsum;
+    const unsigned long long mbits = Ai.margin_bits;
+    double v = s.vel[a], w = s.omega[a], x = s.pos[a], e = s.e[a];
+    __syncwarp();
+    if (own) {
         A.Fbb[a] = tot[a];
         A.Tbb[a] = tot[3 + a];
-    }
-    for (int a = 0; a < 6; ++a) A.Sbb[a] = tot[6 + a];
-    BodyState so = s;
-    for (int a = 0; a < 3; ++a) {
-        A.Fapp[a] = A.Fbb[a] + A.Fc[a];
-        A.Tapp[a] = A.Tbb[a] + A.Tc[a];
+        A.Sbb[a] = tot[6 + a];
+        A.Sbb[3 + a] = tot[9 + a];
+        A.Fapp[a] = Fa;
+        A.Tapp[a] = Ta;
         A.Fc[a] = 0.0;
         A.Tc[a] = 0.0;
     }
     int reclass = 0;
     if (p.kind == BODY_SPHERE && p.mobile) {
         const int n3[3] = {L.nx, L.ny, L.nz};
-        double Fw[3] = {0.0, 0.0, 0.0};
+        double Fw = 0.0;  // WCA contact force, component a
         if (L.wca_eps != 0.0) {
-            for (int j = L.body_begin; j < L.body_begin + L.body_count; ++j) {
-                if (j == k) continue;
-                const BodyParams& q = B.par[j];
-                const BodyState& t = B.state[P][j];
-                if (q.kind == BODY_SPHERE) {
-                    double dd[3];
-                    for (int a = 0; a < 3; ++a) dd[a] = min_image(s.pos[a] - t.pos[a], n3[a]);
-                    const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-                    const double f = wca_force(dist - p.R - q.R, L.wca_sigma, L.wca_eps);
-                    if (f != 0.0)
-                        for (int a = 0; a < 3; ++a) Fw[a] += f * dd[a] / dist;
-                } else {
-                    const int ax = q.wall_axis;
-                    const double dd = min_image(s.pos[ax] - (double)q.wall_index, n3[ax]);
-                    const double f = wca_force(fabs(dd) - 0.5 - p.R, L.wca_sigma, L.wca_eps);
-                    if (f != 0.0) Fw[ax] += dd > 0.0 ? f : -f;
-                }
+            double fw[3] = {0.0, 0.0, 0.0};
+            if (lane == 0) wca_sum<P>(L, B, k, p, s, fw);
+            const double f0 = __shfl_sync(0xffffffffu, fw[0], 0), f1 = __shfl_sync(0xffffffffu, fw[1], 0),
+                         f2 = __shfl_sync(0xffffffffu, fw[2], 0);
+            Fw = a == 0 ? f0 : (a == 1 ? f1 : f2);
+        }
+        v = v + (Fa + Fw) * p.inv_mass;
+        w = w + Ta * p.inv_inertia;
+        x = x + v;
+        if (x >= (double)n3[a]) x -= (double)n3[a];
+        else if (x < 0.0) x += (double)n3[a];
+        // Rotation of e about w by the angle th = |w| (Rodrigues), renormalised:
+        //   e' = e cos(th) + (w x e) sin(th)/th + w (w.e) (1 - cos(th))/th^2.
+        // A body turns by far less than 0.01 rad per step, where the Taylor
+        // series of sin(th)/th and (1 - cos(th))/th^2 to th^8 are exact in
+        // FP64 (the first omitted terms are below 3e-28); larger angles use
+        // sincos.  1/sqrt(n2) for n2 within 1e-8 of 1 is one Newton step from 1
+        // (relative error 3/8 (n2 - 1)^2, below 4e-17).
+        const double t2 = sum3(w * w);
+        if (t2 != 0.0) {
+            double sa, c1, c;
+            if (t2 < 1e-4) {
+                sa = 1.0 + t2 * (-1.0 / 6.0 + t2 * (1.0 / 120.0 + t2 * (-1.0 / 5040.0 + t2 * (1.0 / 362880.0))));
+                c1 = 0.5 + t2 * (-1.0 / 24.0 + t2 * (1.0 / 720.0 + t2 * (-1.0 / 40320.0 + t2 * (1.0 / 3628800.0))));
+                c = 1.0 - t2 * c1;
+            } else {
+                rot_coeffs(t2, sa, c1, c);
             }
+            const int a1 = a == 2 ? 0 : a + 1, a2 = a == 0 ? 2 : a - 1;
+            const double wxe = comp(w, a1) * comp(e, a2) - comp(w, a2) * comp(e, a1);
+            const double we = sum3(w * e);
+            const double r = e * c + wxe * sa + w * (we * c1);
+            const double n2 = sum3(r * r);
+            const double inr = fabs(n2 - 1.0) < 1e-8 ? 1.5 - 0.5 * n2 : inv_sqrt(n2);
+            e = r * inr;
         }
-        for (int a = 0; a < 3; ++a) {
-            so.vel[a] = s.vel[a] + (A.Fapp[a] + Fw[a]) * p.inv_mass;
-            so.omega[a] = s.omega[a] + A.Tapp[a] * p.inv_inertia;
+        const double ve = sum3(v * e), sp = sum3(v * v);
+        const double dd = min_image(x - rc, n3[a]);
+        const double disp2 = sum3(dd * dd);
+        __syncwarp();
+        if (own) A.vsum[a] = vs + v;
+        if (lane == 0) {
+            A.vesum = ves + ve;
+            A.nsum = ns + 1;
+            if (!(sp < 0.25)) set_error(L.err, 5);
         }
-        for (int a = 0; a < 3; ++a) {
-            double q = s.pos[a] + so.vel[a];
-            if (q >= (double)n3[a]) q -= (double)n3[a];
-            else if (q < 0.0) q += (double)n3[a];
-            so.pos[a] = q;
-        }
-        rotate_e(so.e, so.omega);
-        for (int a = 0; a < 3; ++a) A.vsum[a] += so.vel[a];
-        A.vesum += so.vel[0] * so.e[0] + so.vel[1] * so.e[1] + so.vel[2] * so.e[2];
-        A.nsum += 1;
-        const double sp = so.vel[0] * so.vel[0] + so.vel[1] * so.vel[1] + so.vel[2] * so.vel[2];
-        if (!(sp < 0.25)) set_error(L.err, 5);
         // Node crossing test: every node of the box kept its side of the surface
         // if the centre moved less than the distance of the nearest node to the
         // surface at the last classification (less a 1e-9 guard, far above the
         // FP64 error of the inside test).
-        double dd[3];
-        for (int a = 0; a < 3; ++a) dd[a] = min_image(so.pos[a] - A.r_class[a], n3[a]);
-        const double disp = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-        const double margin = __longlong_as_double((long long)A.margin_bits);
-        reclass = !(disp < margin - 1e-9);
-        if (reclass) A.margin_bits = (unsigned long long)__double_as_longlong(DBL_MAX);
+        const double mg = __longlong_as_double((long long)mbits) - 1e-9;
+        reclass = !(mg > 0.0 && disp2 < mg * mg);
+        __syncwarp();
+        if (reclass && lane == 0) A.margin_bits = (unsigned long long)__double_as_longlong(DBL_MAX);
     }
-    A.reclass = reclass;
-    B.state[1 - P][k] = so;
+    BodyState& so = B.state[1 - P][k];
+    if (own) {
+        so.pos[a] = x;
+        so.vel[a] = v;
+        so.omega[a] = w;
+        so.e[a] = e;
+        if (out) {
+            out->pos[a] = x;
+            out->vel[a] = v;
+            out->omega[a] = w;
+            out->e[a] = e;
+        }
+    }
+    if (lane == 0) {
+        A.reclass = reclass;
+        if (out_reclass) *out_reclass = reclass;
+    }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------- k_links
@@ -407,8 +483,34 @@ __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p
         }
     }
     const float B1f = (float)p.B1, B2f = (float)p.B2, shf = (float)(6.0 * L.rho0);
-    for (long long l = (long long)g * blockDim.x + threadIdx.x; l < cnt; l += (long long)G * blockDim.x) {
-        const uint32_t code = links[l];
+    // A thread's links are taken kU at a time: the link codes, then the
+    // outgoing populations of all kU are loaded before any arithmetic or
+    // store, so their memory latencies overlap.
+    constexpr int kU = 2;
+    const long long stride = (long long)G * blockDim.x;
+    for (long long l0 = (long long)g * blockDim.x + threadIdx.x; l0 < cnt; l0 += kU * stride) {
+    uint32_t codes[kU];
+    double fouts[kU];
+    float gouts[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) codes[u] = l0 + u * stride < cnt ? links[l0 + u * stride] : 0u;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        if (l0 + u * stride >= cnt) continue;
+        const int64_t n = codes[u] >> 5;
+        const int i = codes[u] & 31;
+        int x, y, z;
+        cell_coords(L, n, x, y, z);
+        const int64_t ns =
+            cell_index(L, step_wrap(x, cx(i), L.nx), step_wrap(y, cy(i), L.ny), step_wrap(z, cz(i), L.nz));
+        const int64_t out_slot = P == 0 ? (int64_t)opp(i) * Np + n : (int64_t)i * Np + ns;
+        if (DP || !sphere) fouts[u] = load_abs(L, out_slot, i);
+        else gouts[u] = load_dev(L, out_slot);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        if (l0 + u * stride >= cnt) continue;
+        const uint32_t code = codes[u];
         const int64_t n = code >> 5;
         const int i = code & 31, ib = opp(i);
         const int ci[3] = {cx(i), cy(i), cz(i)};
@@ -416,12 +518,11 @@ __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p
         cell_coords(L, n, x, y, z);
         const int64_t ns =
             cell_index(L, step_wrap(x, ci[0], L.nx), step_wrap(y, ci[1], L.ny), step_wrap(z, ci[2], L.nz));
-        // where sweep P left f*_i of the fluid node, and where the next sweep
-        // reads the reflected population f_ib of the fluid node
-        const int64_t out_slot = P == 0 ? (int64_t)ib * Np + n : (int64_t)i * Np + ns;
+        // where sweep P left f*_i of the fluid node (loaded above), and where
+        // the next sweep reads the reflected population f_ib of the fluid node
         const int64_t in_slot = P == 0 ? (int64_t)i * Np + ns : (int64_t)ib * Np + n;
         if (DP || !sphere) {
-            const double fout = load_abs(L, out_slot, i);
+            const double fout = fouts[u];
             double vb[3], d[3];
             if (sphere) {
                 // link midpoint relative to the centre; rigid motion + slip there
@@ -468,7 +569,7 @@ __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p
             }
         } else {
             // FP32 path (reduced storage, sphere): deviations g = f - w rho0
-            const float gout = load_dev(L, out_slot);
+            const float gout = gouts[u];
             float d[3];
             const int xi[3] = {x, y, z};
             const int n3[3] = {L.nx, L.ny, L.nz};
@@ -517,6 +618,7 @@ __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p
 #pragma unroll
             for (int c = 0; c < 12; ++c) acc[c] += (double)t12[c];
         }
+    }
     }
 }
 
@@ -574,14 +676,138 @@ __global__ void __launch_bounds__(kLB) k_links(const Bodies B) {
         if (threadIdx.x < 12) part[threadIdx.x] = s_tot[threadIdx.x];
         if (!last_block(&A.counter_links, G, &s_flag)) continue;
         ordered_partial_sum<12>(B.part_links + (size_t)k * B.GL * 12, G, sm, s_tot);
-        if (threadIdx.x == 0) {
-            update_body<P>(L, B, k, s_tot);
-            s_flag = A.reclass;
-        }
+        if (threadIdx.x < 32) update_body<P>(L, B, k, p, B.state[P][k], A, s_tot);
+        __syncthreads();
+        if (threadIdx.x == 0) s_flag = A.reclass;
         __syncthreads();
         if (s_flag) append_items(B.box_items, B.n_box, B.box_cap, k, p.g_box, B.err, (int*)sm);
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------- per-cell steps
+// Shared by the multi-kernel path (k_classify, k_convert, k_rebuild) and the
+// fused cluster kernel, so that both take the same decisions cell by cell.
+// CG = true: owner and population reads go through L2 (another block of the
+// same launch may have written them).
+
+// New owner of shell node (x, y, z) of sphere id (s = its new state; s32 its
+// FP32 |d|^2).  Nodes farther than `band` from the surface in FP32 are
+// decided in FP32, the rest by the exact FP64 test.  Returns a lower bound of
+// the node's distance to the surface: FP32 offsets and square root (absolute
+// error below 1e-4 for |d| < 2^10) minus 1e-3.
+// Whether node (x, y, z) is inside the sphere of radius R centred at pos
+// (s32: the node's FP32 |d|^2 from dist2_f, band: band_of(R)).  Nodes
+// farther than the band from the surface are decided in FP32 (the FP32 error
+// is less than half the band there), the rest by the exact FP64 test, so the
+// result equals the exact test for every node.
+__device__ __noinline__ bool inside_exact(int nx, int ny, int nz, const double* pos, double R, int x, int y, int z) {
+    const double dx = min_image((double)x - pos[0], nx);
+    const double dy = min_image((double)y - pos[1], ny);
+    const double dz = min_image((double)z - pos[2], nz);
+    return inside_sphere(dx, dy, dz, R);
+}
+
+__device__ __forceinline__ bool inside_node(const Lattice& L, const double pos[3], double R, float s32, float R2f,
+                                            float band, int x, int y, int z) {
+    if (fabsf(s32 - R2f) > band) return s32 < R2f;
+    return inside_exact(L.nx, L.ny, L.nz, pos, R, x, y, z);  // rare: out of line
+}
+
+// Half-width of the band around R^2 in which inside_node falls back to the
+// exact test, for a sphere of radius R: twice the dist2_f error bound for
+// nodes with |t| <= R + 3 plus the rounding of R^2 to FP32.  Nodes farther
+// out are outside the sphere whatever the rounding.
+__device__ __forceinline__ float band_of(float R) {
+    const float T = R + 3.0f;
+    return 3e-6f * T * T + 1e-5f;
+}
+
+template <bool CG>
+__device__ __forceinline__ float classify_cell(const Lattice& L, const BodyParams& p, const BodyState& s, int id,
+                                               int x, int y, int z, float s32, float R2f, float band) {
+    const int64_t n = cell_index(L, x, y, z);
+    const bool in = inside_node(L, s.pos, p.R, s32, R2f, band, x, y, z);
+    const int old = ld<CG>(L.own_prev + n);
+    if (in) {
+        if (old == 0) {
+            const int r = atomicCAS(&L.own[n], 0, id);
+            if (r != 0 && r != id) set_error(L.err, 4);
+        } else if (old != id) {
+            set_error(L.err, 4);
+        }
+    } else if (old == id) {
+        L.own[n] = 0;
+    }
+    const float dist = sqrtf(s32);
+    return fmaxf(fabsf(dist - (float)p.R) - 1e-3f, 0.0f);
+}
+
+// Momentum of the populations of node (x, y, z) (read slots of parity q)
+// and its moment about the centre, added to acc: what a node the body covers
+// gives to the body.  Out of line: rare, and long in FP64.
+template <bool CG>
+__device__ __noinline__ void covered_momentum(const Lattice& L, const BodyState& s, int x, int y, int z, int q,
+                                              double* acc) {
+    double m[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) {
+        const double fi = load_abs<CG>(L, read_slot(L, i, x, y, z, q), i);
+        m[0] += fi * cx(i);
+        m[1] += fi * cy(i);
+        m[2] += fi * cz(i);
+    }
+    const double d[3] = {min_image((double)x - s.pos[0], L.nx), min_image((double)y - s.pos[1], L.ny),
+                         min_image((double)z - s.pos[2], L.nz)};
+    double t[3];
+    cross3(d, m, t);
+    for (int a = 0; a < 3; ++a) {
+        acc[a] += m[a];
+        acc[3 + a] += t[a];
+    }
+}
+
+// Conversion at node (x, y, z) after the re-classification of sphere id
+// (conv: whether it re-classified; q: parity of the next sweep).  A node the
+// sphere covered gives its momentum (and its torque about the centre) to acc;
+// returns 1 for a node it uncovered (refilled by the caller).  Counts into
+// lcount the links from this node, if fluid, to the sphere.
+template <bool CG>
+__device__ __forceinline__ int convert_cell(const Lattice& L, const BodyState& s, int id, int x, int y, int z, int q,
+                                            bool conv, double (&acc)[6], long long& lcount) {
+    const int64_t n = cell_index(L, x, y, z);
+    const int now = ld<CG>(L.own + n);
+    int uncover = 0;
+    if (conv) {
+        const int was = ld<CG>(L.own_prev + n);
+        if (was == 0 && now == id) {
+            covered_momentum<CG>(L, s, x, y, z, q, acc);  // fluid -> solid: to the body
+        } else if (was == id && now == 0) {
+            uncover = 1;
+        }
+    }
+    if (now == 0)
+        for (int i = 1; i < Q; ++i) {
+            const int64_t nn =
+                cell_index(L, step_wrap(x, cx(i), L.nx), step_wrap(y, cy(i), L.ny), step_wrap(z, cz(i), L.nz));
+            lcount += ld<CG>(L.own + nn) == id;
+        }
+    return uncover;
+}
+
+// Directions i of the links from fluid node (x, y, z) (owner `now`) to
+// sphere id, as a bit mask.
+template <bool CG>
+__device__ __forceinline__ uint32_t link_mask(const Lattice& L, int x, int y, int z, int id, int now) {
+    uint32_t mask = 0;
+    if (now == 0) {
+        for (int i = 1; i < Q; ++i) {
+            const int64_t nn =
+                cell_index(L, step_wrap(x, cx(i), L.nx), step_wrap(y, cy(i), L.ny), step_wrap(z, cz(i), L.nz));
+            if (ld<CG>(L.own + nn) == id) mask |= 1u << i;
+        }
+    }
+    return mask;
 }
 
 // ---------------------------------------------------------------- k_classify
@@ -635,10 +861,9 @@ __global__ void __launch_bounds__(kBB) k_classify(const Bodies B) {
         const CentreF cf = centre_f(s);
         const float R2f = (float)(p.R * p.R), Rf = (float)p.R;
         const bool full = A.reclass == 2;  // first classification of a new body
-        // |FP32 |d|^2 - exact| < 2e-3 for every node of a box in a lattice
-        // below 2^15 per axis; nodes farther than this band from the surface
-        // are decided in FP32, the rest by the exact FP64 test
-        const float band = 1e-3f * R2f + 1e-2f;
+        // nodes farther than the band from the surface are decided in FP32,
+        // the rest by the exact FP64 test (see inside_node)
+        const float band = band_of(Rf);
         float mloc = FLT_MAX;
         for (long long b = b0 + threadIdx.x; b < b1; b += kBB) {
             int x, y, z;
@@ -647,31 +872,7 @@ __global__ void __launch_bounds__(kBB) k_classify(const Bodies B) {
             // nodes well inside or well outside kept their side since the last
             // classification (a body moves less than half a node per step)
             if (!full && !in_shell(s32, Rf)) continue;
-            const int64_t n = cell_index(L, x, y, z);
-            bool in;
-            if (fabsf(s32 - R2f) > band) {
-                in = s32 < R2f;
-            } else {
-                const double dx = min_image((double)x - s.pos[0], L.nx);
-                const double dy = min_image((double)y - s.pos[1], L.ny);
-                const double dz = min_image((double)z - s.pos[2], L.nz);
-                in = inside_sphere(dx, dy, dz, p.R);
-            }
-            const int old = L.own_prev[n];
-            if (in) {
-                if (old == 0) {
-                    const int r = atomicCAS(&L.own[n], 0, id);
-                    if (r != 0 && r != id) set_error(L.err, 4);
-                } else if (old != id) {
-                    set_error(L.err, 4);
-                }
-            } else if (old == id) {
-                L.own[n] = 0;
-            }
-            // distance of the node to the surface, as a lower bound: FP32 offsets
-            // and square root (absolute error below 1e-4 for |d| < 2^10) minus 1e-3
-            const float dist = sqrtf(s32);
-            mloc = fminf(mloc, fmaxf(fabsf(dist - (float)p.R) - 1e-3f, 0.0f));
+            mloc = fminf(mloc, classify_cell<false>(L, p, s, id, x, y, z, s32, R2f, band));
         }
         // block minimum (FP32 values, exact)
 #pragma unroll
@@ -689,26 +890,24 @@ __global__ void __launch_bounds__(kBB) k_classify(const Bodies B) {
 
 // ---------------------------------------------------------------- k_convert
 
-// Refill of one uncovered cell by one warp: lane l = 1..18 reads the density of
-// neighbour l (if fluid now and before), the neighbour densities are summed in
-// lane order; lanes 0..18 write the equilibrium of population l.  The created
-// momentum (taken from the body) is added to acc of lane 0.
-__device__ __forceinline__ void refill_cell(const Lattice& L, const BodyState& s, int x, int y, int z, int q,
-                                            double* acc) {
+// 1/k for k = 1..18, correctly rounded (the mean of k neighbour densities is
+// their sum times 1/k, within an ulp of the quotient).
+__constant__ double kInvCount[19] = {0.0,       1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,
+                                     1.0 / 7,   1.0 / 8,    1.0 / 9,  1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13,
+                                     1.0 / 14,  1.0 / 15,   1.0 / 16, 1.0 / 17, 1.0 / 18};
+
+// Second half of a refill (shared by refill_cell and geo_refill): lane l
+// holds the density r of neighbour l and whether it counts (valid).  The
+// neighbour densities are summed in lane order; lanes 0..18 write the
+// equilibrium of population l at the mean density and the rigid-body
+// velocity there.  The created momentum (taken from the body) is added to acc
+// of lane 0.
+__device__ __noinline__ void refill_finish(const Lattice& L, const BodyState& s, int x, int y, int z, int q,
+                                              double r, int valid, double* acc) {
     const int lane = threadIdx.x & 31;
-    double r = 0.0;
-    int valid = 0;
-    if (lane >= 1 && lane < Q) {
-        const int xn = step_wrap(x, cx(lane), L.nx), yn = step_wrap(y, cy(lane), L.ny),
-                  zn = step_wrap(z, cz(lane), L.nz);
-        const int64_t nn = cell_index(L, xn, yn, zn);
-        if (L.own[nn] == 0 && L.own_prev[nn] == 0) {
-            valid = 1;
-            for (int j = 0; j < Q; ++j) r += load_abs(L, read_slot(L, j, xn, yn, zn, q), j);
-        }
-    }
     double sum = 0.0;
     int cnt = 0;
+#pragma unroll 1
     for (int l = 1; l < Q; ++l) {
         const double rl = __shfl_sync(0xffffffffu, r, l);
         const int vl = __shfl_sync(0xffffffffu, valid, l);
@@ -717,7 +916,7 @@ __device__ __forceinline__ void refill_cell(const Lattice& L, const BodyState& s
             cnt++;
         }
     }
-    const double rb = cnt > 0 ? sum / (double)cnt : L.rho0;
+    const double rb = cnt > 0 ? sum * kInvCount[cnt] : L.rho0;
     const double d[3] = {min_image((double)x - s.pos[0], L.nx), min_image((double)y - s.pos[1], L.ny),
                          min_image((double)z - s.pos[2], L.nz)};
     double wd[3];
@@ -731,6 +930,7 @@ __device__ __forceinline__ void refill_cell(const Lattice& L, const BodyState& s
         store_abs(L, read_slot(L, lane, x, y, z, q), lane, fi);
     }
     double m[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
     for (int l = 0; l < Q; ++l) {
         const double fl = __shfl_sync(0xffffffffu, fi, l);
         m[0] += fl * cx(l);
@@ -745,6 +945,27 @@ __device__ __forceinline__ void refill_cell(const Lattice& L, const BodyState& s
             acc[3 + a] -= t[a];
         }
     }
+}
+
+// Refill of one uncovered cell by one warp: lane l = 1..18 reads the density of
+// neighbour l (if fluid now and before); see refill_finish.
+template <bool CG>
+__device__ __noinline__ void refill_cell(const Lattice& L, const BodyState& s, int x, int y, int z, int q,
+                                            double* acc) {
+    const int lane = threadIdx.x & 31;
+    double r = 0.0;
+    int valid = 0;
+    if (lane >= 1 && lane < Q) {
+        const int xn = step_wrap(x, cx(lane), L.nx), yn = step_wrap(y, cy(lane), L.ny),
+                  zn = step_wrap(z, cz(lane), L.nz);
+        const int64_t nn = cell_index(L, xn, yn, zn);
+        if (ld<CG>(L.own + nn) == 0 && ld<CG>(L.own_prev + nn) == 0) {
+            valid = 1;
+#pragma unroll 1
+            for (int j = 0; j < Q; ++j) r += load_abs<CG>(L, read_slot(L, j, xn, yn, zn, q), j);
+        }
+    }
+    refill_finish(L, s, x, y, z, q, r, valid, acc);
 }
 
 template <int P>
@@ -782,40 +1003,7 @@ __global__ void __launch_bounds__(kBB) k_convert(const Bodies B) {
                 box_cell(L, lo, w, b, x, y, z);
                 if (sphere) take = in_shell(dist2_f(L, cf, x, y, z), Rf);
             }
-            if (take) {
-                const int64_t n = cell_index(L, x, y, z);
-                const int now = L.own[n];
-                if (conv) {
-                    const int was = L.own_prev[n];
-                    if (was == 0 && now == id) {
-                        // fluid -> solid: the destroyed momentum goes to the body
-                        double m[3] = {0.0, 0.0, 0.0};
-                        for (int i = 0; i < Q; ++i) {
-                            const double fi = load_abs(L, read_slot(L, i, x, y, z, q), i);
-                            m[0] += fi * cx(i);
-                            m[1] += fi * cy(i);
-                            m[2] += fi * cz(i);
-                        }
-                        const double d[3] = {min_image((double)x - s.pos[0], L.nx),
-                                             min_image((double)y - s.pos[1], L.ny),
-                                             min_image((double)z - s.pos[2], L.nz)};
-                        double t[3];
-                        cross3(d, m, t);
-                        for (int a = 0; a < 3; ++a) {
-                            acc[a] += m[a];
-                            acc[3 + a] += t[a];
-                        }
-                    } else if (was == id && now == 0) {
-                        uncover = 1;
-                    }
-                }
-                if (now == 0)
-                    for (int i = 1; i < Q; ++i) {
-                        const int64_t nn = cell_index(L, step_wrap(x, cx(i), L.nx), step_wrap(y, cy(i), L.ny),
-                                                      step_wrap(z, cz(i), L.nz));
-                        lcount += L.own[nn] == id;
-                    }
-            }
+            if (take) uncover = convert_cell<false>(L, s, id, x, y, z, q, conv, acc, lcount);
             // solid -> fluid cells of this round, in thread order, refilled by warps
             int nu;
             const int pos = block_scan<kBB>(uncover, &nu, s_scan);
@@ -824,7 +1012,7 @@ __global__ void __launch_bounds__(kBB) k_convert(const Bodies B) {
             for (int u = threadIdx.x >> 5; u < nu; u += kBB / 32) {
                 int ux, uy, uz;
                 box_cell(L, lo, w, b0 + s_list[u], ux, uy, uz);
-                refill_cell(L, s, ux, uy, uz, q, acc);
+                refill_cell<false>(L, s, ux, uy, uz, q, acc);
             }
             __syncthreads();
         }
@@ -960,13 +1148,7 @@ __global__ void __launch_bounds__(kBB) k_rebuild(const Bodies B) {
             if (take) {
                 n = cell_index(L, x, y, z);
                 const int now = L.own[n];
-                if (now == 0) {
-                    for (int i = 1; i < Q; ++i) {
-                        const int64_t nn = cell_index(L, step_wrap(x, cx(i), L.nx), step_wrap(y, cy(i), L.ny),
-                                                      step_wrap(z, cz(i), L.nz));
-                        if (L.own[nn] == id) mask |= 1u << i;
-                    }
-                }
+                mask = link_mask<false>(L, x, y, z, id, now);
                 if (commit) L.own_prev[n] = now;
             }
             int tot;
@@ -1005,6 +1187,378 @@ __global__ void k_tick(int* n_box, int* n_rel, long long* step) {
     if (step) *step += 1;
 }
 
+// ---------------------------------------------------------------- k_body_fused
+
+// The whole body step of one sphere in one launch: one thread-block cluster
+// per sphere runs the phases of k_links, k_classify, k_convert and k_rebuild
+// back to back, separated by cluster barriers, and combines its blocks'
+// partial sums through distributed shared memory (rank order, fixed).  The
+// scan covers the sphere's shell stencil instead of its whole box: the
+// offsets o from the centre's node floor(r) for which some centre fraction
+// f in [0,1]^3 puts |o - f| within the shell R - 1.5 .. R + 2 (with margin),
+// in box order (z, y, x), so the link list comes out in the same canonical
+// order as from the box scan.
+//
+// A sphere whose box, grown by one cell, meets another body's grown box at
+// the start of the step (the cells and links of both can change together)
+// re-classifies through the multi-kernel path instead: the cluster queues its
+// box items, as k_links does.  Its force, torque and update stay here.
+constexpr int kFT = 256;  // threads per block
+
+namespace cg = cooperative_groups;
+
+__device__ __forceinline__ bool boxes_near(const Lattice& L, const BodyParams& pa, const BodyState& sa,
+                                           const BodyParams& pb, const BodyState& sb) {
+    int la[3], wa[3], lb[3], wb[3];
+    body_box(L, pa, sa, la, wa);
+    body_box(L, pb, sb, lb, wb);
+    const int n3[3] = {L.nx, L.ny, L.nz};
+    for (int a = 0; a < 3; ++a)
+        if (!axis_overlap(la[a] - 1, wa[a] + 2, lb[a] - 1, wb[a] + 2, n3[a])) return false;
+    return true;
+}
+
+// Geometry of one step's shell scan of an isolated sphere, in offsets from
+// the node ip = floor(r) of the new centre r.  Stencil offset o is the node
+// ip + o; its FP32 offset from the new centre is t = o - frac(r), the value
+// dist2_f computes, and from the centre r_old of the last classification
+// t = (o + sh) - frac(r_old), sh = ip - floor(r_old) (minimum image).  Both
+// are within the error bound of dist2_f, so inside tests decide exactly (see
+// inside_node).
+struct ShellGeo {
+    int ip[3], sh[3], lrel[3], w[3], n3[3];
+    float fn[3], fo[3];
+    float R2f, band, Rf;
+    double R, pos[3], old[3];
+};
+
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+__device__ __forceinline__ float d2_off(int ox, int oy, int oz, const float f[3]) {
+    const float tx = (float)ox - f[0], ty = (float)oy - f[1], tz = (float)oz - f[2];
+    return tx * tx + ty * ty + tz * tz;
+}
+
+// Whether node ip + o is inside the sphere centred at c (G.pos or G.old);
+// s: its FP32 |d|^2 from c.
+__device__ __forceinline__ bool geo_inside(const ShellGeo& G, float s, const double* c, int ox, int oy, int oz) {
+    if (fabsf(s - G.R2f) > G.band) return s < G.R2f;
+    return inside_exact(G.n3[0], G.n3[1], G.n3[2], c, G.R, wrap1(G.ip[0] + ox, G.n3[0]),
+                        wrap1(G.ip[1] + oy, G.n3[1]), wrap1(G.ip[2] + oz, G.n3[2]));
+}
+
+__device__ __forceinline__ void decode_off(uint32_t code, int& ox, int& oy, int& oz) {
+    ox = (int)(code & 1023u) - 512;
+    oy = (int)((code >> 10) & 1023u) - 512;
+    oz = (int)(code >> 20) - 512;
+}
+
+// Whether offset o lies in the scan box and in the shell; s: its FP32 |d|^2.
+__device__ __forceinline__ bool geo_take(const ShellGeo& G, int ox, int oy, int oz, float& s) {
+    if ((unsigned)(ox - G.lrel[0]) >= (unsigned)G.w[0] || (unsigned)(oy - G.lrel[1]) >= (unsigned)G.w[1] ||
+        (unsigned)(oz - G.lrel[2]) >= (unsigned)G.w[2])
+        return false;
+    s = d2_off(ox, oy, oz, G.fn);
+    return in_shell(s, G.Rf);
+}
+
+__device__ __forceinline__ int64_t geo_cell(const Lattice& L, const ShellGeo& G, int ox, int oy, int oz, int& x,
+                                            int& y, int& z) {
+    x = wrap1(G.ip[0] + ox, L.nx);
+    y = wrap1(G.ip[1] + oy, L.ny);
+    z = wrap1(G.ip[2] + oz, L.nz);
+    return cell_index(L, x, y, z);
+}
+
+// Links from the fluid node ip + o to the sphere at its new centre, as a bit
+// mask over directions.
+__device__ __forceinline__ uint32_t geo_mask(const ShellGeo& G, int ox, int oy, int oz) {
+    uint32_t mask = 0;
+#pragma unroll 1
+    for (int i = 1; i < Q; ++i) {
+        const int a = ox + cx(i), b = oy + cy(i), c = oz + cz(i);
+        if (geo_inside(G, d2_off(a, b, c, G.fn), G.pos, a, b, c)) mask |= 1u << i;
+    }
+    return mask;
+}
+
+// Refill of the uncovered node ip + o (see refill_cell): the neighbours that
+// are fluid now and were fluid at the last classification are those outside
+// the sphere at both centres, so the owner field is not read.
+__device__ __noinline__ void geo_refill(const Lattice& L, const ShellGeo& G, const BodyState& s, int ox, int oy,
+                                        int oz, int q, double* acc) {
+    const int lane = threadIdx.x & 31;
+    double r = 0.0;
+    int valid = 0;
+    if (lane >= 1 && lane < Q) {
+        const int a = ox + cx(lane), b = oy + cy(lane), c = oz + cz(lane);
+        if (!geo_inside(G, d2_off(a, b, c, G.fn), G.pos, a, b, c) &&
+            !geo_inside(G, d2_off(a + G.sh[0], b + G.sh[1], c + G.sh[2], G.fo), G.old, a, b, c)) {
+            valid = 1;
+            int xn, yn, zn;
+            geo_cell(L, G, a, b, c, xn, yn, zn);
+#pragma unroll 1
+            for (int j = 0; j < Q; ++j) r += load_abs<true>(L, read_slot(L, j, xn, yn, zn, q), j);
+        }
+    }
+    int x, y, z;
+    geo_cell(L, G, ox, oy, oz, x, y, z);
+    refill_finish(L, s, x, y, z, q, r, valid, acc);
+}
+
+// Copy n bytes (a multiple of 8) from global to shared memory, by the block.
+__device__ __forceinline__ void copy_words(void* dst, const void* src, int n) {
+    for (int t = threadIdx.x; t < n / 8; t += blockDim.x)
+        reinterpret_cast<long long*>(dst)[t] = __ldcg(reinterpret_cast<const long long*>(src) + t);
+}
+
+constexpr int kStcBuf = 2048;  // stencil entries a block keeps in shared memory
+
+template <int P>
+__global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int KC = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int cid = blockIdx.x / KC, ncl = gridDim.x / KC;
+    __shared__ double sm[12 * kFT + 12 * 8];
+    __shared__ double s_tot[12], s_conv[6];
+    __shared__ Lattice s_L;
+    __shared__ BodyParams s_p;
+    __shared__ BodyState s_s0, s_new, s_cur;
+    __shared__ BodyAcc s_A;
+    __shared__ ShellGeo s_geo;
+    __shared__ uint32_t s_stc[kStcBuf];
+    __shared__ int s_lo[3];
+    __shared__ long long sml[kFT / 32];
+    __shared__ long long s_count, s_before;
+    __shared__ int s_scan[kFT / 32 + 1], s_list[kFT], s_mode, s_base;
+    __shared__ float s_min[kFT / 32], s_margin;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = B.fused_first[cls], nitems = B.n_fused[cls];
+    for (int it = cid; it < nitems; it += ncl) {
+        // everything of this body and lattice that the step reads, in one go
+        // (the sweep streams the whole lattice through L2 between two steps,
+        // so these tables come from HBM)
+        const int2 item = B.fused_items[i0 + it];
+        const int k = item.x;
+        __syncthreads();  // the previous item's readers of the copies are done
+        copy_words(&s_L, B.lats + item.y, sizeof(Lattice));
+        copy_words(&s_p, B.par + k, sizeof(BodyParams));
+        copy_words(&s_s0, B.state[P] + k, sizeof(BodyState));
+        copy_words(&s_A, B.acc + k, sizeof(BodyAcc));
+        __syncthreads();
+        const Lattice& L = s_L;
+        const BodyParams& p = s_p;
+        const BodyState& s0 = s_s0;
+        if (!lattice_active(L)) continue;  // the same in every block of the cluster
+        // this block's share of the shell stencil, fetched while the links run
+        const uint32_t* stc = B.stencil + p.st_off;
+        long long b0, b1;
+        box_range(p.st_count, rank, KC, b0, b1);
+        for (long long b = b0 + threadIdx.x; b < b1 && b < b0 + kStcBuf; b += kFT) s_stc[b - b0] = __ldg(stc + b);
+
+        // ---- bounce-back and momentum exchange on the links (as k_links)
+        double acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = 0.0;
+        if (L.storage == ST_F64)
+            link_terms<P, true>(L, p, s0, s_A.link_count, B.links + p.link_off, rank, KC, acc);
+        else
+            link_terms<P, false>(L, p, s0, s_A.link_count, B.links + p.link_off, rank, KC, acc);
+        block_sum_fixed<12, kFT>(acc, sm, s_tot);
+        int near = 0;
+        if (rank == 0)
+            for (int j = L.body_begin + threadIdx.x; j < L.body_begin + L.body_count; j += kFT)
+                if (j != k && boxes_near(L, p, s0, B.par[j], B.state[P][j])) near = 1;
+        near = __syncthreads_or(near);
+        cl.sync();
+        if (rank == 0) {
+            // the blocks' partial sums, all fetched at once, then summed in rank order
+            if (threadIdx.x < 12 * KC) sm[threadIdx.x] = cl.map_shared_rank(s_tot, threadIdx.x / 12)[threadIdx.x % 12];
+            __syncthreads();
+            if (threadIdx.x < 12) {
+                double t = 0.0;
+                for (int r = 0; r < KC; ++r) t += sm[r * 12 + threadIdx.x];
+                sm[12 * KC + threadIdx.x] = t;
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) update_body<P>(L, B, k, p, s0, s_A, sm + 12 * KC, &s_new, &s_mode);
+            __syncthreads();
+            if (threadIdx.x == 0) s_mode = s_mode ? (near ? 2 : 1) : 0;
+            __syncthreads();
+            if (s_mode == 2) append_items(B.box_items, B.n_box, B.box_cap, k, p.g_box, B.err, &s_base);
+        }
+        cl.sync();
+        if (*cl.map_shared_rank(&s_mode, 0) != 1) continue;
+        BodyAcc& A = B.acc[k];
+
+        // ---- phase A: re-classification of the shell, conversions, link count
+        // (as k_classify + k_convert).  No other body owns a cell of the box, so
+        // the owner of a node is whether it is inside the sphere: now at the new
+        // centre, before at the centre of the last classification.
+        if (threadIdx.x < 12) {  // the new state, one double per thread
+            const double* src = reinterpret_cast<const double*>(cl.map_shared_rank(&s_new, 0));
+            reinterpret_cast<double*>(&s_cur)[threadIdx.x] = src[threadIdx.x];
+        }
+        if (threadIdx.x < 3) {  // geometry of axis a
+            const int a = threadIdx.x;
+            ShellGeo& G = s_geo;
+            const int n = a == 0 ? L.nx : (a == 1 ? L.ny : L.nz);
+            const double rn = cl.map_shared_rank(&s_new, 0)->pos[a], ro = s_A.r_class[a];
+            const int lo = (int)floor(rn - p.R) - 2;  // as body_box
+            G.ip[a] = (int)floor(rn);
+            G.fn[a] = (float)(rn - (double)G.ip[a]);
+            const int io = (int)floor(ro);
+            G.fo[a] = (float)(ro - (double)io);
+            int d = G.ip[a] - io;
+            if (2 * d > n) d -= n;
+            else if (2 * d <= -n) d += n;
+            G.sh[a] = d;
+            G.lrel[a] = lo - G.ip[a];
+            G.w[a] = p.box_w[a];
+            G.n3[a] = n;
+            G.pos[a] = rn;
+            G.old[a] = ro;
+            s_lo[a] = lo;
+            if (a == 0) {
+                G.R = p.R;
+                G.Rf = (float)p.R;
+                G.R2f = (float)(p.R * p.R);
+                G.band = band_of(G.Rf);
+            }
+        }
+        __syncthreads();
+        const ShellGeo& G = s_geo;
+        const BodyState& s = s_cur;
+        const int id = k + 1;
+        // stencil entry b of this block's share (shared memory up to kStcBuf)
+        auto entry = [&](long long b) -> uint32_t { return b - b0 < kStcBuf ? s_stc[b - b0] : __ldg(stc + b); };
+        const int q = 1 - P;
+        float mloc = FLT_MAX;
+        double cacc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        long long lcount = 0;
+        for (long long r0 = b0; r0 < b1; r0 += kFT) {
+            const long long b = r0 + threadIdx.x;
+            int uncover = 0, ox = 0, oy = 0, oz = 0;
+            float s32;
+            if (b < b1) decode_off(entry(b), ox, oy, oz);
+            if (b < b1 && geo_take(G, ox, oy, oz, s32)) {
+                const bool now = geo_inside(G, s32, G.pos, ox, oy, oz);
+                const bool was =
+                    geo_inside(G, d2_off(ox + G.sh[0], oy + G.sh[1], oz + G.sh[2], G.fo), G.old, ox, oy, oz);
+                mloc = fminf(mloc, fmaxf(fabsf(sqrtf(s32) - G.Rf) - 1e-3f, 0.0f));
+                if (now != was) {
+                    int x, y, z;
+                    const int64_t n = geo_cell(L, G, ox, oy, oz, x, y, z);
+                    L.own[n] = now ? id : 0;
+                    if (now) covered_momentum<true>(L, s, x, y, z, q, cacc);  // fluid -> solid: to the body
+                    else uncover = 1;
+                }
+                if (!now) lcount += __popc(geo_mask(G, ox, oy, oz));
+            }
+            // uncovered nodes of this round, refilled one per warp
+            int nu;
+            const int pos = block_scan<kFT>(uncover, &nu, s_scan);
+            if (uncover) s_list[pos] = (int)(b - r0);
+            __syncthreads();
+            for (int u = warp; u < nu; u += kFT / 32) {
+                int ux, uy, uz;
+                decode_off(entry(r0 + s_list[u]), ux, uy, uz);
+                geo_refill(L, G, s, ux, uy, uz, q, cacc);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mloc = fminf(mloc, __shfl_down_sync(0xffffffffu, mloc, o));
+        if (lane == 0) s_min[warp] = mloc;
+        const int had = cacc[0] != 0.0 || cacc[1] != 0.0 || cacc[2] != 0.0 || cacc[3] != 0.0 || cacc[4] != 0.0 ||
+                        cacc[5] != 0.0;
+        if (__syncthreads_or(had)) {
+            block_sum_fixed<6, kFT>(cacc, sm, s_conv);
+        } else if (threadIdx.x < 6) {
+            s_conv[threadIdx.x] = 0.0;
+        }
+        lcount = block_sum_ll<kFT>(lcount, sml);
+        if (threadIdx.x == 0) {
+            s_count = lcount;
+            float m = FLT_MAX;
+            for (int r = 0; r < kFT / 32; ++r) m = fminf(m, s_min[r]);
+            s_margin = m;
+        }
+        cl.sync();
+
+        // ---- phase B: link list compaction, commit of the owners (as k_rebuild)
+        // link counts and node margins of all blocks: lane r of warp 0 reads
+        // block r's (integer sums and a minimum: any order gives the same)
+        if (warp == 0) {
+            const long long v = lane < KC ? *cl.map_shared_rank(&s_count, lane) : 0;
+            float m = lane < KC ? *cl.map_shared_rank(&s_margin, lane) : FLT_MAX;
+            long long all = v, bef = lane < rank ? v : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                all += __shfl_xor_sync(0xffffffffu, all, o);
+                bef += __shfl_xor_sync(0xffffffffu, bef, o);
+                m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            }
+            if (lane == 0) {
+                s_before = bef;
+                if (rank == 0) {
+                    if (all > p.link_cap) set_error(L.err, 8);
+                    A.link_count = all < p.link_cap ? all : p.link_cap;
+                    A.margin_bits = (unsigned long long)__double_as_longlong((double)m);
+                }
+            }
+        }
+        if (rank == 0 && threadIdx.x >= 32 && threadIdx.x < 38) {  // conversion force, blocks in rank order
+            const int c = threadIdx.x - 32;
+            double t = 0.0;
+            for (int r = 0; r < KC; ++r) t += cl.map_shared_rank(s_conv, r)[c];
+            // the update of this step consumed (zeroed) the previous booking
+            if (c < 3) A.Fc[c] = t;
+            else A.Tc[c - 3] = t;
+        }
+        if (rank == 0 && threadIdx.x >= 64 && threadIdx.x < 67) {
+            const int a = threadIdx.x - 64;
+            A.box_lo[a] = s_lo[a];
+            A.r_class[a] = s.pos[a];
+        }
+        __syncthreads();
+        const long long before = s_before;
+        uint32_t* links = B.links + p.link_off;
+        const long long cap = p.link_cap;
+        long long base = before;
+        for (long long r0 = b0; r0 < b1; r0 += kFT) {
+            const long long b = r0 + threadIdx.x;
+            uint32_t mask = 0;
+            int64_t n = 0;
+            int ox = 0, oy = 0, oz = 0;
+            float s32;
+            if (b < b1) decode_off(entry(b), ox, oy, oz);
+            if (b < b1 && geo_take(G, ox, oy, oz, s32)) {
+                int x, y, z;
+                n = geo_cell(L, G, ox, oy, oz, x, y, z);
+                const bool now = geo_inside(G, s32, G.pos, ox, oy, oz);
+                const bool was =
+                    geo_inside(G, d2_off(ox + G.sh[0], oy + G.sh[1], oz + G.sh[2], G.fo), G.old, ox, oy, oz);
+                if (now != was) L.own_prev[n] = now ? id : 0;
+                if (!now) mask = geo_mask(G, ox, oy, oz);
+            }
+            int tot;
+            const int off = block_scan<kFT>(__popc(mask), &tot, s_scan);
+            long long pos = base + off;
+            while (mask) {
+                const int i = __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (pos < cap) links[pos] = (uint32_t)(n * 32 + i);
+                pos++;
+            }
+            base += tot;
+        }
+    }
+    // no block leaves while another may still read its shared memory
+    cl.sync();
+}
+
 // ---------------------------------------------------------------- launchers
 
 // which: 1 links, 2 classify, 3 convert, 4 rebuild, 5 tick.  The link kernel
@@ -1027,6 +1581,37 @@ void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, 
     } else {
         k_tick<<<1, 1, 0, st>>>(B.n_box, B.n_rel, step);
     }
+}
+
+// Once per process and device, before the first launch of k_body_fused:
+// allow clusters of 16 blocks (above the portable maximum of 8).
+cudaError_t prepare_body_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_body_fused<0>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_body_fused<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+// Blocks per cluster of fused-kernel class c (see fused_class).
+int fused_cluster(int c) { return c == 0 ? 16 : (c == 1 ? 8 : 4); }
+
+// The fused body kernel over the spheres of class cls in B.fused_items:
+// `clusters` clusters of fused_cluster(cls) blocks.
+void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st) {
+    if (clusters <= 0) return;
+    const int kc = fused_cluster(cls);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(clusters * kc);
+    cfg.blockDim = dim3(kFT);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (parity == 0) cudaLaunchKernelEx(&cfg, k_body_fused<0>, B, cls);
+    else cudaLaunchKernelEx(&cfg, k_body_fused<1>, B, cls);
 }
 
 // A step's body kernels: links, classify, convert, rebuild (whose last block

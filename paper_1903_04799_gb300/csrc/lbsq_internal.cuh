@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -126,13 +127,24 @@ __device__ __forceinline__ int64_t read_slot(const Lattice& L, int i, int x, int
     return (int64_t)opp(i) * L.Np + cell_index(L, xs, ys, zs);
 }
 
+// Global load; CG = true reads through L2 only (data another block of the
+// same launch may have written).
+template <bool CG, class T>
+__device__ __forceinline__ T ld(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // Absolute value f_i from a stored slot, in FP64.
+template <bool CG = false>
 __device__ __forceinline__ double load_abs(const Lattice& L, int64_t slot, int i) {
     switch (L.storage) {
-        case ST_F64: return ((const double*)L.F)[slot];
-        case ST_F32: return wgt(i) * L.rho0 + (double)((const float*)L.F)[slot];
-        case ST_F16: return wgt(i) * L.rho0 + (double)(__half2float(((const __half*)L.F)[slot]) * L.inv_scale);
-        default: return wgt(i) * L.rho0 + (double)(__bfloat162float(((const __nv_bfloat16*)L.F)[slot]) * L.inv_scale);
+        case ST_F64: return ld<CG>((const double*)L.F + slot);
+        case ST_F32: return wgt(i) * L.rho0 + (double)ld<CG>((const float*)L.F + slot);
+        case ST_F16: return wgt(i) * L.rho0 + (double)(__half2float(ld<CG>((const __half*)L.F + slot)) * L.inv_scale);
+        default:
+            return wgt(i) * L.rho0 +
+                   (double)(__bfloat162float(ld<CG>((const __nv_bfloat16*)L.F + slot)) * L.inv_scale);
     }
 }
 
@@ -195,6 +207,9 @@ struct BodyParams {
     int lat;           // index of the body's lattice
     int copy_only;     // a still body whose force nobody reads: bounce-back is a plain copy
     double inv_mass, inv_inertia;
+    int64_t st_off;    // first entry of the sphere's shell stencil (see k_body_fused)
+    int st_count;      // stencil entries; 0 for bodies the fused kernel does not handle
+    int st_pad;
 };
 
 struct BodyState {  // ping-pong by step parity
@@ -222,6 +237,8 @@ struct BodyAcc {
 // block's share of a body; per-step lists are appended on the device:
 // the update appends the box items of bodies that must re-classify, the
 // classification appends the items of every body whose links must be rebuilt.
+std::vector<uint32_t> shell_stencil(double R);
+
 struct Bodies {
     const Lattice* lats;
     const BodyParams* par;
@@ -244,7 +261,29 @@ struct Bodies {
     int* err;              // error word for list overflow (shared)
     int* win;              // near-body z-windows [2][2] of lattice 0 (z0, length) by step parity, or null
     long long* gstep;      // server: global step counter, advanced by the rebuild kernel (or null)
+    // spheres advanced by k_body_fused (body, lattice), grouped by cluster
+    // class: class c holds items [fused_first[c], fused_first[c] + n_fused[c])
+    const int2* fused_items;
+    const int* fused_first;  // [3]
+    const int* n_fused;      // [3]
+    const uint32_t* stencil; // shell stencils of those spheres
 };
+
+// Cluster class of the fused body kernel for a lattice with nf fused spheres:
+// 0 (16 blocks per sphere) up to 8 spheres, 1 (8 blocks) up to 64, else 2
+// (4 blocks).  Fewer blocks per sphere when there are many spheres: the
+// clusters then fill the GPU in fewer waves.  A function of the lattice
+// alone, so a body's result does not depend on other lattices.
+inline int fused_class(int nf) { return nf <= 8 ? 0 : (nf <= 64 ? 1 : 2); }
+
+// Largest sphere radius with a shell stencil (stencil offsets fit 10 bits).
+constexpr double kStencilMaxR = 400.0;
+
+// Whether the fused body kernel advances a body: moving-surface spheres with
+// a stencil (still obstacles are plain copies, walls never re-classify).
+inline bool fused_body(const BodyParams& b) {
+    return b.kind == BODY_SPHERE && !b.copy_only && b.R <= kStencilMaxR;
+}
 
 // Scan box of a body: origin and extent.
 __device__ __forceinline__ void body_box(const Lattice& L, const BodyParams& p, const BodyState& s, int lo[3],

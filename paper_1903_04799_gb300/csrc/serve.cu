@@ -294,6 +294,9 @@ Bodies bodies_view(lb_server* s, bool step) {
     B.err = s->d_errs;  // list overflow is reported on slot 0's word
     B.win = nullptr;
     B.gstep = step ? s->d_gstep : nullptr;
+    B.fused_items = nullptr;  // the server runs every body through the multi-kernel path
+    B.n_fused = nullptr;
+    B.stencil = nullptr;
     return B;
 }
 

@@ -2,6 +2,10 @@
 // them runs inside a time step.
 #include <cfloat>
 
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "lbsq_internal.cuh"
 
 namespace lbsq {
@@ -200,6 +204,35 @@ void launch_plane_claim(const Lattice& L, int32_t* own, int axis, int index, int
 }
 void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, cudaStream_t st) {
     k_set_flags<<<(nb + kB - 1) / kB, kB, 0, st>>>(acc, nb, k, reclass);
+}
+
+
+// Shell stencil of a sphere of radius R for k_body_fused: the offsets o from
+// the centre's node floor(r) for which some centre fraction f in [0,1]^3 puts
+// |o - f|^2 inside the bounds of in_shell widened by 1, packed as
+// (ox + 512) | (oy + 512) << 10 | (oz + 512) << 20, in (z, y, x) order.
+// Requires R <= kStencilMaxR.
+std::vector<uint32_t> shell_stencil(double R) {
+    const double lo2 = R > 1.5 ? (R - 1.5) * (R - 1.5) - 0.25 : -1.0;
+    const double hi2 = (R + 2.0) * (R + 2.0) + 0.25;
+    const int m = (int)std::ceil(R + 4.0);
+    std::vector<uint32_t> v;
+    for (int oz = -m; oz <= m; ++oz)
+        for (int oy = -m; oy <= m; ++oy)
+            for (int ox = -m; ox <= m; ++ox) {
+                const int o[3] = {ox, oy, oz};
+                double dmin = 0.0, dmax = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double t = o[a];
+                    const double nearest = t < 0.0 ? -t : (t > 1.0 ? t - 1.0 : 0.0);
+                    const double farthest = std::max(std::fabs(t), std::fabs(t - 1.0));
+                    dmin += nearest * nearest;
+                    dmax += farthest * farthest;
+                }
+                if (dmin < hi2 + 1.0 && dmax > lo2 - 1.0)
+                    v.push_back((uint32_t)(ox + 512) | (uint32_t)(oy + 512) << 10 | (uint32_t)(oz + 512) << 20);
+            }
+    return v;
 }
 
 }  // namespace lbsq

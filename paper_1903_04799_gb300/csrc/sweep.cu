@@ -52,12 +52,14 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaSt
 // variant: 0 = default (two cells per thread where nx is even, FP64 one cell),
 // 1 = one cell per thread, 2 = two cells per thread where possible.
 // zmode / win / gz: plane selection (see SweepArgs); gz = grid planes (nz for
-// modes 0 and 1, an upper bound of the window length for mode 2).
+// modes 0 and 1, an upper bound of the window length for mode 2).  Odd steps
+// sweep the planes in descending order.
 void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, int zmode,
                   const int* win, int gz, cudaStream_t st) {
     SweepArgs a = sweep_args(L, lambda_e, lambda_o);
     a.zmode = zmode;
     a.win = win;
+    a.reverse = parity;
     if (gz <= 0) return;
     switch (L.storage) {
         case ST_F64: launch_s<ST_F64>(a, parity, variant, gz, st); break;

@@ -33,18 +33,24 @@ struct SweepArgs {
     // inside it, blockIdx.z counting from z0
     int zmode;
     const int* win;
+    // planes in descending order (blocks are dispatched roughly in blockIdx
+    // order): sweeps alternate direction, so that a sweep first reads the
+    // planes the previous sweep wrote last, which are still in L2.  Any plane
+    // order gives the same result (each cell touches only its own slots).
+    int reverse;
 };
 
 // Plane swept by this block, or -1 if none.
 __device__ __forceinline__ int sweep_plane(const SweepArgs& a) {
-    const int bz = blockIdx.z;
-    if (a.zmode == 0) return bz;
+    int bz = blockIdx.z;
+    if (a.zmode == 0) return a.reverse ? a.nz - 1 - bz : bz;
     const int z0 = __ldg(a.win), len = __ldg(a.win + 1);
     if (a.zmode == 2) {
         if (bz >= len) return -1;
-        const int z = z0 + bz;
+        const int z = z0 + (a.reverse ? len - 1 - bz : bz);
         return z >= a.nz ? z - a.nz : z;
     }
+    if (a.reverse) bz = a.nz - 1 - bz;
     const int rel = bz - z0 < 0 ? bz - z0 + a.nz : bz - z0;
     return rel < len ? -1 : bz;
 }
@@ -237,6 +243,7 @@ __host__ __device__ inline SweepArgs sweep_args(const Lattice& L, double lambda_
     a.inv_scale = L.inv_scale;
     a.zmode = 0;
     a.win = nullptr;
+    a.reverse = 0;
     return a;
 }
 
