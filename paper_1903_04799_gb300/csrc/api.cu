@@ -19,7 +19,7 @@ void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity
 void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, int grid_box, long long* step,
                         cudaStream_t st);
 void launch_body_step(const Bodies& B, int parity, int grid_links, int grid_box, long long* step, cudaStream_t st);
-void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st);
+void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st, int tail);
 cudaError_t prepare_body_kernels();
 void launch_fill_rest(const Lattice& L, cudaStream_t st);
 void launch_set_eq(const Lattice& L, const double* rho, const double* u, int q, cudaStream_t st);
@@ -65,12 +65,16 @@ struct lb_ctx {
     int2* d_box_items = nullptr;
     int2* d_rel_items = nullptr;
     int* d_counts = nullptr;  // [0] link items, [1] box items, [2] relink items, [3] rebuild blocks done,
-                              // [4..6] fused spheres per class, [7..9] first fused item per class
+                              // [4..6] fused spheres per class, [7..9] first fused item per class,
+                              // [10] clusters of a solo fused launch done
     int n_link_items = 0, list_cap = 0, list_alloc = 0;
     // spheres advanced by the fused cluster kernel, and their shell stencils
     int2* d_fused_items = nullptr;
     uint32_t* d_stencil = nullptr;
     int n_fused = 0, fused_cls = 0, fused_alloc = 0;
+    // the lattice holds one fused sphere and no other body: its step needs
+    // only the fused kernel (no body can come near another)
+    bool solo = false;
     int64_t stencil_alloc = 0;
     int grid_box = 1;
     int n_sm = 152;
@@ -188,6 +192,7 @@ Bodies bodies_view(const lb_ctx* c) {
     B.n_fused = c->d_counts + 4;
     B.fused_first = c->d_counts + 7;
     B.stencil = c->d_stencil;
+    B.fused_done = c->d_counts + 10;
     return B;
 }
 
@@ -334,6 +339,7 @@ lb_status relayout(lb_ctx* c) {
     }
     c->n_fused = (int)fused.size();
     c->fused_cls = fused_class(c->n_fused);
+    c->solo = c->n_fused == 1 && nb == 1;
     if (!fused.empty()) {
         CK(cudaMemcpyAsync(c->d_fused_items, fused.data(), sizeof(int2) * fused.size(), cudaMemcpyHostToDevice,
                            c->stream));
@@ -372,7 +378,7 @@ lb_status relayout(lb_ctx* c) {
     c->grid_box = std::max(1, std::min(sum_gb, 4 * c->n_sm));
     CK(cudaMemcpyAsync(c->d_link_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
                        c->stream));
-    int counts[10] = {c->n_link_items, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int counts[11] = {c->n_link_items, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     counts[4 + c->fused_cls] = c->n_fused;  // one lattice: one class, starting at item 0
     CK(cudaMemcpyAsync(c->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_par, c->par.data(), sizeof(BodyParams) * nb, cudaMemcpyHostToDevice, c->stream));
@@ -528,7 +534,7 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     c->d_err = dalloc_t<int>(c, 2);
     c->d_count = dalloc_t<int>(c, 2);
     c->d_lat = dalloc_t<Lattice>(c, 1);
-    c->d_counts = dalloc_t<int>(c, 10);
+    c->d_counts = dalloc_t<int>(c, 11);
     c->d_win = dalloc_t<int>(c, 4);
     int prio_lo = 0, prio_hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) return bail(LB_ERR_CUDA);
@@ -782,11 +788,16 @@ static void sweep_all(lb_ctx* c, int parity, cudaStream_t st) {
 // The body kernels of one step on stream st: the fused kernel (spheres), the
 // link kernel (walls and still obstacles, if any), then classify, convert and
 // rebuild, which re-classify the spheres queued by the other two (bodies near
-// another body) and end the step.  Returns the launch count.
+// another body) and end the step; for a lattice with a single sphere and no
+// other body, the fused kernel alone.  Returns the launch count.
 static int body_step(lb_ctx* c, const Bodies& B, int parity, cudaStream_t st) {
+    if (c->solo) {  // the fused kernel is the whole body step
+        launch_body_fused(B, parity, c->fused_cls, 1, st, 1);
+        return 1;
+    }
     int n = 0;
     if (c->n_fused > 0) {
-        launch_body_fused(B, parity, c->fused_cls, c->n_fused, st);
+        launch_body_fused(B, parity, c->fused_cls, c->n_fused, st, 0);
         n++;
     }
     if (c->n_link_items > 0) {
@@ -810,7 +821,7 @@ static void enqueue_traced_step(lb_ctx* c) {
         } else if (k == 1) {
             const Bodies B = bodies_view(c);
             if (c->n_fused > 0) {
-                launch_body_fused(B, parity, c->fused_cls, c->n_fused, c->stream);
+                launch_body_fused(B, parity, c->fused_cls, c->n_fused, c->stream, 0);
                 c->launches += 1;
             }
             if (c->n_link_items > 0) {

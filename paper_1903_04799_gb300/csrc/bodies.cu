@@ -1315,7 +1315,7 @@ __device__ __forceinline__ void copy_words(void* dst, const void* src, int n) {
 constexpr int kStcBuf = 2048;  // stencil entries a block keeps in shared memory
 
 template <int P>
-__global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls) {
+__global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, int tail) {
     cg::cluster_group cl = cg::this_cluster();
     const int KC = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
@@ -1557,6 +1557,18 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls) 
     }
     // no block leaves while another may still read its shared memory
     cl.sync();
+    // tail != 0: this launch is the lattice's whole body step (one sphere and
+    // nothing else, so the multi-kernel path never has work): the last
+    // cluster to finish computes the near-body window of the coming sweeps,
+    // as the rebuild kernel does otherwise.
+    if (tail && B.win && rank == 0 && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(B.fused_done, 1) == ncl - 1) {
+            *B.fused_done = 0;
+            __threadfence();
+            near_window<P>(B);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1595,8 +1607,8 @@ cudaError_t prepare_body_kernels() {
 int fused_cluster(int c) { return c == 0 ? 16 : (c == 1 ? 8 : 4); }
 
 // The fused body kernel over the spheres of class cls in B.fused_items:
-// `clusters` clusters of fused_cluster(cls) blocks.
-void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st) {
+// `clusters` clusters of fused_cluster(cls) blocks; tail: see k_body_fused.
+void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st, int tail) {
     if (clusters <= 0) return;
     const int kc = fused_cluster(cls);
     cudaLaunchConfig_t cfg = {};
@@ -1610,8 +1622,8 @@ void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaS
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (parity == 0) cudaLaunchKernelEx(&cfg, k_body_fused<0>, B, cls);
-    else cudaLaunchKernelEx(&cfg, k_body_fused<1>, B, cls);
+    if (parity == 0) cudaLaunchKernelEx(&cfg, k_body_fused<0>, B, cls, tail);
+    else cudaLaunchKernelEx(&cfg, k_body_fused<1>, B, cls, tail);
 }
 
 // A step's body kernels: links, classify, convert, rebuild (whose last block

@@ -267,6 +267,7 @@ struct Bodies {
     const int* fused_first;  // [3]
     const int* n_fused;      // [3]
     const uint32_t* stencil; // shell stencils of those spheres
+    int* fused_done;         // clusters of a solo fused launch that finished (self-resetting)
 };
 
 // Cluster class of the fused body kernel for a lattice with nf fused spheres:
