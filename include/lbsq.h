@@ -213,10 +213,14 @@ const char* lb_last_error(const lb_ctx* c);
 /* Number of kernel launches the context has enqueued so far (all kinds). */
 int64_t lb_kernel_launches(const lb_ctx* c);
 
-/* Tuning: the launch shape of the stream-collide kernel.  0 = default (two
- * cells per thread with paired loads where nx is even, except FP64), 1 = one
- * cell per thread, 2 = two cells per thread where nx is even.  Results are
- * identical bit for bit; only the speed differs. */
+/* Tuning: the launch shape of the stream-collide kernel.  0 = default
+ * (reduced storages with even nx: two cells per thread with paired loads and
+ * the two cells collided together on the packed FP32 pipe; FP64: one cell),
+ * 1 = one cell per thread, 2 = two cells per thread where nx is even, 3 =
+ * FP16 / BF16 storage: four cells per thread in aligned 8-byte chunks where
+ * nx is a multiple of 128 (else as 2), 4 = FP16 / BF16: two cells per thread
+ * with the values kept packed (else as 2).  Results are identical bit for
+ * bit; only the speed differs.  LB_ERR_INVALID for another value. */
 lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant);
 
 /* Kernel tracing.  Between lb_profile_begin and lb_profile_end, lb_step

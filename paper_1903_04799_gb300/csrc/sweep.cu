@@ -28,8 +28,38 @@ __global__ void __launch_bounds__(256, 2) k_sweep2(const SweepArgs a) {
     sweep_two<S, P>(a, x0, y, z);
 }
 
+// 16-bit storages: the packed two-cell form, three blocks per SM.
+template <int S, int P>
+__global__ void __launch_bounds__(256, 3) k_sweep2p(const SweepArgs a) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = sweep_plane(a);
+    if (x0 >= a.nx || y >= a.ny || z < 0) return;
+    sweep_two16<S, P>(a, x0, y, z);
+}
+
+// 16-bit storages with nx % 128 == 0 and 19 Np < 2^31: a warp per 128 cells
+// of a row, eight rows per block (see sweep_four).
+template <int S, int P>
+__global__ void __launch_bounds__(256, 2) k_sweep4(const SweepArgs a) {
+    const int lane = threadIdx.x;
+    const int x0 = 128 * blockIdx.x + 4 * lane;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = sweep_plane(a);
+    if (y >= a.ny || z < 0) return;  // a whole warp
+    sweep_four<S, P>(a, x0, y, z, lane);
+}
+
 template <int S>
 static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaStream_t st) {
+    if constexpr (S == ST_F16 || S == ST_BF16) {
+        if (variant == 3 && a.nx % 128 == 0 && 19 * a.Np < (int64_t(1) << 31)) {
+            dim3 block(32, 8), grid(a.nx / 128, (a.ny + 7) / 8, gz);
+            if (parity == 0) k_sweep4<S, 0><<<grid, block, 0, st>>>(a);
+            else k_sweep4<S, 1><<<grid, block, 0, st>>>(a);
+            return;
+        }
+    }
     if constexpr (S != ST_F64) {
         if (variant != 1 && a.nx % 2 == 0) {
             const int pairs = a.nx / 2;
@@ -37,6 +67,13 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaSt
             if (bx > 128) bx = 128;
             const int by = 256 / bx;
             dim3 block(bx, by), grid((pairs + bx - 1) / bx, (a.ny + by - 1) / by, gz);
+            if constexpr (S == ST_F16 || S == ST_BF16) {
+                if (variant == 4 && 19 * a.Np < (int64_t(1) << 31)) {  // the packed form
+                    if (parity == 0) k_sweep2p<S, 0><<<grid, block, 0, st>>>(a);
+                    else k_sweep2p<S, 1><<<grid, block, 0, st>>>(a);
+                    return;
+                }
+            }
             if (parity == 0) k_sweep2<S, 0><<<grid, block, 0, st>>>(a);
             else k_sweep2<S, 1><<<grid, block, 0, st>>>(a);
             return;
@@ -49,8 +86,10 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaSt
     else k_sweep<S, 1><<<grid, bx, 0, st>>>(a);
 }
 
-// variant: 0 = default (two cells per thread where nx is even, FP64 one cell),
-// 1 = one cell per thread, 2 = two cells per thread where possible.
+// variant: 0 = default (reduced storages with even nx: two cells per thread;
+// FP64: one), 1 = one cell per thread, 2 = two cells per thread where
+// possible, 3 = FP16 / BF16: four cells per thread where possible (else as
+// 2), 4 = FP16 / BF16: two cells per thread, packed (else as 2).
 // zmode / win / gz: plane selection (see SweepArgs); gz = grid planes (nz for
 // modes 0 and 1, an upper bound of the window length for mode 2).  Odd steps
 // sweep the planes in descending order.

@@ -22,6 +22,21 @@
 
 namespace lbsq {
 
+// Rate constants of the collision, computed once per sweep (FP64 and FP32):
+// le, le / 3, 1 - le, -le / 2, -lo / 2, 3 lo / 18, 3 lo / 36.
+struct TrtK {
+    double d[7];
+    float f[7];
+};
+__host__ __device__ inline TrtK trt_constants(double le, double lo) {
+    TrtK k;
+    const double v[7] = {le, le / 3.0, 1.0 - le, -0.5 * le, -0.5 * lo, 3.0 * lo / 18.0, 3.0 * lo / 36.0};
+    for (int i = 0; i < 7; ++i) {
+        k.d[i] = v[i];
+        k.f[i] = (float)v[i];
+    }
+    return k;
+}
 struct SweepArgs {
     void* F;
     int nx, ny, nz;
@@ -31,6 +46,7 @@ struct SweepArgs {
     // z-window split: mode 0 sweeps every plane; mode 1 ("far") the planes
     // outside the window win[0..1] = (z0, length); mode 2 ("near") the planes
     // inside it, blockIdx.z counting from z0
+    TrtK K;  // collision constants (trt_constants)
     int zmode;
     const int* win;
     // planes in descending order (blocks are dispatched roughly in blockIdx
@@ -55,54 +71,114 @@ __device__ __forceinline__ int sweep_plane(const SweepArgs& a) {
     return rel < len ? -1 : bz;
 }
 
-template <class R, bool DEV>
-__device__ __forceinline__ void collide_trt(R g[Q], R le, R lo, R rho0) {
-    // pair sums and differences
-    R s[10], d[10];
-#pragma unroll
-    for (int p = 1; p <= 9; ++p) {
-        s[p] = g[2 * p - 1] + g[2 * p];
-        d[p] = g[2 * p - 1] - g[2 * p];
-    }
-    R sum = g[0];
-#pragma unroll
-    for (int p = 1; p <= 9; ++p) sum += s[p];
-    R jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-    for (int p = 1; p <= 9; ++p) {
-        if (cx(2 * p - 1) == 1) jx += d[p];
-        if (cx(2 * p - 1) == -1) jx -= d[p];
-        if (cy(2 * p - 1) == 1) jy += d[p];
-        if (cy(2 * p - 1) == -1) jy -= d[p];
-        if (cz(2 * p - 1) == 1) jz += d[p];
-        if (cz(2 * p - 1) == -1) jz -= d[p];
-    }
-    const R rho = DEV ? rho0 + sum : sum;
-    const R inv = R(1) / rho;
-    const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
-    const R ju = jx * ux + jy * uy + jz * uz;  // rho u.u
-    // base = (feq+ of the rest class) / w, minus rho0 for deviations
-    const R base = (DEV ? sum : rho) - R(1.5) * ju;
-    g[0] = g[0] + le * (R(1.0 / 3.0) * base - g[0]);
-    const R hle = R(0.5) * le, hlo = R(0.5) * lo;
+// Arithmetic of the collision with every rounding spelled out (no contraction
+// left to the compiler), so that every sweep form -- one, two or four cells
+// per thread, the server's tiles -- gives a cell the same bits.
+template <class V> struct Ar;
+template <> struct Ar<double> {
+    __device__ static double c(double x) { return x; }
+    __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+    __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ static double rcp(double a) { return __ddiv_rn(1.0, a); }
+};
+template <> struct Ar<float> {
+    __device__ static float c(double x) { return (float)x; }
+    __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+    __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    __device__ static float rcp(float a) { return __fdiv_rn(1.0f, a); }
+};
+// Signed sum over the nine velocity pairs of the component c(2p - 1) of the
+// pair's first member times d[p].  The first member of every pair has a
+// leading +1, and the first pair with a nonzero component has it positive,
+// so the sum starts from a term, never from zero, and needs no negation.
+template <class V, int AX>
+__device__ __forceinline__ V pair_moment(const V d[10]) {
+    using A = Ar<V>;
+    V acc{};
+    bool first = true;
 #pragma unroll
     for (int p = 1; p <= 9; ++p) {
         const int i = 2 * p - 1;
-        const R w = (R)wgt(i);
-        R cu = R(0), cj = R(0);
-        if (cx(i) == 1) { cu += ux; cj += jx; }
-        if (cx(i) == -1) { cu -= ux; cj -= jx; }
-        if (cy(i) == 1) { cu += uy; cj += jy; }
-        if (cy(i) == -1) { cu -= uy; cj -= jy; }
-        if (cz(i) == 1) { cu += uz; cj += jz; }
-        if (cz(i) == -1) { cu -= uz; cj -= jz; }
-        const R ep = w * base + R(4.5) * w * (cu * cj);
-        const R E = le * ep - hle * s[p];
-        const R O = (R(3) * lo) * w * cj - hlo * d[p];
-        g[i] = g[i] + (E + O);
-        g[i + 1] = g[i + 1] + (E - O);
+        const int c = AX == 0 ? cx(i) : (AX == 1 ? cy(i) : cz(i));
+        if (c == 0) continue;
+        if (first) acc = d[p];
+        else acc = c > 0 ? A::add(acc, d[p]) : A::sub(acc, d[p]);
+        first = false;
+    }
+    return acc;
+}
+
+// c_i . v for the first member i of a pair (leading component +1).
+template <class V>
+__device__ __forceinline__ V pair_dot(int i, V x, V y, V z) {
+    using A = Ar<V>;
+    const int a = cx(i), b = cy(i), c = cz(i);
+    if (a != 0 && b != 0) return b > 0 ? A::add(x, y) : A::sub(x, y);
+    if (a != 0 && c != 0) return c > 0 ? A::add(x, z) : A::sub(x, z);
+    if (b != 0 && c != 0) return c > 0 ? A::add(y, z) : A::sub(y, z);
+    return a != 0 ? x : (b != 0 ? y : z);
+}
+
+// TRT collision (Sec. III) of one cell (V = double or float), in pair form: with s = g_i + g_ib and d = g_i - g_ib for the nine pairs,
+//   g_0 += le (f_0^eq - g_0),
+//   g_i  += E + O,  g_ib += E - O,
+//   E = le (w_i base + 9/2 w_i (c_i.u)(c_i.j)) - le/2 s,  O = 3 lo w_i c_i.j - lo/2 d,
+// base = rho - 3/2 rho u.u (deviations: rho - rho0 - 3/2 rho u.u), u = j / rho.
+// DEV: g holds deviations f - w rho0 (rho = rho0 + sum g).
+template <class V> __device__ __forceinline__ const V* trt_k(const TrtK& k);
+template <> __device__ __forceinline__ const double* trt_k<double>(const TrtK& k) { return k.d; }
+template <> __device__ __forceinline__ const float* trt_k<float>(const TrtK& k) { return k.f; }
+
+template <class V, bool DEV>
+__device__ __forceinline__ void collide_trt(V g[Q], const TrtK& K, V rho0) {
+    using A = Ar<V>;
+    const V* k = trt_k<V>(K);
+    const V le = k[0];
+    V s[10], d[10];
+#pragma unroll
+    for (int p = 1; p <= 9; ++p) {
+        s[p] = A::add(g[2 * p - 1], g[2 * p]);
+        d[p] = A::sub(g[2 * p - 1], g[2 * p]);
+    }
+    V sum = g[0];
+#pragma unroll
+    for (int p = 1; p <= 9; ++p) sum = A::add(sum, s[p]);
+    const V jx = pair_moment<V, 0>(d), jy = pair_moment<V, 1>(d), jz = pair_moment<V, 2>(d);
+    const V rho = DEV ? A::add(rho0, sum) : sum;
+    const V inv = A::rcp(rho);
+    const V ux = A::mul(jx, inv), uy = A::mul(jy, inv), uz = A::mul(jz, inv);
+    const V ju = A::fma(jz, uz, A::fma(jy, uy, A::mul(jx, ux)));  // rho u.u
+    const V base = A::fma(A::c(-1.5), ju, DEV ? sum : rho);
+    // g_0 + le (base / 3 - g_0) = (le / 3) base + (1 - le) g_0
+    g[0] = A::fma(k[1], base, A::mul(k[2], g[0]));
+    const V mhle = k[3], mhlo = k[4], lw18 = k[5], lw36 = k[6];
+    const V wb18 = A::mul(A::c(1.0 / 18.0), base), wb36 = A::mul(A::c(1.0 / 36.0), base);
+#pragma unroll
+    for (int p = 1; p <= 9; ++p) {
+        const int i = 2 * p - 1;
+        const bool face = i < 7;
+        const V cu = pair_dot<V>(i, ux, uy, uz), cj = pair_dot<V>(i, jx, jy, jz);
+        const V ep = A::fma(A::c(face ? 4.5 / 18.0 : 4.5 / 36.0), A::mul(cu, cj), face ? wb18 : wb36);
+        const V E = A::fma(le, ep, A::mul(mhle, s[p]));
+        const V O = A::fma(face ? lw18 : lw36, cj, A::mul(mhlo, d[p]));
+        g[i] = A::add(g[i], A::add(E, O));
+        g[i + 1] = A::add(g[i + 1], A::sub(E, O));
     }
 }
+
+// 16-bit storages hold the deviations times a power of two s (FP16: 2^k,
+// BF16: 1).  The collision is homogeneous of degree one in (g, rho0) -- u =
+// j / rho does not change, every other term scales by s -- and scaling by a
+// power of two commutes with every FP32 rounding (products, quotients, sums
+// and FMAs alike, barring overflow and subnormals, far from these values).
+// So the sweep collides the stored values as they are, with rho0 s for rho0,
+// and gets the same bits as descaling, colliding and rescaling would, without
+// a multiply per population.
+template <int S> constexpr bool kScaled = S == ST_F16 || S == ST_BF16;
 
 // One cell (x, y, z).
 template <int S, int P>
@@ -116,7 +192,9 @@ __device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int 
     const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
     T* __restrict__ F = (T*)a.F;
     const int64_t Np = a.Np;
-    const R isc = (R)a.inv_scale, sc = (R)a.scale;
+    // 16-bit storages collide in their scaled units (see kScaled)
+    const R isc = kScaled<S> ? R(1) : (R)a.inv_scale, sc = kScaled<S> ? R(1) : (R)a.scale;
+    const R rho0 = kScaled<S> ? (R)a.rho0 * (R)a.scale : (R)a.rho0;
     R g[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -130,7 +208,7 @@ __device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int 
         }
         g[i] = ST::load(F + off, isc);
     }
-    collide_trt<R, ST::dev>(g, (R)a.lambda_e, (R)a.lambda_o, (R)a.rho0);
+    collide_trt<R, ST::dev>(g, a.K, rho0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         int64_t off;
@@ -162,6 +240,18 @@ template <> __device__ __forceinline__ float enc<ST_F32>(float v, float) { retur
 template <> __device__ __forceinline__ __half enc<ST_F16>(float v, float sc) { return __float2half_rn(v * sc); }
 template <> __device__ __forceinline__ __nv_bfloat16 enc<ST_BF16>(float v, float sc) { return __float2bfloat16_rn(v * sc); }
 
+// Encode two values into the storage's pair type (one packed conversion for
+// the 16-bit storages; each half rounds as enc would).
+template <int S> __device__ __forceinline__ typename Pair<typename StoreT<S>::T>::V enc2(float a, float b, float sc);
+template <> __device__ __forceinline__ float2 enc2<ST_F32>(float a, float b, float) { return make_float2(a, b); }
+template <> __device__ __forceinline__ __half2 enc2<ST_F16>(float a, float b, float sc) {
+    return __floats2half2_rn(a * sc, b * sc);
+}
+template <> __device__ __forceinline__ __nv_bfloat162 enc2<ST_BF16>(float a, float b, float sc) {
+    return __floats2bfloat162_rn(a * sc, b * sc);
+}
+template <> __device__ __forceinline__ double2 enc2<ST_F64>(float, float, float) { return make_double2(0.0, 0.0); }
+
 // Two cells (x0, x0 + 1), x0 even; nx must be even.  Paired (vector)
 // accesses wherever both cells' slots are adjacent and aligned: all
 // directions on even steps, the directions with c_x = 0 on odd steps; scalar
@@ -182,7 +272,8 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
     const int xp1 = x0 + 2 == nx ? 0 : x0 + 2;  // x0 + 2
     T* __restrict__ F = (T*)a.F;
     const int64_t Np = a.Np;
-    const float isc = a.inv_scale, sc = a.scale;
+    const float isc = kScaled<S> ? 1.0f : a.inv_scale, sc = kScaled<S> ? 1.0f : a.scale;
+    const R rho0 = kScaled<S> ? (R)a.rho0 * (R)a.scale : (R)a.rho0;
     auto row = [&](int dy, int dz) -> int64_t { return (int64_t)nx * (ys[1 + dy] + (int64_t)ny * zs[1 + dz]); };
     R g0[Q], g1[Q];
 #pragma unroll
@@ -206,23 +297,194 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
             }
         }
     }
-    collide_trt<R, ST::dev>(g0, (R)a.lambda_e, (R)a.lambda_o, (R)a.rho0);
-    collide_trt<R, ST::dev>(g1, (R)a.lambda_e, (R)a.lambda_o, (R)a.rho0);
+    collide_trt<R, ST::dev>(g0, a.K, rho0);
+    collide_trt<R, ST::dev>(g1, a.K, rho0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (P == 0) {
-            *reinterpret_cast<V*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0) =
-                PV::make(enc<S>(g0[i], sc), enc<S>(g1[i], sc));
+            *reinterpret_cast<V*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0) = enc2<S>(g0[i], g1[i], sc);
         } else {
             T* base = F + (int64_t)i * Np + row(cy(i), cz(i));
             if (cx(i) == 0) {
-                *reinterpret_cast<V*>(base + x0) = PV::make(enc<S>(g0[i], sc), enc<S>(g1[i], sc));
+                *reinterpret_cast<V*>(base + x0) = enc2<S>(g0[i], g1[i], sc);
             } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
                 base[x0 + 1] = enc<S>(g0[i], sc);
                 base[xp1] = enc<S>(g1[i], sc);
             } else {  // targets x0 - 1 and x0
                 base[xm0] = enc<S>(g0[i], sc);
                 base[x0] = enc<S>(g1[i], sc);
+            }
+        }
+    }
+}
+
+template <int S> __device__ __forceinline__ float dec16(unsigned int h, float isc);
+template <> __device__ __forceinline__ float dec16<ST_F16>(unsigned int h, float isc) {
+    return __half2float(__ushort_as_half((unsigned short)h)) * isc;
+}
+template <> __device__ __forceinline__ float dec16<ST_BF16>(unsigned int h, float isc) {
+    return __bfloat162float(__ushort_as_bfloat16((unsigned short)h)) * isc;
+}
+template <int S> __device__ __forceinline__ unsigned int enc16(float v, float sc);
+template <> __device__ __forceinline__ unsigned int enc16<ST_F16>(float v, float sc) {
+    return __half_as_ushort(__float2half_rn(v * sc));
+}
+template <> __device__ __forceinline__ unsigned int enc16<ST_BF16>(float v, float sc) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v * sc));
+}
+
+// 16-bit storages, two cells (x0, x0 + 1) per thread, x0 even: the 19 values
+// of the pair stay packed (e0 | e1 << 16) in 19 registers and the cells are
+// decoded, collided and encoded back one at a time, so the kernel fits three
+// blocks of 256 threads per SM (the 16-bit sweep is short of warps to hide
+// its latency, not of memory instructions).  Loads and stores as sweep_two,
+// with 32-bit element offsets (requires 19 Np < 2^31).
+template <int S, int P>
+__device__ __forceinline__ void sweep_two16(const SweepArgs& a, int x0, int y, int z) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    // element offsets fit 32 bits (19 Np < 2^31, checked at launch)
+    const unsigned int Np = (unsigned int)a.Np, unx = (unsigned int)nx;
+    const unsigned int ys[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1), (unsigned)y, (unsigned)(y == ny - 1 ? 0 : y + 1)};
+    const unsigned int zs[3] = {(unsigned)(z == 0 ? nz - 1 : z - 1), (unsigned)z, (unsigned)(z == nz - 1 ? 0 : z + 1)};
+    const unsigned int xm0 = x0 == 0 ? nx - 1 : x0 - 1;  // x0 - 1
+    const unsigned int xp1 = x0 + 2 == nx ? 0 : x0 + 2;  // x0 + 2
+    const unsigned int ux0 = (unsigned)x0;
+    unsigned short* F = (unsigned short*)a.F;
+    const float rho0 = (float)a.rho0 * a.scale;  // scaled units (see kScaled)
+    auto row = [&](int dy, int dz) -> unsigned int { return unx * (ys[1 + dy] + (unsigned)ny * zs[1 + dz]); };
+    unsigned int g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (P == 0) {
+            g[i] = *reinterpret_cast<const unsigned int*>(F + ((unsigned)i * Np + row(0, 0) + ux0));
+        } else {
+            const unsigned int base = (unsigned)opp(i) * Np + row(-cy(i), -cz(i));
+            if (cx(i) == 0) g[i] = *reinterpret_cast<const unsigned int*>(F + (base + ux0));
+            else if (cx(i) == 1) g[i] = (unsigned int)F[base + xm0] | ((unsigned int)F[base + ux0] << 16);
+            else g[i] = (unsigned int)F[base + ux0 + 1] | ((unsigned int)F[base + xp1] << 16);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        float gc[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) gc[i] = dec16<S>(c ? (g[i] >> 16) : (g[i] & 0xffffu), 1.0f);
+        collide_trt<float, true>(gc, a.K, rho0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const unsigned int e = enc16<S>(gc[i], 1.0f);
+            g[i] = c ? ((g[i] & 0xffffu) | (e << 16)) : ((g[i] & 0xffff0000u) | e);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (P == 0) {
+            *reinterpret_cast<unsigned int*>(F + ((unsigned)opp(i) * Np + row(0, 0) + ux0)) = g[i];
+        } else {
+            const unsigned int base = (unsigned)i * Np + row(cy(i), cz(i));
+            if (cx(i) == 0) {
+                *reinterpret_cast<unsigned int*>(F + (base + ux0)) = g[i];
+            } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
+                F[base + ux0 + 1] = (unsigned short)(g[i] & 0xffffu);
+                F[base + xp1] = (unsigned short)(g[i] >> 16);
+            } else {  // targets x0 - 1 and x0
+                F[base + xm0] = (unsigned short)(g[i] & 0xffffu);
+                F[base + ux0] = (unsigned short)(g[i] >> 16);
+            }
+        }
+    }
+}
+
+// 16-bit storages, four cells per thread.  A warp sweeps 128 consecutive
+// cells x0 .. x0 + 127 of one row (lane l: x0 + 4l .. x0 + 4l + 3), so every
+// population plane is read and written in aligned 8-byte chunks.  On odd
+// steps the x-shifted directions need the chunk moved by one cell: the
+// missing element comes from the neighbouring lane by a shuffle, and only
+// lanes 0 and 31 touch the single element beyond the warp's cells (with the
+// periodic wrap at the row ends).  Requires nx % 128 == 0 and 19 Np < 2^31
+// (32-bit element offsets keep the address arithmetic light).  The per-cell
+// arithmetic is that of sweep_one, so the results are the same bit for bit.
+template <int S, int P>
+__device__ __forceinline__ void sweep_four(const SweepArgs& a, int x0, int y, int z, int lane) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    // element offsets fit 32 bits (19 Np < 2^31, checked at launch)
+    const unsigned int Np = (unsigned int)a.Np, unx = (unsigned int)nx;
+    const unsigned int ys[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1), (unsigned)y, (unsigned)(y == ny - 1 ? 0 : y + 1)};
+    const unsigned int zs[3] = {(unsigned)(z == 0 ? nz - 1 : z - 1), (unsigned)z, (unsigned)(z == nz - 1 ? 0 : z + 1)};
+    const unsigned int xl = x0 == 0 ? nx - 1 : x0 - 1;  // the element left of the lane's chunk
+    const unsigned int xr = x0 + 4 == nx ? 0 : x0 + 4;  // and right of it
+    unsigned short* F = (unsigned short*)a.F;
+    const float isc = 1.0f, sc = 1.0f, rho0 = (float)a.rho0 * a.scale;  // scaled units (see kScaled)
+    auto row = [&](int dy, int dz) -> unsigned int { return unx * (ys[1 + dy] + (unsigned)ny * zs[1 + dz]); };
+    // chunk of 4 packed elements: .x = e0 | e1 << 16, .y = e2 | e3 << 16
+    uint2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (P == 0) {
+            g[i] = *reinterpret_cast<const uint2*>(F + ((unsigned)i * Np + row(0, 0) + x0));
+        } else {
+            const unsigned int base = (unsigned)opp(i) * Np + row(-cy(i), -cz(i));
+            const uint2 c = *reinterpret_cast<const uint2*>(F + (base + x0));
+            if (cx(i) == 0) {
+                g[i] = c;
+            } else if (cx(i) == 1) {  // sources x0 - 1 .. x0 + 2
+                unsigned int prev = __shfl_up_sync(kAll, c.y, 1) >> 16;
+                if (lane == 0) prev = F[base + xl];
+                g[i] = make_uint2(prev | (c.x << 16), (c.x >> 16) | (c.y << 16));
+            } else {  // sources x0 + 1 .. x0 + 4
+                unsigned int next = __shfl_down_sync(kAll, c.x, 1) & 0xffffu;
+                if (lane == 31) next = F[base + xr];
+                g[i] = make_uint2((c.x >> 16) | (c.y << 16), (c.y >> 16) | (next << 16));
+            }
+        }
+    }
+    // collide the cells one at a time, each result back into its 16-bit slot
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float gc[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const unsigned int w = c < 2 ? g[i].x : g[i].y;
+            gc[i] = dec16<S>((c & 1) ? (w >> 16) : (w & 0xffffu), isc);
+        }
+        collide_trt<float, true>(gc, a.K, rho0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const unsigned int e = enc16<S>(gc[i], sc);
+            unsigned int& w = c < 2 ? g[i].x : g[i].y;
+            w = (c & 1) ? ((w & 0xffffu) | (e << 16)) : ((w & 0xffff0000u) | e);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const uint2 o = g[i];  // post-collision f_i of cells x0 .. x0 + 3
+        if (P == 0) {
+            *reinterpret_cast<uint2*>(F + ((unsigned)opp(i) * Np + row(0, 0) + x0)) = o;
+        } else {
+            const unsigned int base = (unsigned)i * Np + row(cy(i), cz(i));
+            if (cx(i) == 0) {
+                *reinterpret_cast<uint2*>(F + (base + x0)) = o;
+            } else if (cx(i) == 1) {  // targets x0 + 1 .. x0 + 4
+                const unsigned int prev3 = __shfl_up_sync(kAll, o.y, 1) >> 16;
+                if (lane != 0) {
+                    *reinterpret_cast<uint2*>(F + (base + x0)) =
+                        make_uint2(prev3 | (o.x << 16), (o.x >> 16) | (o.y << 16));
+                } else {  // element x0 comes from the warp to the left
+                    F[base + x0 + 1] = (unsigned short)(o.x & 0xffffu);
+                    *reinterpret_cast<unsigned int*>(F + (base + x0 + 2)) = (o.x >> 16) | (o.y << 16);
+                }
+                if (lane == 31) F[base + xr] = (unsigned short)(o.y >> 16);
+            } else {  // targets x0 - 1 .. x0 + 2
+                const unsigned int next0 = __shfl_down_sync(kAll, o.x, 1) & 0xffffu;
+                if (lane != 31) {
+                    *reinterpret_cast<uint2*>(F + (base + x0)) =
+                        make_uint2((o.x >> 16) | (o.y << 16), (o.y >> 16) | (next0 << 16));
+                } else {  // element x0 + 3 comes from the warp to the right
+                    *reinterpret_cast<unsigned int*>(F + (base + x0)) = (o.x >> 16) | (o.y << 16);
+                    F[base + x0 + 2] = (unsigned short)(o.y >> 16);
+                }
+                if (lane == 0) F[base + xl] = (unsigned short)(o.x & 0xffffu);
             }
         }
     }
@@ -238,6 +500,7 @@ __host__ __device__ inline SweepArgs sweep_args(const Lattice& L, double lambda_
     a.Np = L.Np;
     a.lambda_e = lambda_e;
     a.lambda_o = lambda_o;
+    a.K = trt_constants(lambda_e, lambda_o);
     a.rho0 = L.rho0;
     a.scale = L.scale;
     a.inv_scale = L.inv_scale;
