@@ -350,6 +350,23 @@ def precision_sweep(torch, device=0, steps=None):
             "stresslet_zz_closed_form": S_closed, "v0": v0, "storages": out}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """x maximised over all ranks (a replica job takes as long as its slowest
+    rank); x itself without a process group."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(cells_per_rank: int, steps: int, ranks: int, total_ms: float) -> float:
+    """Whole-job throughput of `ranks` replicas that each advanced
+    cells_per_rank cells by `steps` steps in total_ms (max over ranks)."""
+    return ranks * cells_per_rank * steps / (total_ms * 1e-3) / 1e6
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
@@ -394,13 +411,9 @@ def ours(args):
     n_traced = min(args.steps, 400)
     traced_ms, prof = traced_steps(g, n_traced, flush, torch)
     g.close()
-    total_ms = sum(step_ms)
-    if dist:
-        tt = torch.tensor([total_ms], device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, f"cuda:{local}")
     cells = wl.cells
-    value = ws * cells * args.steps / (total_ms * 1e-3) / 1e6
+    value = job_mlups(cells, args.steps, ws, total_ms)
     sweep_ms = prof["sweep"][0] / max(prof["sweep"][1], 1)
     sweep_bytes = cells * 2 * 19 * BYTES[head]
     achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9
@@ -422,10 +435,17 @@ def ours(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": ncu_traffic(f"sweep_{head}_{wl.name}"),
-                     "kernel": "k_sweep", "bytes_per_launch": sweep_bytes,
+                     "kernel": ("k_sweep (one cell per thread)" if head == "f64"
+                                else "k_sweep2 (two cells per thread)"),
+                     "bytes_per_launch": sweep_bytes,
                      "per_unit": f"2*19*{BYTES[head]} B per cell update", "peak_kind": peak_kind,
                      "sweep_ms": sweep_ms},
         "kernels_ms_per_step": {k: v[0] / max(v[1], 1) * (v[1] / n_traced) for k, v in prof.items()},
+        "kernels_note": ("links = k_body_fused (bounce-back, force, Newton-Euler, re-classification, "
+                         "conversions and link rebuild of each isolated sphere, one thread-block cluster "
+                         "per sphere) plus k_links (walls); classify / convert / rebuild = the multi-kernel "
+                         "path for spheres near another body (launched empty otherwise; not launched at all "
+                         "for a lattice with a single sphere outside the traced pass)"),
         "traced": {"steps": n_traced, "ms_per_step": sum(traced_ms) / n_traced,
                    "note": "kernel-by-kernel launches with CUDA events between kernels, right after the "
                            "timed region; source of the per-kernel times and of the roofline's sweep time"},
