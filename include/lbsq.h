@@ -214,13 +214,18 @@ const char* lb_last_error(const lb_ctx* c);
 int64_t lb_kernel_launches(const lb_ctx* c);
 
 /* Tuning: the launch shape of the stream-collide kernel.  0 = default
- * (reduced storages with even nx: two cells per thread with paired loads and
- * the two cells collided together on the packed FP32 pipe; FP64: one cell),
+ * (FP16 / BF16 storage: even steps as 6, odd steps as 2; FP32 with even nx:
+ * two cells per thread with paired loads; FP64: one cell),
  * 1 = one cell per thread, 2 = two cells per thread where nx is even, 3 =
  * FP16 / BF16 storage: four cells per thread in aligned 8-byte chunks where
  * nx is a multiple of 128 (else as 2), 4 = FP16 / BF16: two cells per thread
- * with the values kept packed (else as 2).  Results are identical bit for
- * bit; only the speed differs.  LB_ERR_INVALID for another value. */
+ * with the values kept packed (else as 2), 5 = FP16 / BF16: two cells per
+ * thread on four consecutive planes, the loads of the next plane issued
+ * before the collision of the current one (else as 2), 6 = FP16 / BF16: four
+ * cells per thread in blocks of whole rows, the odd-step x-shifts through
+ * shared memory (nx a multiple of 4 up to 768; else as 2).  Results are
+ * identical bit for bit; only the speed differs.  LB_ERR_INVALID for another
+ * value. */
 lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant);
 
 /* Kernel tracing.  Between lb_profile_begin and lb_profile_end, lb_step

@@ -933,7 +933,7 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
 }
 
 lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant) {
-    if (!c || variant < 0 || variant > 4) return LB_ERR_INVALID;
+    if (!c || variant < 0 || variant > 6) return LB_ERR_INVALID;
     c->sweep_variant = variant;
     drop_graph(c);
     return LB_OK;

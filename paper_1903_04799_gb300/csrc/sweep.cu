@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(256, 3) k_sweep2p(const SweepArgs a) {
 
 // 16-bit storages with nx % 128 == 0 and 19 Np < 2^31: a warp per 128 cells
 // of a row, eight rows per block (see sweep_four).
-template <int S, int P>
-__global__ void __launch_bounds__(256, 2) k_sweep4(const SweepArgs a) {
+template <int S, int P, int ROWS>
+__global__ void __launch_bounds__(32 * ROWS, 2) k_sweep4(const SweepArgs a) {
     const int lane = threadIdx.x;
     const int x0 = 128 * blockIdx.x + 4 * lane;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -50,13 +50,81 @@ __global__ void __launch_bounds__(256, 2) k_sweep4(const SweepArgs a) {
     sweep_four<S, P>(a, x0, y, z, lane);
 }
 
+// 16-bit storages, two cells per thread on kPlanes consecutive plane slots,
+// software-pipelined (see load_pair16).
+constexpr int kPlanes = 4;
+
+template <int S, int P>
+__global__ void __launch_bounds__(256, 2) k_sweep2z(const SweepArgs a, int slots) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= a.nx || y >= a.ny) return;
+    const int p0 = blockIdx.z * kPlanes;
+    unsigned int cur[Q], nxt[Q];
+    int z = sweep_plane_at(a, p0);
+    if (z >= 0) load_pair16<S, P>(a, x0, y, z, cur);
+    for (int k = 0; k < kPlanes && p0 + k < slots; ++k) {
+        const int zn = (k + 1 < kPlanes && p0 + k + 1 < slots) ? sweep_plane_at(a, p0 + k + 1) : -1;
+        if (zn >= 0) load_pair16<S, P>(a, x0, y, zn, nxt);  // in flight during the collision below
+        if (z >= 0) collide_store_pair16<S, P>(a, x0, y, z, cur);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
+        z = zn;
+    }
+}
+
+// 16-bit storages with nx % 4 == 0, nx <= 768: blocks of whole rows, four
+// cells per thread (see sweep_four_rows); dynamic shared memory of
+// 10 x rows x nx elements on odd steps.
+template <int S, int P>
+__global__ void __launch_bounds__(P == 0 ? 256 : 192, 2) k_sweep4r(const SweepArgs a) {
+    extern __shared__ unsigned short rowbuf[];
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = sweep_plane(a);
+    if (z < 0) return;  // the whole block
+    sweep_four_rows<S, P>(a, y, z, y < a.ny, rowbuf);
+}
+
 template <int S>
 static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaStream_t st) {
     if constexpr (S == ST_F16 || S == ST_BF16) {
+        if (variant == 5 && a.nx % 2 == 0) {
+            const int pairs = a.nx / 2;
+            int bx = ((pairs + 31) / 32) * 32;
+            if (bx > 128) bx = 128;
+            const int by = 256 / bx;
+            dim3 block(bx, by), grid((pairs + bx - 1) / bx, (a.ny + by - 1) / by, (gz + kPlanes - 1) / kPlanes);
+            if (parity == 0) k_sweep2z<S, 0><<<grid, block, 0, st>>>(a, gz);
+            else k_sweep2z<S, 1><<<grid, block, 0, st>>>(a, gz);
+            return;
+        }
+        // default: even steps in whole-row four-cell blocks (aligned 8-byte
+        // chunks: 0.86 of the copy bandwidth at 256^3, against 0.74 for two
+        // cells), odd steps in the two-cell form (0.63; the whole-row form's
+        // odd steps, with their x-shifts through shared memory, measured 0.62)
+        const bool rows4 = a.nx % 4 == 0 && a.nx <= 768;
+        if ((variant == 6 || (variant == 0 && parity == 0)) && rows4) {
+            // odd steps (more live values) in blocks of at most 192 threads
+            const int tx = a.nx / 4, ty = (parity == 0 ? 256 : 192) / tx > 0 ? (parity == 0 ? 256 : 192) / tx : 1;
+            dim3 block(tx, ty), grid(1, (a.ny + ty - 1) / ty, gz);
+            if (parity == 0) {
+                k_sweep4r<S, 0><<<grid, block, 0, st>>>(a);
+            } else {
+                const size_t smem = (size_t)10 * ty * a.nx * sizeof(unsigned short);
+                k_sweep4r<S, 1><<<grid, block, smem, st>>>(a);
+            }
+            return;
+        }
         if (variant == 3 && a.nx % 128 == 0 && 19 * a.Np < (int64_t(1) << 31)) {
-            dim3 block(32, 8), grid(a.nx / 128, (a.ny + 7) / 8, gz);
-            if (parity == 0) k_sweep4<S, 0><<<grid, block, 0, st>>>(a);
-            else k_sweep4<S, 1><<<grid, block, 0, st>>>(a);
+            // odd steps hold more live values (the x-shifted chunks): 6 rows per
+            // block leave them 170 registers a thread at 2 blocks per SM
+            if (parity == 0) {
+                dim3 block(32, 8), grid(a.nx / 128, (a.ny + 7) / 8, gz);
+                k_sweep4<S, 0, 8><<<grid, block, 0, st>>>(a);
+            } else {
+                dim3 block(32, 6), grid(a.nx / 128, (a.ny + 5) / 6, gz);
+                k_sweep4<S, 1, 6><<<grid, block, 0, st>>>(a);
+            }
             return;
         }
     }
@@ -86,10 +154,14 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaSt
     else k_sweep<S, 1><<<grid, bx, 0, st>>>(a);
 }
 
-// variant: 0 = default (reduced storages with even nx: two cells per thread;
-// FP64: one), 1 = one cell per thread, 2 = two cells per thread where
+// variant: 0 = default (FP16 / BF16: even steps as 6, odd steps as 2; other
+// reduced storages with even nx: two cells per thread; FP64: one), 1 = one
+// cell per thread, 2 = two cells per thread where
 // possible, 3 = FP16 / BF16: four cells per thread where possible (else as
-// 2), 4 = FP16 / BF16: two cells per thread, packed (else as 2).
+// 2), 4 = FP16 / BF16: two cells per thread, packed (else as 2), 5 = FP16 /
+// BF16: two cells per thread on kPlanes planes, software-pipelined (else as 2),
+// 6 = FP16 / BF16: four cells per thread in blocks of whole rows, odd-step
+// x-shifts through shared memory (nx % 4 == 0, nx <= 768; else as 2).
 // zmode / win / gz: plane selection (see SweepArgs); gz = grid planes (nz for
 // modes 0 and 1, an upper bound of the window length for mode 2).  Odd steps
 // sweep the planes in descending order.

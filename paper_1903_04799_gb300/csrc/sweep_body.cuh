@@ -56,9 +56,9 @@ struct SweepArgs {
     int reverse;
 };
 
-// Plane swept by this block, or -1 if none.
-__device__ __forceinline__ int sweep_plane(const SweepArgs& a) {
-    int bz = blockIdx.z;
+// Plane of plane slot bz (grid z index, or a block's k-th plane in the
+// multi-plane form), or -1 if none.
+__device__ __forceinline__ int sweep_plane_at(const SweepArgs& a, int bz) {
     if (a.zmode == 0) return a.reverse ? a.nz - 1 - bz : bz;
     const int z0 = __ldg(a.win), len = __ldg(a.win + 1);
     if (a.zmode == 2) {
@@ -70,6 +70,9 @@ __device__ __forceinline__ int sweep_plane(const SweepArgs& a) {
     const int rel = bz - z0 < 0 ? bz - z0 + a.nz : bz - z0;
     return rel < len ? -1 : bz;
 }
+
+// Plane swept by this block, or -1 if none.
+__device__ __forceinline__ int sweep_plane(const SweepArgs& a) { return sweep_plane_at(a, blockIdx.z); }
 
 // Arithmetic of the collision with every rounding spelled out (no contraction
 // left to the compiler), so that every sweep form -- one, two or four cells
@@ -395,6 +398,78 @@ __device__ __forceinline__ void sweep_two16(const SweepArgs& a, int x0, int y, i
     }
 }
 
+// 16-bit storages, two cells (x0, x0 + 1) per thread on several planes of
+// the same column, software-pipelined: the loads of the next plane are issued
+// before the collision of the current one, so a thread keeps its loads in
+// flight while it computes (the 16-bit sweep is short of bytes in flight per
+// SM).  In-place AA makes this safe: a cell's read and write slots are its own
+// 19 slots, disjoint from any other cell's.  Values stay packed (e0 | e1 <<
+// 16) between load and collision; per-cell arithmetic as sweep_one.
+template <int S, int P>
+__device__ __forceinline__ void load_pair16(const SweepArgs& a, int x0, int y, int z, unsigned int (&g)[Q]) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+    const int xm0 = x0 == 0 ? nx - 1 : x0 - 1;
+    const int xp1 = x0 + 2 == nx ? 0 : x0 + 2;
+    const unsigned short* F = (const unsigned short*)a.F;
+    const int64_t Np = a.Np;
+    auto row = [&](int dy, int dz) -> int64_t { return (int64_t)nx * (ys[1 + dy] + (int64_t)ny * zs[1 + dz]); };
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (P == 0) {
+            g[i] = __ldg(reinterpret_cast<const unsigned int*>(F + (int64_t)i * Np + row(0, 0) + x0));
+        } else {
+            const unsigned short* base = F + (int64_t)opp(i) * Np + row(-cy(i), -cz(i));
+            if (cx(i) == 0) g[i] = __ldg(reinterpret_cast<const unsigned int*>(base + x0));
+            else if (cx(i) == 1) g[i] = (unsigned int)__ldg(base + xm0) | ((unsigned int)__ldg(base + x0) << 16);
+            else g[i] = (unsigned int)__ldg(base + x0 + 1) | ((unsigned int)__ldg(base + xp1) << 16);
+        }
+    }
+}
+
+template <int S, int P>
+__device__ __forceinline__ void collide_store_pair16(const SweepArgs& a, int x0, int y, int z, unsigned int (&g)[Q]) {
+    const float rho0 = (float)a.rho0 * a.scale;  // scaled units (see kScaled)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        float gc[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) gc[i] = dec16<S>(c ? (g[i] >> 16) : (g[i] & 0xffffu), 1.0f);
+        collide_trt<float, true>(gc, a.K, rho0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const unsigned int e = enc16<S>(gc[i], 1.0f);
+            g[i] = c ? ((g[i] & 0xffffu) | (e << 16)) : ((g[i] & 0xffff0000u) | e);
+        }
+    }
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+    const int xm0 = x0 == 0 ? nx - 1 : x0 - 1;
+    const int xp1 = x0 + 2 == nx ? 0 : x0 + 2;
+    unsigned short* F = (unsigned short*)a.F;
+    const int64_t Np = a.Np;
+    auto row = [&](int dy, int dz) -> int64_t { return (int64_t)nx * (ys[1 + dy] + (int64_t)ny * zs[1 + dz]); };
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (P == 0) {
+            *reinterpret_cast<unsigned int*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0) = g[i];
+        } else {
+            unsigned short* base = F + (int64_t)i * Np + row(cy(i), cz(i));
+            if (cx(i) == 0) {
+                *reinterpret_cast<unsigned int*>(base + x0) = g[i];
+            } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
+                base[x0 + 1] = (unsigned short)(g[i] & 0xffffu);
+                base[xp1] = (unsigned short)(g[i] >> 16);
+            } else {  // targets x0 - 1 and x0
+                base[xm0] = (unsigned short)(g[i] & 0xffffu);
+                base[x0] = (unsigned short)(g[i] >> 16);
+            }
+        }
+    }
+}
+
 // 16-bit storages, four cells per thread.  A warp sweeps 128 consecutive
 // cells x0 .. x0 + 127 of one row (lane l: x0 + 4l .. x0 + 4l + 3), so every
 // population plane is read and written in aligned 8-byte chunks.  On odd
@@ -486,6 +561,112 @@ __device__ __forceinline__ void sweep_four(const SweepArgs& a, int x0, int y, in
                 }
                 if (lane == 0) F[base + xl] = (unsigned short)(o.x & 0xffffu);
             }
+        }
+    }
+}
+
+// 16-bit storages, four cells per thread, blocks of whole rows: a row of nx
+// cells is nx / 4 threads (nx % 4 == 0, nx <= 768), so the x-neighbours of
+// every cell, the periodic wrap included, lie in the block.  Every global
+// access is an aligned 8-byte chunk.  On odd steps the ten x-shifted
+// directions go through a shared-memory copy of the rows: loads write the
+// aligned source chunks there and read the shifted elements back; stores
+// write the shifted results there and store the aligned chunks.  `buf` holds
+// 10 x blockDim.y x nx elements.  All threads of the block take part in the
+// barriers (`active`: the thread's row exists).
+template <int S, int P>
+__device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z, bool active, unsigned short* buf) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x0 = 4 * threadIdx.x;
+    const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y >= ny - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+    unsigned short* F = (unsigned short*)a.F;
+    const int64_t Np = a.Np;
+    const float rho0 = (float)a.rho0 * a.scale;  // scaled units (see kScaled)
+    auto row = [&](int dy, int dz) -> int64_t { return (int64_t)nx * (ys[1 + dy] + (int64_t)ny * zs[1 + dz]); };
+    unsigned short* rowbuf = buf + (int64_t)threadIdx.y * nx;  // + d * blockDim.y * nx for shifted direction d
+    const int dstride = blockDim.y * nx;
+    auto at = [&](int x) -> int { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
+    uint2 g[Q];
+    int d = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (P == 0) {
+            if (active) g[i] = *reinterpret_cast<const uint2*>(F + (int64_t)i * Np + row(0, 0) + x0);
+        } else {
+            const unsigned short* base = F + (int64_t)opp(i) * Np + row(-cy(i), -cz(i));
+            if (cx(i) == 0) {
+                if (active) g[i] = *reinterpret_cast<const uint2*>(base + x0);
+            } else {
+                if (active)
+                    *reinterpret_cast<uint2*>(rowbuf + d * dstride + x0) = *reinterpret_cast<const uint2*>(base + x0);
+                ++d;
+            }
+        }
+    }
+    if (P == 1) {
+        __syncthreads();
+        d = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (cx(i) == 0) continue;
+            const unsigned short* r = rowbuf + d * dstride;
+            ++d;
+            // sources x0 - 1 .. x0 + 2 (c_x = +1) or x0 + 1 .. x0 + 4 (c_x = -1)
+            const int s0 = cx(i) == 1 ? x0 - 1 : x0 + 1;
+            unsigned int e[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e[k] = r[at(s0 + k)];
+            g[i] = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+        }
+        __syncthreads();  // the buffer is reused for the stores
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float gc[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const unsigned int w = c < 2 ? g[i].x : g[i].y;
+            gc[i] = dec16<S>((c & 1) ? (w >> 16) : (w & 0xffffu), 1.0f);
+        }
+        collide_trt<float, true>(gc, a.K, rho0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const unsigned int e = enc16<S>(gc[i], 1.0f);
+            unsigned int& w = c < 2 ? g[i].x : g[i].y;
+            w = (c & 1) ? ((w & 0xffffu) | (e << 16)) : ((w & 0xffff0000u) | e);
+        }
+    }
+    d = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const uint2 o = g[i];
+        if (P == 0) {
+            if (active) *reinterpret_cast<uint2*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0) = o;
+        } else if (cx(i) == 0) {
+            if (active) *reinterpret_cast<uint2*>(F + (int64_t)i * Np + row(cy(i), cz(i)) + x0) = o;
+        } else {
+            // targets x0 + 1 .. x0 + 4 (c_x = +1) or x0 - 1 .. x0 + 2 (c_x = -1)
+            unsigned short* r = rowbuf + d * dstride;
+            ++d;
+            const int t0 = cx(i) == 1 ? x0 + 1 : x0 - 1;
+            r[at(t0)] = (unsigned short)(o.x & 0xffffu);
+            r[at(t0 + 1)] = (unsigned short)(o.x >> 16);
+            r[at(t0 + 2)] = (unsigned short)(o.y & 0xffffu);
+            r[at(t0 + 3)] = (unsigned short)(o.y >> 16);
+        }
+    }
+    if (P == 1) {
+        __syncthreads();
+        d = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (cx(i) == 0) continue;
+            const unsigned short* r = rowbuf + d * dstride;
+            ++d;
+            if (active)
+                *reinterpret_cast<uint2*>(F + (int64_t)i * Np + row(cy(i), cz(i)) + x0) =
+                    *reinterpret_cast<const uint2*>(r + x0);
         }
     }
 }

@@ -276,20 +276,23 @@ def test_sweep_variants_bitwise_16bit(storage, nx):
     form (both cells collided together on the packed FP32 pipe), the four-cell
     16-bit form (nx a multiple of 128: a warp per 128 cells, x-shifted chunks
     assembled by shuffles, lanes 0 and 31 handling the elements beyond the
-    warp and the periodic wrap) and the packed two-cell 16-bit form; on both
-    step parities, with a swimmer in the lattice and ragged ny, nz."""
+    warp and the periodic wrap), the packed two-cell 16-bit form and the
+    pipelined multi-plane 16-bit form (nz = 14: a partial last group of
+    planes) and the whole-row four-cell form (odd-step x-shifts through shared
+    memory; ny = 13: blocks with rows beyond the lattice); on both step
+    parities, with a swimmer in the lattice and ragged ny, nz."""
     shape = (nx, 13, 14)
     w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
     f = W.random_populations(int(np.prod(shape)), seed=11, base=w, spread=0.2)
     out = {}
-    for variant in (1, 2, 3, 4):
+    for variant in (1, 2, 3, 4, 5, 6):
         g = Lattice(shape, collision="trt", storage=storage)
         g.set_sweep_variant(variant)
         g.set_populations(f)
         gi = g.add_squirmer((nx / 2 + 0.3, 6.2, 6.9), (1.0, 0.2, 0.1), 3.0, 0.02, -1.0, mobile=True)
         g.step(7)
         out[variant] = (g.populations(), g.state(gi)[0])
-    for v in (2, 3, 4):
+    for v in (2, 3, 4, 5, 6):
         assert np.array_equal(out[v][0], out[1][0]), v
         assert np.array_equal(out[v][1], out[1][1]), v
 
