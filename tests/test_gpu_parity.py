@@ -231,6 +231,58 @@ def test_two_swimmers_f64():
         _compare_bodies(g, o, gids, oids)
 
 
+def _random_spheres(rng, shape, count, R, min_dist):
+    """`count` sphere centres by random sequential addition (minimum-image
+    distance >= min_dist), random unit axes, beta ~ U[-4, 4]."""
+    n = np.array(shape, dtype=float)
+    pts, out = [], []
+    while len(pts) < count:
+        p = rng.uniform(0, n)
+        if all(np.linalg.norm((p - q) - n * np.round((p - q) / n)) >= min_dist for q in pts):
+            e = rng.standard_normal(3)
+            pts.append(p)
+            out.append((tuple(p), tuple(e / np.linalg.norm(e)), R, 0.03, float(rng.uniform(-4, 4))))
+    return out
+
+
+@pytest.mark.parametrize("count,shape,R", [(20, (48, 44, 40), 3.0), (80, (72, 64, 60), 2.6)])
+def test_many_spheres_cluster_classes_f64(count, shape, R):
+    """20 mobile squirmers (the fused kernel at 8 blocks per sphere) and 80 (4
+    blocks), close enough that some grown scan boxes meet, so those spheres
+    re-classify through the multi-kernel path while the rest stay fused:
+    fields, classification, links, forces and states against the oracle."""
+    rng = np.random.default_rng(1000 + count)
+    bodies = _random_spheres(rng, shape, count, R, 2 * R + 2.5)
+    g, o = make_pair(shape, "trt", 1.0)
+    gids = [g.add_squirmer(*b, mobile=True) for b in bodies]
+    oids = [o.add_sphere(*b, mobile=True) for b in bodies]
+    for _ in range(3):
+        g.step(20)
+        o.step(20)
+    _compare_bodies(g, o, gids, oids, R=R)
+
+
+def test_c4_full_size_parity_f64():
+    """The 256^3 suspension of 200 squirmers (R = 6) at full size, in the
+    launch configuration bench.py times, 16 steps: classification, fields and
+    every body's state against the oracle."""
+    wl = W.c4_suspension()
+    g = Lattice(wl.shape, collision="trt", storage="f64")
+    o = OracleSim(*wl.shape, lambda_e=1.0, collision="trt")
+    # B1 raised so that cells change within the run
+    gids = [g.add_squirmer(b.pos, b.e, b.R, 0.05, b.beta, mobile=True) for b in wl.bodies]
+    oids = [o.add_sphere(b.pos, b.e, b.R, 0.05, b.beta, mobile=True) for b in wl.bodies]
+    g.step(16)
+    o.step(16)
+    assert (g.owner() == o.owner()).all()
+    _, ug = g.fields()
+    _, uo = o.fields()
+    assert rel(ug, uo) < 1e-12
+    for gi, oi in zip(gids, oids):
+        for a, b in zip(g.state(gi), o.state(oi)):
+            assert np.abs(a - b).max() < 1e-12
+
+
 def test_determinism_bitwise():
     """The same run twice gives the same bits (fixed-order reductions)."""
     outs = []
