@@ -23,15 +23,16 @@
 namespace lbsq {
 
 // Rate constants of the collision, computed once per sweep (FP64 and FP32):
-// le, le / 3, 1 - le, -le / 2, -lo / 2, 3 lo / 18, 3 lo / 36.
+// le, le / 3, 1 - le, -le / 2, -lo / 2, 3 lo / 18, 3 lo / 36, (1 - lo) / 2.
 struct TrtK {
-    double d[7];
-    float f[7];
+    double d[8];
+    float f[8];
 };
 __host__ __device__ inline TrtK trt_constants(double le, double lo) {
     TrtK k;
-    const double v[7] = {le, le / 3.0, 1.0 - le, -0.5 * le, -0.5 * lo, 3.0 * lo / 18.0, 3.0 * lo / 36.0};
-    for (int i = 0; i < 7; ++i) {
+    const double v[8] = {le,       le / 3.0,         1.0 - le,         -0.5 * le,
+                         -0.5 * lo, 3.0 * lo / 18.0, 3.0 * lo / 36.0, 0.5 * (1.0 - lo)};
+    for (int i = 0; i < 8; ++i) {
         k.d[i] = v[i];
         k.f[i] = (float)v[i];
     }
@@ -156,10 +157,30 @@ __device__ __forceinline__ void collide_trt(V g[Q], const TrtK& K, V rho0) {
     const V ux = A::mul(jx, inv), uy = A::mul(jy, inv), uz = A::mul(jz, inv);
     const V ju = A::fma(jz, uz, A::fma(jy, uy, A::mul(jx, ux)));  // rho u.u
     const V base = A::fma(A::c(-1.5), ju, DEV ? sum : rho);
+    const V lw18 = k[5], lw36 = k[6];
+    const V wb18 = A::mul(A::c(1.0 / 18.0), base), wb36 = A::mul(A::c(1.0 / 36.0), base);
+    if (k[2] == V(0)) {
+        // le = 1 (every TRT and BGK configuration here): the even part relaxes
+        // fully, so with h = (1 - lo)/2 d + 3 lo w (c.j) the pair update is
+        //   g_i = ep + h,  g_ib = ep - h,  g_0 = base / 3,
+        // the general form below with the s terms cancelled exactly.
+        g[0] = A::mul(k[1], base);
+        const V ch = k[7];
+#pragma unroll
+        for (int p = 1; p <= 9; ++p) {
+            const int i = 2 * p - 1;
+            const bool face = i < 7;
+            const V cu = pair_dot<V>(i, ux, uy, uz), cj = pair_dot<V>(i, jx, jy, jz);
+            const V ep = A::fma(A::c(face ? 4.5 / 18.0 : 4.5 / 36.0), A::mul(cu, cj), face ? wb18 : wb36);
+            const V h = A::fma(face ? lw18 : lw36, cj, A::mul(ch, d[p]));
+            g[i] = A::add(ep, h);
+            g[i + 1] = A::sub(ep, h);
+        }
+        return;
+    }
     // g_0 + le (base / 3 - g_0) = (le / 3) base + (1 - le) g_0
     g[0] = A::fma(k[1], base, A::mul(k[2], g[0]));
-    const V mhle = k[3], mhlo = k[4], lw18 = k[5], lw36 = k[6];
-    const V wb18 = A::mul(A::c(1.0 / 18.0), base), wb36 = A::mul(A::c(1.0 / 36.0), base);
+    const V mhle = k[3], mhlo = k[4];
 #pragma unroll
     for (int p = 1; p <= 9; ++p) {
         const int i = 2 * p - 1;

@@ -322,8 +322,8 @@ def test_reduced_storage_free_swimmer(storage, tol):
 
 
 @pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
-@pytest.mark.parametrize("nx", [128, 256])
-def test_sweep_variants_bitwise_16bit(storage, nx):
+@pytest.mark.parametrize("nx,lambda_e", [(128, 1.0), (256, 1.0), (128, 1.3)])
+def test_sweep_variants_bitwise_16bit(storage, nx, lambda_e):
     """Every sweep form gives the same bits as the one-cell form: the two-cell
     form (both cells collided together on the packed FP32 pipe), the four-cell
     16-bit form (nx a multiple of 128: a warp per 128 cells, x-shifted chunks
@@ -332,13 +332,15 @@ def test_sweep_variants_bitwise_16bit(storage, nx):
     pipelined multi-plane 16-bit form (nz = 14: a partial last group of
     planes) and the whole-row four-cell form (odd-step x-shifts through shared
     memory; ny = 13: blocks with rows beyond the lattice); on both step
-    parities, with a swimmer in the lattice and ragged ny, nz."""
+    parities, with a swimmer in the lattice and ragged ny, nz; with lambda_e
+    = 1 (the collision's fully relaxed even part) and 1.3 (the general
+    form)."""
     shape = (nx, 13, 14)
     w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
     f = W.random_populations(int(np.prod(shape)), seed=11, base=w, spread=0.2)
     out = {}
     for variant in (1, 2, 3, 4, 5, 6):
-        g = Lattice(shape, collision="trt", storage=storage)
+        g = Lattice(shape, collision="trt", lambda_e=lambda_e, storage=storage)
         g.set_sweep_variant(variant)
         g.set_populations(f)
         gi = g.add_squirmer((nx / 2 + 0.3, 6.2, 6.9), (1.0, 0.2, 0.1), 3.0, 0.02, -1.0, mobile=True)
