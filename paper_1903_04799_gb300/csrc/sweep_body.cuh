@@ -85,7 +85,18 @@ template <> struct Ar<double> {
     __device__ static double sub(double a, double b) { return __dsub_rn(a, b); }
     __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
     __device__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-    __device__ static double rcp(double a) { return __ddiv_rn(1.0, a); }
+    // 1/a by Newton-Raphson (r <- r + r (1 - a r)) from the FP32 reciprocal:
+    // the seed's relative error (< 2^-23) squares at each step, so two steps
+    // leave only the final rounding (within an ulp of the quotient), with 4
+    // FP64 FMAs instead of a full division on this GPU's slow FP64 pipe.
+    // For a in the normal FP32 range (here a = rho, about 1).
+    __device__ static double rcp(double a) {
+        double r = (double)__frcp_rn((float)a);
+        double e = __fma_rn(-a, r, 1.0);
+        r = __fma_rn(r, e, r);
+        e = __fma_rn(-a, r, 1.0);
+        return __fma_rn(r, e, r);
+    }
 };
 template <> struct Ar<float> {
     __device__ static float c(double x) { return (float)x; }
@@ -154,9 +165,10 @@ __device__ __forceinline__ void collide_trt(V g[Q], const TrtK& K, V rho0) {
     const V jx = pair_moment<V, 0>(d), jy = pair_moment<V, 1>(d), jz = pair_moment<V, 2>(d);
     const V rho = DEV ? A::add(rho0, sum) : sum;
     const V inv = A::rcp(rho);
-    const V ux = A::mul(jx, inv), uy = A::mul(jy, inv), uz = A::mul(jz, inv);
-    const V ju = A::fma(jz, uz, A::fma(jy, uy, A::mul(jx, ux)));  // rho u.u
+    // no velocity vector: rho u.u = |j|^2 / rho and (c.u)(c.j) = (c.j)^2 / rho
+    const V ju = A::mul(A::fma(jz, jz, A::fma(jy, jy, A::mul(jx, jx))), inv);  // rho u.u
     const V base = A::fma(A::c(-1.5), ju, DEV ? sum : rho);
+    const V q18 = A::mul(A::c(4.5 / 18.0), inv), q36 = A::mul(A::c(4.5 / 36.0), inv);
     const V lw18 = k[5], lw36 = k[6];
     const V wb18 = A::mul(A::c(1.0 / 18.0), base), wb36 = A::mul(A::c(1.0 / 36.0), base);
     if (k[2] == V(0)) {
@@ -170,8 +182,8 @@ __device__ __forceinline__ void collide_trt(V g[Q], const TrtK& K, V rho0) {
         for (int p = 1; p <= 9; ++p) {
             const int i = 2 * p - 1;
             const bool face = i < 7;
-            const V cu = pair_dot<V>(i, ux, uy, uz), cj = pair_dot<V>(i, jx, jy, jz);
-            const V ep = A::fma(A::c(face ? 4.5 / 18.0 : 4.5 / 36.0), A::mul(cu, cj), face ? wb18 : wb36);
+            const V cj = pair_dot<V>(i, jx, jy, jz);
+            const V ep = A::fma(face ? q18 : q36, A::mul(cj, cj), face ? wb18 : wb36);
             const V h = A::fma(face ? lw18 : lw36, cj, A::mul(ch, d[p]));
             g[i] = A::add(ep, h);
             g[i + 1] = A::sub(ep, h);
@@ -185,8 +197,8 @@ __device__ __forceinline__ void collide_trt(V g[Q], const TrtK& K, V rho0) {
     for (int p = 1; p <= 9; ++p) {
         const int i = 2 * p - 1;
         const bool face = i < 7;
-        const V cu = pair_dot<V>(i, ux, uy, uz), cj = pair_dot<V>(i, jx, jy, jz);
-        const V ep = A::fma(A::c(face ? 4.5 / 18.0 : 4.5 / 36.0), A::mul(cu, cj), face ? wb18 : wb36);
+        const V cj = pair_dot<V>(i, jx, jy, jz);
+        const V ep = A::fma(face ? q18 : q36, A::mul(cj, cj), face ? wb18 : wb36);
         const V E = A::fma(le, ep, A::mul(mhle, s[p]));
         const V O = A::fma(face ? lw18 : lw36, cj, A::mul(mhlo, d[p]));
         g[i] = A::add(g[i], A::add(E, O));
