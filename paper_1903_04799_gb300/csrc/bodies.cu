@@ -347,16 +347,19 @@ __device__ __forceinline__ double comp(double v, int b) { return __shfl_sync(0xf
 // shortens the serial FP64 chain, which this GPU issues at a low rate.
 // p, s, Ai: the body's parameters, state of this step and accumulators (the
 // tables of B or copies of them); the results go to the tables of B.
-// If `out` is given, the new state and the re-classification flag are also
-// written there (lane a < 3: components a; lane 0: *out_reclass).
+// Results go to *Ao (accumulators) and *So (the state of the next step); if
+// `out` is given, the new state and the re-classification flag are also
+// written there (lane a < 3: components a; lane 0: *out_reclass).  Out of
+// line, with its outputs behind pointers: a call with the outputs pointed at
+// scratch runs the same instructions (see k_body_fused).
 template <int P>
 __device__ __noinline__ void update_body(const Lattice& L, const Bodies& B, int k, const BodyParams& p,
-                                         const BodyState& s, const BodyAcc& Ai, const double* tot,
-                                         BodyState* out = nullptr, int* out_reclass = nullptr) {
+                                         const BodyState& s, const BodyAcc& Ai, const double* tot, BodyAcc* Ao,
+                                         BodyState* So, BodyState* out = nullptr, int* out_reclass = nullptr) {
     const int lane = threadIdx.x & 31;
     const int a = lane < 3 ? lane : 0;  // lanes >= 3 shadow component 0 and store nothing
     const bool own = lane < 3;
-    BodyAcc& A = B.acc[k];
+    BodyAcc& A = *Ao;
     const double Fa = tot[a] + Ai.Fc[a], Ta = tot[3 + a] + Ai.Tc[a];
     const double rc = Ai.r_class[a], vs = Ai.vsum[a], ves = Ai.vesum;
     const long long ns = Ai.nsum;
@@ -433,7 +436,7 @@ __device__ __noinline__ void update_body(const Lattice& L, const Bodies& B, int 
         __syncwarp();
         if (reclass && lane == 0) A.margin_bits = (unsigned long long)__double_as_longlong(DBL_MAX);
     }
-    BodyState& so = B.state[1 - P][k];
+    BodyState& so = *So;
     if (own) {
         so.pos[a] = x;
         so.vel[a] = v;
@@ -676,7 +679,7 @@ __global__ void __launch_bounds__(kLB) k_links(const Bodies B) {
         if (threadIdx.x < 12) part[threadIdx.x] = s_tot[threadIdx.x];
         if (!last_block(&A.counter_links, G, &s_flag)) continue;
         ordered_partial_sum<12>(B.part_links + (size_t)k * B.GL * 12, G, sm, s_tot);
-        if (threadIdx.x < 32) update_body<P>(L, B, k, p, B.state[P][k], A, s_tot);
+        if (threadIdx.x < 32) update_body<P>(L, B, k, p, B.state[P][k], A, s_tot, &A, &B.state[1 - P][k]);
         __syncthreads();
         if (threadIdx.x == 0) s_flag = A.reclass;
         __syncthreads();
@@ -1325,7 +1328,10 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
     __shared__ Lattice s_L;
     __shared__ BodyParams s_p;
     __shared__ BodyState s_s0, s_new, s_cur;
-    __shared__ BodyAcc s_A;
+    __shared__ BodyAcc s_A, s_dryA;
+    __shared__ BodyState s_dryS, s_dryS2;
+    __shared__ double s_zero[12];
+    __shared__ int s_dryMode;
     __shared__ ShellGeo s_geo;
     __shared__ uint32_t s_stc[kStcBuf];
     __shared__ int s_lo[3];
@@ -1335,6 +1341,7 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
     __shared__ float s_min[kFT / 32], s_margin;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i0 = B.fused_first[cls], nitems = B.n_fused[cls];
+    if (threadIdx.x < 12) s_zero[threadIdx.x] = 0.0;
     for (int it = cid; it < nitems; it += ncl) {
         // everything of this body and lattice that the step reads, in one go
         // (the sweep streams the whole lattice through L2 between two steps,
@@ -1357,14 +1364,22 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
         box_range(p.st_count, rank, KC, b0, b1);
         for (long long b = b0 + threadIdx.x; b < b1 && b < b0 + kStcBuf; b += kFT) s_stc[b - b0] = __ldg(stc + b);
 
-        // ---- bounce-back and momentum exchange on the links (as k_links)
+        // ---- bounce-back and momentum exchange on the links (as k_links), by
+        // ranks 1 .. KC-1.  Meanwhile warp 0 of rank 0 runs the update once on
+        // scratch: its code is cold every step (the sweep streams the lattice
+        // through L2 between steps), and the real update after the reduction
+        // then runs warm.  The scratch call writes only shared memory.
         double acc[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) acc[c] = 0.0;
-        if (L.storage == ST_F64)
-            link_terms<P, true>(L, p, s0, s_A.link_count, B.links + p.link_off, rank, KC, acc);
-        else
-            link_terms<P, false>(L, p, s0, s_A.link_count, B.links + p.link_off, rank, KC, acc);
+        if (rank == 0) {
+            if (threadIdx.x < 32)
+                update_body<P>(L, B, k, p, s0, s_A, s_zero, &s_dryA, &s_dryS, &s_dryS2, &s_dryMode);
+        } else if (L.storage == ST_F64) {
+            link_terms<P, true>(L, p, s0, s_A.link_count, B.links + p.link_off, rank - 1, KC - 1, acc);
+        } else {
+            link_terms<P, false>(L, p, s0, s_A.link_count, B.links + p.link_off, rank - 1, KC - 1, acc);
+        }
         block_sum_fixed<12, kFT>(acc, sm, s_tot);
         int near = 0;
         if (rank == 0)
@@ -1382,7 +1397,8 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
                 sm[12 * KC + threadIdx.x] = t;
             }
             __syncthreads();
-            if (threadIdx.x < 32) update_body<P>(L, B, k, p, s0, s_A, sm + 12 * KC, &s_new, &s_mode);
+            if (threadIdx.x < 32)
+                update_body<P>(L, B, k, p, s0, s_A, sm + 12 * KC, &B.acc[k], &B.state[1 - P][k], &s_new, &s_mode);
             __syncthreads();
             if (threadIdx.x == 0) s_mode = s_mode ? (near ? 2 : 1) : 0;
             __syncthreads();
