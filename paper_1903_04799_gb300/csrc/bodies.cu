@@ -753,12 +753,26 @@ template <bool CG>
 __device__ __noinline__ void covered_momentum(const Lattice& L, const BodyState& s, int x, int y, int z, int q,
                                               double* acc) {
     double m[3] = {0.0, 0.0, 0.0};
+    if (L.storage == ST_F64) {
 #pragma unroll 1
-    for (int i = 0; i < Q; ++i) {
-        const double fi = load_abs<CG>(L, read_slot(L, i, x, y, z, q), i);
-        m[0] += fi * cx(i);
-        m[1] += fi * cy(i);
-        m[2] += fi * cz(i);
+        for (int i = 0; i < Q; ++i) {
+            const double fi = load_abs<CG>(L, read_slot(L, i, x, y, z, q), i);
+            m[0] += fi * cx(i);
+            m[1] += fi * cy(i);
+            m[2] += fi * cz(i);
+        }
+    } else {
+        // sum_i c_i w_i rho0 = 0: the momentum is that of the stored deviations,
+        // summed in FP32 (their own precision)
+        float mf[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 1
+        for (int i = 0; i < Q; ++i) {
+            const float gi = load_dev<CG>(L, read_slot(L, i, x, y, z, q));
+            mf[0] += gi * (float)cx(i);
+            mf[1] += gi * (float)cy(i);
+            mf[2] += gi * (float)cz(i);
+        }
+        for (int a = 0; a < 3; ++a) m[a] = (double)mf[a];
     }
     const double d[3] = {min_image((double)x - s.pos[0], L.nx), min_image((double)y - s.pos[1], L.ny),
                          min_image((double)z - s.pos[2], L.nz)};
@@ -893,6 +907,32 @@ __global__ void __launch_bounds__(kBB) k_classify(const Bodies B) {
 
 // ---------------------------------------------------------------- k_convert
 
+// Sum of one double per lane over the warp, in a fixed tree order (lane 0
+// holds the result): five shuffle levels instead of a serial chain, each
+// level one FP64 add for the whole warp.
+__device__ __forceinline__ double warp_tree_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Density of node (x, y, z) from its populations in the read slots of parity
+// q.  Reduced storages: rho0 plus the FP32 sum of the stored deviations (the
+// stored values carry FP32 precision or less), one FP64 add in all.
+template <bool CG>
+__device__ __forceinline__ double node_density(const Lattice& L, int x, int y, int z, int q) {
+    if (L.storage == ST_F64) {
+        double r = 0.0;
+#pragma unroll 1
+        for (int j = 0; j < Q; ++j) r += ld<CG>((const double*)L.F + read_slot(L, j, x, y, z, q));
+        return r;
+    }
+    float g = 0.0f;
+#pragma unroll 1
+    for (int j = 0; j < Q; ++j) g += load_dev<CG>(L, read_slot(L, j, x, y, z, q));
+    return L.rho0 + (double)g;
+}
+
 // 1/k for k = 1..18, correctly rounded (the mean of k neighbour densities is
 // their sum times 1/k, within an ulp of the quotient).
 __constant__ double kInvCount[19] = {0.0,       1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,
@@ -908,17 +948,8 @@ __constant__ double kInvCount[19] = {0.0,       1.0,        1.0 / 2,  1.0 / 3,  
 __device__ __noinline__ void refill_finish(const Lattice& L, const BodyState& s, int x, int y, int z, int q,
                                               double r, int valid, double* acc) {
     const int lane = threadIdx.x & 31;
-    double sum = 0.0;
-    int cnt = 0;
-#pragma unroll 1
-    for (int l = 1; l < Q; ++l) {
-        const double rl = __shfl_sync(0xffffffffu, r, l);
-        const int vl = __shfl_sync(0xffffffffu, valid, l);
-        if (vl) {
-            sum += rl;
-            cnt++;
-        }
-    }
+    const int cnt = __popc(__ballot_sync(0xffffffffu, valid != 0));
+    const double sum = __shfl_sync(0xffffffffu, warp_tree_sum(valid ? r : 0.0), 0);
     const double rb = cnt > 0 ? sum * kInvCount[cnt] : L.rho0;
     const double d[3] = {min_image((double)x - s.pos[0], L.nx), min_image((double)y - s.pos[1], L.ny),
                          min_image((double)z - s.pos[2], L.nz)};
@@ -932,14 +963,9 @@ __device__ __noinline__ void refill_finish(const Lattice& L, const BodyState& s,
         fi = wgt(lane) * rb * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
         store_abs(L, read_slot(L, lane, x, y, z, q), lane, fi);
     }
-    double m[3] = {0.0, 0.0, 0.0};
-#pragma unroll 1
-    for (int l = 0; l < Q; ++l) {
-        const double fl = __shfl_sync(0xffffffffu, fi, l);
-        m[0] += fl * cx(l);
-        m[1] += fl * cy(l);
-        m[2] += fl * cz(l);
-    }
+    // created momentum sum_l c_l f_l: lane l holds its term (zero beyond Q)
+    const double m[3] = {warp_tree_sum(lane < Q ? fi * cx(lane) : 0.0), warp_tree_sum(lane < Q ? fi * cy(lane) : 0.0),
+                         warp_tree_sum(lane < Q ? fi * cz(lane) : 0.0)};
     if (lane == 0) {
         double t[3];
         cross3(d, m, t);
@@ -964,8 +990,7 @@ __device__ __noinline__ void refill_cell(const Lattice& L, const BodyState& s, i
         const int64_t nn = cell_index(L, xn, yn, zn);
         if (ld<CG>(L.own + nn) == 0 && ld<CG>(L.own_prev + nn) == 0) {
             valid = 1;
-#pragma unroll 1
-            for (int j = 0; j < Q; ++j) r += load_abs<CG>(L, read_slot(L, j, xn, yn, zn, q), j);
+            r = node_density<CG>(L, xn, yn, zn, q);
         }
     }
     refill_finish(L, s, x, y, z, q, r, valid, acc);
@@ -1300,8 +1325,7 @@ __device__ __noinline__ void geo_refill(const Lattice& L, const ShellGeo& G, con
             valid = 1;
             int xn, yn, zn;
             geo_cell(L, G, a, b, c, xn, yn, zn);
-#pragma unroll 1
-            for (int j = 0; j < Q; ++j) r += load_abs<true>(L, read_slot(L, j, xn, yn, zn, q), j);
+            r = node_density<true>(L, xn, yn, zn, q);
         }
     }
     int x, y, z;

@@ -160,11 +160,12 @@ __device__ __forceinline__ void store_abs(const Lattice& L, int64_t slot, int i,
 
 // Deviation g_i = f_i - w_i rho0 of a reduced-storage slot, in FP32 (no FP64
 // arithmetic), and its store.  Not for FP64 storage.
+template <bool CG = false>
 __device__ __forceinline__ float load_dev(const Lattice& L, int64_t slot) {
     switch (L.storage) {
-        case ST_F32: return ((const float*)L.F)[slot];
-        case ST_F16: return __half2float(((const __half*)L.F)[slot]) * L.inv_scale;
-        default: return __bfloat162float(((const __nv_bfloat16*)L.F)[slot]) * L.inv_scale;
+        case ST_F32: return ld<CG>((const float*)L.F + slot);
+        case ST_F16: return __half2float(ld<CG>((const __half*)L.F + slot)) * L.inv_scale;
+        default: return __bfloat162float(ld<CG>((const __nv_bfloat16*)L.F + slot)) * L.inv_scale;
     }
 }
 __device__ __forceinline__ void store_dev(const Lattice& L, int64_t slot, float g) {

@@ -31,7 +31,9 @@ def _rank(rank, ws, port, out):
 
 def test_two_gloo_ranks_agree_on_max_time_and_job_throughput():
     ws = 2
-    with mp.Manager() as m:
+    # spawn, not fork: earlier tests in this process may have started OpenMP
+    # threads (the oracle), and a fork of a threaded process can deadlock
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(ws, _free_port(), out), nprocs=ws, join=True)
         res = dict(out)
