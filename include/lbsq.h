@@ -152,11 +152,17 @@ lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u);
 lb_status lb_set_populations(lb_ctx* c, const double* f);
 lb_status lb_get_populations(lb_ctx* c, double* f);
 
-/* Enqueue nsteps >= 0 time steps.  Errors: LB_ERR_INVALID, LB_ERR_STATE,
- * LB_ERR_CUDA. */
+/* Enqueue nsteps >= 0 time steps.  When the bodies occupy a thin box of
+ * rows, a step's body kernels run beside the sweep of the cells away from
+ * the bodies in the next step; the body kernels of the last step enqueued
+ * are then issued by the next call that steps, reads or changes the context
+ * (every lb_get_*, lb_set_*, lb_add_*, lb_profile_begin), so that
+ * consecutive lb_step calls keep that overlap.  Results never depend on it.
+ * Errors: LB_ERR_INVALID, LB_ERR_STATE, LB_ERR_CUDA. */
 lb_status lb_step(lb_ctx* c, int64_t nsteps);
 
-/* Wait for the context's stream and report the device error word. */
+/* Wait for the work issued on the context's stream and report the device
+ * error word (it issues no pending body kernels: see lb_step). */
 lb_status lb_sync(lb_ctx* c);
 
 /* Steps taken so far. */

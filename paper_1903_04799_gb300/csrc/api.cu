@@ -15,11 +15,12 @@
 
 namespace lbsq {
 void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, int zmode,
-                  const int* win, int gz, cudaStream_t st);
+                  const int* win, int gz, int gy, cudaStream_t st);
 void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, int grid_box, long long* step,
                         cudaStream_t st);
 void launch_body_step(const Bodies& B, int parity, int grid_links, int grid_box, long long* step, cudaStream_t st);
-void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st, int tail);
+void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st, int tail,
+                       cudaEvent_t started = nullptr);
 cudaError_t prepare_body_kernels();
 void launch_fill_rest(const Lattice& L, cudaStream_t st);
 void launch_set_eq(const Lattice& L, const double* rho, const double* u, int q, cudaStream_t st);
@@ -102,9 +103,12 @@ struct lb_ctx {
     // that SM slots freed by sweep blocks go to the short body kernels first)
     cudaStream_t side = nullptr, hi = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
-    int* d_win = nullptr;  // [2][2] near-body z-windows by step parity
+    cudaEvent_t ev_started = nullptr;  // every block of the fused body kernel has begun (see enqueue_unit)
+    int* d_win = nullptr;  // [2][4] near-body windows (z0, z length, y0, y length) by step parity
     bool split = false;    // whether steps are split into far and near sweeps
-    int win_max = 0;       // upper bound of the window length (planes)
+    int win_max = 0;       // upper bound of the window's z length (planes)
+    int ywin_max = 0;      // upper bound of its y length (rows)
+    bool pending = false;  // split steps: the body step of step `step - 1` is not issued yet (see settle)
     // kernel tracing
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -388,18 +392,28 @@ lb_status relayout(lb_ctx* c) {
                        c->stream));
     lb_status s = upload_lattice(c);
     if (s != LB_OK) return s;
-    // near-body window: an upper bound of its length from the box heights; the
-    // split pays only when the window leaves most of the lattice outside
-    int wmax = 0;
+    // near-body window: upper bounds of its z and y lengths from the box
+    // sizes (a z-normal wall spans every row); the split pays only when the
+    // window leaves most of the planes outside
+    int wmax = 0, ymax = 0;
     bool across = false;
     for (auto& b : c->par) {
-        if (b.kind == BODY_SPHERE) wmax += b.box_w[2] + 5;
-        else if (b.wall_axis == 2) wmax += 3 + 5;
-        else across = true;
+        if (b.kind == BODY_SPHERE) {
+            wmax += b.box_w[2] + 5;
+            ymax += b.box_w[1] + 5;
+        } else if (b.wall_axis == 2) {
+            wmax += 3 + 5;
+            ymax += c->L.ny;
+        } else {
+            across = true;
+        }
     }
     c->win_max = std::min(wmax, c->L.nz);
+    // the device takes every row once the extent may reach 3/5 of them
+    c->ywin_max = ymax * 5 < 3 * c->L.ny ? ymax : c->L.ny;
     c->split = !across && nb > 0 && wmax * 5 < 3 * c->L.nz;
-    const int win_init[4] = {0, c->L.nz, 0, c->L.nz};  // whole lattice until the first rebuild
+    // whole lattice until the first rebuild
+    const int win_init[8] = {0, c->L.nz, 0, c->L.ny, 0, c->L.nz, 0, c->L.ny};
     CK(cudaMemcpyAsync(c->d_win, win_init, sizeof(win_init), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));  // host vectors above are transient
     drop_graph(c);
@@ -464,6 +478,8 @@ lb_status new_body(lb_ctx* c, const BodyParams& bp, const BodyState& st, int kin
 }  // namespace
 
 extern "C" {
+
+static void settle(lb_ctx* c);  // issues pending body kernels (defined with lb_step)
 
 void lb_params_default(lb_params* p) {
     if (!p) return;
@@ -535,14 +551,15 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     c->d_count = dalloc_t<int>(c, 2);
     c->d_lat = dalloc_t<Lattice>(c, 1);
     c->d_counts = dalloc_t<int>(c, 11);
-    c->d_win = dalloc_t<int>(c, 4);
+    c->d_win = dalloc_t<int>(c, 8);
     int prio_lo = 0, prio_hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) return bail(LB_ERR_CUDA);
     if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
         cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_started, cudaEventDisableTiming) != cudaSuccess)
         return bail(LB_ERR_CUDA);
     if (!L.F || !c->own || !c->own_prev || !c->d_mass_part || !c->d_small || !c->d_err || !c->d_count ||
         !c->d_lat || !c->d_counts || !c->d_win)
@@ -572,6 +589,7 @@ lb_status lb_destroy(lb_ctx* c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_join2) cudaEventDestroy(c->ev_join2);
+    if (c->ev_started) cudaEventDestroy(c->ev_started);
     for (cudaStream_t st : {c->side, c->hi})
         if (st) {
             cudaStreamSynchronize(st);
@@ -591,6 +609,8 @@ lb_status lb_add_squirmer(lb_ctx* c, const double pos[3], const double e[3], dou
                           int32_t mobile, double density, int32_t* id) {
     if (!c || !pos || !e || !id) return LB_ERR_INVALID;
     if (c->sticky) return fail(c, LB_ERR_STATE, "context holds a device error");
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
     const int nmin = std::min(c->L.nx, std::min(c->L.ny, c->L.nz));
     const double ne = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
     if (!(R > 0.0) || !(2.0 * R + 6.0 < (double)nmin)) return fail(c, LB_ERR_INVALID, "radius vs box");
@@ -655,6 +675,7 @@ lb_status lb_add_wall(lb_ctx* c, int32_t kind, const double* params, int32_t npa
     if (!c || !id) return LB_ERR_INVALID;
     if (c->sticky) return fail(c, LB_ERR_STATE, "context holds a device error");
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     const int n3[3] = {c->L.nx, c->L.ny, c->L.nz};
     if (kind == 2) {
         if (!params || nparams < 4) return fail(c, LB_ERR_INVALID, "obstacle needs x, y, z, radius");
@@ -714,6 +735,8 @@ lb_status lb_add_wall(lb_ctx* c, int32_t kind, const double* params, int32_t npa
 
 lb_status lb_set_contact(lb_ctx* c, double sigma, double eps) {
     if (!c || !(sigma > 0.0) || !(eps >= 0.0)) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
     c->wca_sigma = sigma;
     c->wca_eps = eps;
     drop_graph(c);
@@ -733,6 +756,7 @@ static lb_status ensure_scratch(lb_ctx* c, double** buf, size_t n) {
 lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u) {
     if (!c || !rho || !u) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     const size_t N = (size_t)c->L.N;
     lb_status s = ensure_scratch(c, &c->d_fields, 4 * N);
     if (s != LB_OK) return s;
@@ -748,6 +772,7 @@ lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u) {
 lb_status lb_set_populations(lb_ctx* c, const double* f) {
     if (!c || !f) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     const size_t N = (size_t)c->L.N;
     lb_status s = ensure_scratch(c, &c->d_pop, Q * N);
     if (s != LB_OK) return s;
@@ -762,6 +787,7 @@ lb_status lb_set_populations(lb_ctx* c, const double* f) {
 lb_status lb_get_populations(lb_ctx* c, double* f) {
     if (!c || !f) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     const size_t N = (size_t)c->L.N;
     lb_status s = ensure_scratch(c, &c->d_pop, Q * N);
     if (s != LB_OK) return s;
@@ -782,7 +808,7 @@ static cudaEvent_t pool_event(lb_ctx* c, size_t k) {
 }
 
 static void sweep_all(lb_ctx* c, int parity, cudaStream_t st) {
-    launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, 0, nullptr, c->L.nz, st);
+    launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, 0, nullptr, c->L.nz, c->L.ny, st);
 }
 
 // The body kernels of one step on stream st: the fused kernel (spheres), the
@@ -790,14 +816,16 @@ static void sweep_all(lb_ctx* c, int parity, cudaStream_t st) {
 // rebuild, which re-classify the spheres queued by the other two (bodies near
 // another body) and end the step; for a lattice with a single sphere and no
 // other body, the fused kernel alone.  Returns the launch count.
-static int body_step(lb_ctx* c, const Bodies& B, int parity, cudaStream_t st) {
+// started: recorded when every block of the fused kernel has begun (if it is
+// launched: c->solo or c->n_fused > 0).
+static int body_step(lb_ctx* c, const Bodies& B, int parity, cudaStream_t st, cudaEvent_t started = nullptr) {
     if (c->solo) {  // the fused kernel is the whole body step
-        launch_body_fused(B, parity, c->fused_cls, 1, st, 1);
+        launch_body_fused(B, parity, c->fused_cls, 1, st, 1, started);
         return 1;
     }
     int n = 0;
     if (c->n_fused > 0) {
-        launch_body_fused(B, parity, c->fused_cls, c->n_fused, st, 0);
+        launch_body_fused(B, parity, c->fused_cls, c->n_fused, st, 0, started);
         n++;
     }
     if (c->n_link_items > 0) {
@@ -838,45 +866,54 @@ static void enqueue_traced_step(lb_ctx* c) {
     c->step++;
 }
 
-// n steps on the context's stream.  When the bodies occupy a thin slab of
-// planes, the sweep of step t+1 is split: the planes outside the near-body
-// window (none of whose slots the body kernels touch) run on a side stream
-// while the body kernels of step t run, the planes inside it after them.
+// n whole steps on the context's stream (the sweep, then the body kernels).
 static void enqueue_steps(lb_ctx* c, int64_t n) {
     const bool bodies = !c->par.empty();
     const Bodies B = bodies_view(c);
-    bool swept = false;  // sweep of the current step already issued
     for (int64_t k = 0; k < n; ++k) {
         const int parity = (int)(c->step & 1);
-        if (!swept) {
-            sweep_all(c, parity, c->stream);
-            c->launches += 1;
-        }
-        swept = false;
-        if (!bodies) {
-            c->step++;
-            continue;
-        }
-        if (c->split && k + 1 < n) {
-            const int q = 1 - parity;
-            const int* win = c->d_win + 2 * q;
-            cudaEventRecord(c->ev_fork, c->stream);
-            cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-            cudaStreamWaitEvent(c->hi, c->ev_fork, 0);
-            c->launches += body_step(c, B, parity, c->hi);
-            launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 1, win, c->L.nz, c->side);
-            cudaEventRecord(c->ev_join, c->side);
-            cudaEventRecord(c->ev_join2, c->hi);
-            cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-            cudaStreamWaitEvent(c->stream, c->ev_join2, 0);
-            launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 2, win, c->win_max, c->stream);
-            c->launches += 2;
-            swept = true;
-        } else {
-            c->launches += body_step(c, B, parity, c->stream);
-        }
+        sweep_all(c, parity, c->stream);
+        c->launches += 1;
+        if (bodies) c->launches += body_step(c, B, parity, c->stream);
         c->step++;
     }
+}
+
+// When the bodies occupy a thin box of rows, steps run as a pipeline of
+// units.  Unit t: the body kernels of step t (whose sweep is done) on `hi`,
+// beside the far sweep of step t+1 (every cell outside the near-body window,
+// none of whose slots the body kernels touch) on `side`; then the near sweep
+// of step t+1.  After a unit the body kernels of step t+1 are pending.
+// lb_step returns with them pending, so that consecutive calls keep the
+// overlap; every call that reads or changes the context issues them first.
+static void enqueue_unit(lb_ctx* c) {
+    const int parity = (int)((c->step - 1) & 1), q = 1 - parity;
+    const Bodies B = bodies_view(c);
+    const int* win = c->d_win + 4 * q;
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    cudaStreamWaitEvent(c->hi, c->ev_fork, 0);
+    // the far sweep starts once the fused kernel's clusters are placed: started
+    // first, it would fill every SM, and a cluster waits for SMs of one GPC to
+    // drain together
+    const bool fused = c->solo || c->n_fused > 0;
+    c->launches += body_step(c, B, parity, c->hi, fused ? c->ev_started : nullptr);
+    if (fused) cudaStreamWaitEvent(c->side, c->ev_started, 0);
+    launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 1, win, c->L.nz, c->L.ny, c->side);
+    cudaEventRecord(c->ev_join, c->side);
+    cudaEventRecord(c->ev_join2, c->hi);
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    cudaStreamWaitEvent(c->stream, c->ev_join2, 0);
+    launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 2, win, c->win_max, c->ywin_max, c->stream);
+    c->launches += 2;
+    c->step++;
+}
+
+// Issue the pending body kernels, if any: the context then holds whole steps.
+static void settle(lb_ctx* c) {
+    if (!c->pending) return;
+    c->launches += body_step(c, bodies_view(c), (int)((c->step - 1) & 1), c->stream);
+    c->pending = false;
 }
 
 constexpr int kGraphSteps = 8;
@@ -884,9 +921,14 @@ constexpr int kGraphSteps = 8;
 static lb_status build_graph(lb_ctx* c) {
     cudaGraph_t g = nullptr;
     const int64_t saved_launches = c->launches, saved_step = c->step;
-    c->step = 0;  // the graph starts on an even step
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_steps(c, kGraphSteps);
+    if (c->split) {
+        c->step = 2;  // 8 units from t = 1
+        for (int k = 0; k < kGraphSteps; ++k) enqueue_unit(c);
+    } else {
+        c->step = 0;  // 8 steps from an even step
+        enqueue_steps(c, kGraphSteps);
+    }
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     c->graph_launches = c->launches - saved_launches;
     c->launches = saved_launches;
@@ -911,7 +953,19 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
         return LB_OK;
     }
     int64_t left = nsteps;
-    if (left > 0 && (c->step & 1)) {  // graphs start on even steps
+    if (c->split) {
+        if (left > 0 && !c->pending) {
+            sweep_all(c, (int)(c->step & 1), c->stream);
+            c->launches += 1;
+            c->step++;
+            c->pending = true;
+            left--;
+        }
+        if (left > 0 && ((c->step - 1) & 1) == 0) {  // graphs start on a unit of odd t
+            enqueue_unit(c);
+            left--;
+        }
+    } else if (left > 0 && (c->step & 1)) {  // graphs start on even steps
         enqueue_steps(c, 1);
         left--;
     }
@@ -927,13 +981,19 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
             left -= kGraphSteps;
         }
     }
-    if (left > 0) enqueue_steps(c, left);
+    if (c->split) {
+        for (; left > 0; --left) enqueue_unit(c);
+    } else if (left > 0) {
+        enqueue_steps(c, left);
+    }
     CK(cudaGetLastError());
     return LB_OK;
 }
 
 lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant) {
     if (!c || variant < 0 || variant > 6) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
     c->sweep_variant = variant;
     drop_graph(c);
     return LB_OK;
@@ -941,6 +1001,8 @@ lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant) {
 
 lb_status lb_profile_begin(lb_ctx* c) {
     if (!c) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
     c->profiling = true;
     c->ev_used.clear();
     return LB_OK;
@@ -978,6 +1040,7 @@ lb_status lb_sync(lb_ctx* c) {
 lb_status lb_get_fields_device(lb_ctx* c, double* rho_dev, double* u_dev) {
     if (!c) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     launch_fields(c->L, c->own, rho_dev, u_dev, (int)(c->step & 1), c->stream);
     c->launches += 1;
     CK(cudaGetLastError());
@@ -987,6 +1050,7 @@ lb_status lb_get_fields_device(lb_ctx* c, double* rho_dev, double* u_dev) {
 lb_status lb_get_fields(lb_ctx* c, double* rho, double* u) {
     if (!c) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     const size_t N = (size_t)c->L.N;
     lb_status s = ensure_scratch(c, &c->d_fields, 4 * N);
     if (s != LB_OK) return s;
@@ -1004,6 +1068,7 @@ lb_status lb_get_fields(lb_ctx* c, double* rho, double* u) {
 lb_status lb_get_owner(lb_ctx* c, int32_t* owner) {
     if (!c || !owner) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     lb_status s = sync_checked(c);
     if (s != LB_OK) return s;
     CK(cudaMemcpyAsync(owner, c->own, sizeof(int32_t) * c->L.N, cudaMemcpyDeviceToHost, c->stream));
@@ -1014,6 +1079,7 @@ lb_status lb_get_owner(lb_ctx* c, int32_t* owner) {
 static lb_status read_acc(lb_ctx* c, int32_t id, BodyAcc* a) {
     if (id < 1 || id > (int32_t)c->par.size()) return fail(c, LB_ERR_INVALID, "bad body id");
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     lb_status s = sync_checked(c);
     if (s != LB_OK) return s;
     CK(cudaMemcpyAsync(a, c->d_acc + (id - 1), sizeof(BodyAcc), cudaMemcpyDeviceToHost, c->stream));
@@ -1046,6 +1112,7 @@ lb_status lb_get_object_state(lb_ctx* c, int32_t id, double pos[3], double vel[3
     if (!c) return LB_ERR_INVALID;
     if (id < 1 || id > (int32_t)c->par.size()) return fail(c, LB_ERR_INVALID, "bad body id");
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     lb_status s = sync_checked(c);
     if (s != LB_OK) return s;
     BodyState st;
@@ -1064,6 +1131,7 @@ lb_status lb_get_object_state(lb_ctx* c, int32_t id, double pos[3], double vel[3
 lb_status lb_get_mass(lb_ctx* c, double* mass, double mom[3]) {
     if (!c) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     launch_mass(c->L, c->own, c->d_mass_part, c->d_small, (int)(c->step & 1), c->stream);
     c->launches += 2;
     CK(cudaGetLastError());
@@ -1082,6 +1150,7 @@ lb_status lb_get_links(lb_ctx* c, int32_t id, int64_t* out, int64_t cap, int64_t
     if (!c || !count || cap < 0 || (cap > 0 && !out)) return LB_ERR_INVALID;
     if (id < 0 || id > (int32_t)c->par.size()) return fail(c, LB_ERR_INVALID, "bad body id");
     CK(cudaSetDevice(c->p.device));
+    settle(c);
     lb_status s = sync_checked(c);
     if (s != LB_OK) return s;
     const int nb = (int)c->par.size();

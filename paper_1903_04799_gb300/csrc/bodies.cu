@@ -1068,52 +1068,70 @@ __global__ void __launch_bounds__(kBB) k_convert(const Bodies B) {
 
 // ---------------------------------------------------------------- k_rebuild
 
-// z-window of lattice 0 that holds every cell the body kernels of the next
-// step can touch: the z-extent of every body's scan box at the new positions,
-// two more planes on each side (a body moves less than half a cell per
-// step).  Stored in win[P] for the sweeps two steps later (see api.cu); the
-// whole lattice when the bodies spread over more than 3/5 of it.
-template <int P>
-__device__ void near_window(const Bodies& B) {
-    const Lattice& L = B.lats[0];
-    const int n = L.nz;
-    int lo_min = 0, hi_max = 0, ref = 0;
-    bool first = true, full = L.body_count == 0;
-    for (int j = L.body_begin; j < L.body_begin + L.body_count && !full; ++j) {
-        const BodyParams& q = B.par[j];
-        int lo, w;
-        if (q.kind == BODY_SPHERE) {
-            lo = (int)floor(B.state[1 - P][j].pos[2] - q.R) - 2;
-            w = q.box_w[2];
-        } else if (q.wall_axis == 2) {
-            lo = q.wall_index - 1;
-            w = 3;
-        } else {
-            full = true;  // a wall across every plane
-            break;
-        }
-        // unwrap the box centre to within half a lattice of the first body's
-        int c = lo + w / 2;
+// Periodic extent [lo, hi) along one axis of n cells that holds the ranges
+// [lo_j, lo_j + w_j) added to it, each unwrapped to within half a lattice of
+// the first one's centre.
+struct Extent {
+    int lo = 0, hi = 0, ref = 0;
+    bool first = true;
+    __device__ void add(int lo_j, int w, int n) {
+        int c = lo_j + w / 2;
         if (first) ref = c;
         while (c - ref > n / 2) {
-            lo -= n;
+            lo_j -= n;
             c -= n;
         }
         while (c - ref < -n / 2) {
-            lo += n;
+            lo_j += n;
             c += n;
         }
-        if (first || lo - 2 < lo_min) lo_min = lo - 2;
-        if (first || lo + w + 2 > hi_max) hi_max = lo + w + 2;
+        if (first || lo_j < lo) lo = lo_j;
+        if (first || lo_j + w > hi) hi = lo_j + w;
         first = false;
     }
-    int z0 = 0, len = n;
-    if (!full && (hi_max - lo_min) * 5 < 3 * n) {
-        z0 = ((lo_min % n) + n) % n;
-        len = hi_max - lo_min;
+    // (start, length) in [0, n) x [1, n]: the whole axis when the extent
+    // covers more than 3/5 of it
+    __device__ void window(int n, int* out) const {
+        if ((hi - lo) * 5 < 3 * n) {
+            out[0] = ((lo % n) + n) % n;
+            out[1] = hi - lo;
+        } else {
+            out[0] = 0;
+            out[1] = n;
+        }
     }
-    B.win[2 * P] = z0;
-    B.win[2 * P + 1] = len;
+};
+
+// Window of lattice 0 that holds every cell the body kernels of the next step
+// can touch: the z- and y-extent of every body's scan box at the new
+// positions, two more cells on each side (a body moves less than half a cell
+// per step).  A z-normal wall spans every row.  Stored in win[P] for the
+// sweeps two steps later (see api.cu); the whole lattice when the bodies
+// spread over more than 3/5 of the planes.
+template <int P>
+__device__ void near_window(const Bodies& B) {
+    const Lattice& L = B.lats[0];
+    Extent ez, ey;
+    bool full = L.body_count == 0, all_rows = false;
+    for (int j = L.body_begin; j < L.body_begin + L.body_count && !full; ++j) {
+        const BodyParams& q = B.par[j];
+        if (q.kind == BODY_SPHERE) {
+            const double* pos = B.state[1 - P][j].pos;
+            ez.add((int)floor(pos[2] - q.R) - 4, q.box_w[2] + 4, L.nz);
+            ey.add((int)floor(pos[1] - q.R) - 4, q.box_w[1] + 4, L.ny);
+        } else if (q.wall_axis == 2) {
+            ez.add(q.wall_index - 3, 3 + 4, L.nz);
+            all_rows = true;
+        } else {
+            full = true;  // a wall across every plane
+        }
+    }
+    int w[4] = {0, L.nz, 0, L.ny};
+    if (!full) {
+        ez.window(L.nz, w);
+        if (w[1] < L.nz && !all_rows) ey.window(L.ny, w + 2);
+    }
+    for (int i = 0; i < 4; ++i) B.win[4 * P + i] = w[i];
 }
 
 template <int P>
@@ -1648,20 +1666,31 @@ int fused_cluster(int c) { return c == 0 ? 16 : (c == 1 ? 8 : 4); }
 
 // The fused body kernel over the spheres of class cls in B.fused_items:
 // `clusters` clusters of fused_cluster(cls) blocks; tail: see k_body_fused.
-void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st, int tail) {
+// started: null, or an event (created with cudaEventDisableTiming) to fire
+// once every block of the launch has begun (a launch-completion event): a
+// stream that waits on it starts after the clusters are placed, not after
+// the kernel ends.
+void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st, int tail,
+                       cudaEvent_t started) {
     if (clusters <= 0) return;
     const int kc = fused_cluster(cls);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(clusters * kc);
     cfg.blockDim = dim3(kFT);
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = kc;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (started) {
+        attr[1].id = cudaLaunchAttributeLaunchCompletionEvent;
+        attr[1].val.launchCompletionEvent.event = started;
+        attr[1].val.launchCompletionEvent.flags = 0;
+        cfg.numAttrs = 2;
+    }
     if (parity == 0) cudaLaunchKernelEx(&cfg, k_body_fused<0>, B, cls, tail);
     else cudaLaunchKernelEx(&cfg, k_body_fused<1>, B, cls, tail);
 }

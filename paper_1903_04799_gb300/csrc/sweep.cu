@@ -15,16 +15,17 @@ template <int S, int P>
 __global__ void __launch_bounds__(256) k_sweep(const SweepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int z = sweep_plane(a);
-    if (x >= a.nx || z < 0) return;
-    sweep_one<S, P>(a, x, blockIdx.y, z);
+    const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y, z);
+    if (x >= a.nx || y < 0) return;
+    sweep_one<S, P>(a, x, y, z);
 }
 
 template <int S, int P>
 __global__ void __launch_bounds__(256, 2) k_sweep2(const SweepArgs a) {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = sweep_plane(a);
-    if (x0 >= a.nx || y >= a.ny || z < 0) return;
+    const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
+    if (x0 >= a.nx || y < 0) return;
     sweep_two<S, P>(a, x0, y, z);
 }
 
@@ -32,9 +33,9 @@ __global__ void __launch_bounds__(256, 2) k_sweep2(const SweepArgs a) {
 template <int S, int P>
 __global__ void __launch_bounds__(256, 3) k_sweep2p(const SweepArgs a) {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = sweep_plane(a);
-    if (x0 >= a.nx || y >= a.ny || z < 0) return;
+    const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
+    if (x0 >= a.nx || y < 0) return;
     sweep_two16<S, P>(a, x0, y, z);
 }
 
@@ -44,9 +45,9 @@ template <int S, int P, int ROWS>
 __global__ void __launch_bounds__(32 * ROWS, 2) k_sweep4(const SweepArgs a) {
     const int lane = threadIdx.x;
     const int x0 = 128 * blockIdx.x + 4 * lane;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = sweep_plane(a);
-    if (y >= a.ny || z < 0) return;  // a whole warp
+    const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
+    if (y < 0) return;  // a whole warp
     sweep_four<S, P>(a, x0, y, z, lane);
 }
 
@@ -57,19 +58,22 @@ constexpr int kPlanes = 4;
 template <int S, int P>
 __global__ void __launch_bounds__(256, 2) k_sweep2z(const SweepArgs a, int slots) {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x0 >= a.nx || y >= a.ny) return;
+    const int ly = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= a.nx) return;
     const int p0 = blockIdx.z * kPlanes;
     unsigned int cur[Q], nxt[Q];
     int z = sweep_plane_at(a, p0);
-    if (z >= 0) load_pair16<S, P>(a, x0, y, z, cur);
+    int y = z < 0 ? -1 : sweep_row(a, ly, z);  // the row depends on the plane in the far sweep
+    if (y >= 0) load_pair16<S, P>(a, x0, y, z, cur);
     for (int k = 0; k < kPlanes && p0 + k < slots; ++k) {
         const int zn = (k + 1 < kPlanes && p0 + k + 1 < slots) ? sweep_plane_at(a, p0 + k + 1) : -1;
-        if (zn >= 0) load_pair16<S, P>(a, x0, y, zn, nxt);  // in flight during the collision below
-        if (z >= 0) collide_store_pair16<S, P>(a, x0, y, z, cur);
+        const int yn = zn < 0 ? -1 : sweep_row(a, ly, zn);
+        if (yn >= 0) load_pair16<S, P>(a, x0, yn, zn, nxt);  // in flight during the collision below
+        if (y >= 0) collide_store_pair16<S, P>(a, x0, y, z, cur);
 #pragma unroll
         for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
         z = zn;
+        y = yn;
     }
 }
 
@@ -79,21 +83,21 @@ __global__ void __launch_bounds__(256, 2) k_sweep2z(const SweepArgs a, int slots
 template <int S, int P>
 __global__ void __launch_bounds__(P == 0 ? 256 : 192, 2) k_sweep4r(const SweepArgs a) {
     extern __shared__ unsigned short rowbuf[];
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = sweep_plane(a);
     if (z < 0) return;  // the whole block
-    sweep_four_rows<S, P>(a, y, z, y < a.ny, rowbuf);
+    const int y = sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
+    sweep_four_rows<S, P>(a, y < 0 ? 0 : y, z, y >= 0, rowbuf);
 }
 
 template <int S>
-static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaStream_t st) {
+static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy, cudaStream_t st) {
     if constexpr (S == ST_F16 || S == ST_BF16) {
         if (variant == 5 && a.nx % 2 == 0) {
             const int pairs = a.nx / 2;
             int bx = ((pairs + 31) / 32) * 32;
             if (bx > 128) bx = 128;
             const int by = 256 / bx;
-            dim3 block(bx, by), grid((pairs + bx - 1) / bx, (a.ny + by - 1) / by, (gz + kPlanes - 1) / kPlanes);
+            dim3 block(bx, by), grid((pairs + bx - 1) / bx, (gy + by - 1) / by, (gz + kPlanes - 1) / kPlanes);
             if (parity == 0) k_sweep2z<S, 0><<<grid, block, 0, st>>>(a, gz);
             else k_sweep2z<S, 1><<<grid, block, 0, st>>>(a, gz);
             return;
@@ -106,7 +110,7 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaSt
         if ((variant == 6 || (variant == 0 && parity == 0)) && rows4) {
             // odd steps (more live values) in blocks of at most 192 threads
             const int tx = a.nx / 4, ty = (parity == 0 ? 256 : 192) / tx > 0 ? (parity == 0 ? 256 : 192) / tx : 1;
-            dim3 block(tx, ty), grid(1, (a.ny + ty - 1) / ty, gz);
+            dim3 block(tx, ty), grid(1, (gy + ty - 1) / ty, gz);
             if (parity == 0) {
                 k_sweep4r<S, 0><<<grid, block, 0, st>>>(a);
             } else {
@@ -119,10 +123,10 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaSt
             // odd steps hold more live values (the x-shifted chunks): 6 rows per
             // block leave them 170 registers a thread at 2 blocks per SM
             if (parity == 0) {
-                dim3 block(32, 8), grid(a.nx / 128, (a.ny + 7) / 8, gz);
+                dim3 block(32, 8), grid(a.nx / 128, (gy + 7) / 8, gz);
                 k_sweep4<S, 0, 8><<<grid, block, 0, st>>>(a);
             } else {
-                dim3 block(32, 6), grid(a.nx / 128, (a.ny + 5) / 6, gz);
+                dim3 block(32, 6), grid(a.nx / 128, (gy + 5) / 6, gz);
                 k_sweep4<S, 1, 6><<<grid, block, 0, st>>>(a);
             }
             return;
@@ -134,7 +138,7 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaSt
             int bx = ((pairs + 31) / 32) * 32;
             if (bx > 128) bx = 128;
             const int by = 256 / bx;
-            dim3 block(bx, by), grid((pairs + bx - 1) / bx, (a.ny + by - 1) / by, gz);
+            dim3 block(bx, by), grid((pairs + bx - 1) / bx, (gy + by - 1) / by, gz);
             if constexpr (S == ST_F16 || S == ST_BF16) {
                 if (variant == 4 && 19 * a.Np < (int64_t(1) << 31)) {  // the packed form
                     if (parity == 0) k_sweep2p<S, 0><<<grid, block, 0, st>>>(a);
@@ -149,7 +153,7 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaSt
     }
     int bx = ((a.nx + 31) / 32) * 32;
     if (bx > 256) bx = 256;
-    dim3 grid((a.nx + bx - 1) / bx, a.ny, gz);
+    dim3 grid((a.nx + bx - 1) / bx, gy, gz);
     if (parity == 0) k_sweep<S, 0><<<grid, bx, 0, st>>>(a);
     else k_sweep<S, 1><<<grid, bx, 0, st>>>(a);
 }
@@ -162,21 +166,22 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, cudaSt
 // BF16: two cells per thread on kPlanes planes, software-pipelined (else as 2),
 // 6 = FP16 / BF16: four cells per thread in blocks of whole rows, odd-step
 // x-shifts through shared memory (nx % 4 == 0, nx <= 768; else as 2).
-// zmode / win / gz: plane selection (see SweepArgs); gz = grid planes (nz for
-// modes 0 and 1, an upper bound of the window length for mode 2).  Odd steps
-// sweep the planes in descending order.
+// zmode / win / gz / gy: cell selection (see SweepArgs); gz and gy = grid
+// planes and rows (nz and ny for modes 0 and 1, upper bounds of the window's
+// z and y lengths for mode 2).  Odd steps sweep the planes in descending
+// order.
 void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, int zmode,
-                  const int* win, int gz, cudaStream_t st) {
+                  const int* win, int gz, int gy, cudaStream_t st) {
     SweepArgs a = sweep_args(L, lambda_e, lambda_o);
     a.zmode = zmode;
     a.win = win;
     a.reverse = parity;
-    if (gz <= 0) return;
+    if (gz <= 0 || gy <= 0) return;
     switch (L.storage) {
-        case ST_F64: launch_s<ST_F64>(a, parity, variant, gz, st); break;
-        case ST_F32: launch_s<ST_F32>(a, parity, variant, gz, st); break;
-        case ST_F16: launch_s<ST_F16>(a, parity, variant, gz, st); break;
-        default: launch_s<ST_BF16>(a, parity, variant, gz, st); break;
+        case ST_F64: launch_s<ST_F64>(a, parity, variant, gz, gy, st); break;
+        case ST_F32: launch_s<ST_F32>(a, parity, variant, gz, gy, st); break;
+        case ST_F16: launch_s<ST_F16>(a, parity, variant, gz, gy, st); break;
+        default: launch_s<ST_BF16>(a, parity, variant, gz, gy, st); break;
     }
 }
 

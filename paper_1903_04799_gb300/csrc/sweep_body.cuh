@@ -44,9 +44,11 @@ struct SweepArgs {
     int64_t Np;
     double lambda_e, lambda_o, rho0;
     float scale, inv_scale;
-    // z-window split: mode 0 sweeps every plane; mode 1 ("far") the planes
-    // outside the window win[0..1] = (z0, length); mode 2 ("near") the planes
-    // inside it, blockIdx.z counting from z0
+    // near-body window split.  The window is the box of rows win[0..3] =
+    // (z0, z length, y0, y length), periodic in both.  Mode 0 sweeps every
+    // cell; mode 1 ("far") every cell outside the window; mode 2 ("near") the
+    // cells inside it, blockIdx.z counting planes from z0 and the grid's rows
+    // counting from y0
     TrtK K;  // collision constants (trt_constants)
     int zmode;
     const int* win;
@@ -58,7 +60,8 @@ struct SweepArgs {
 };
 
 // Plane of plane slot bz (grid z index, or a block's k-th plane in the
-// multi-plane form), or -1 if none.
+// multi-plane form), or -1 if none.  The far sweep leaves out a window plane
+// only when the window spans every row.
 __device__ __forceinline__ int sweep_plane_at(const SweepArgs& a, int bz) {
     if (a.zmode == 0) return a.reverse ? a.nz - 1 - bz : bz;
     const int z0 = __ldg(a.win), len = __ldg(a.win + 1);
@@ -69,7 +72,24 @@ __device__ __forceinline__ int sweep_plane_at(const SweepArgs& a, int bz) {
     }
     if (a.reverse) bz = a.nz - 1 - bz;
     const int rel = bz - z0 < 0 ? bz - z0 + a.nz : bz - z0;
-    return rel < len ? -1 : bz;
+    return rel < len && __ldg(a.win + 3) >= a.ny ? -1 : bz;
+}
+
+// Row swept by grid row ly on plane z (a plane sweep_plane_at returned), or
+// -1 if none.
+__device__ __forceinline__ int sweep_row(const SweepArgs& a, int ly, int z) {
+    if (a.zmode == 0) return ly < a.ny ? ly : -1;
+    const int y0 = __ldg(a.win + 2), ylen = __ldg(a.win + 3);
+    if (a.zmode == 2) {
+        if (ly >= ylen) return -1;
+        const int y = y0 + ly;
+        return y >= a.ny ? y - a.ny : y;
+    }
+    if (ly >= a.ny) return -1;
+    const int z0 = __ldg(a.win), zlen = __ldg(a.win + 1);
+    const int rz = z - z0 < 0 ? z - z0 + a.nz : z - z0;
+    const int ry = ly - y0 < 0 ? ly - y0 + a.ny : ly - y0;
+    return rz < zlen && ry < ylen ? -1 : ly;
 }
 
 // Plane swept by this block, or -1 if none.

@@ -295,6 +295,45 @@ def test_determinism_bitwise():
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("storage,variant", [("f64", 0), ("f32", 0), ("f32", 1), ("f16dev", 0), ("f16dev", 1),
+                                             ("f16dev", 3), ("f16dev", 4), ("f16dev", 5), ("bf16dev", 0)])
+def test_near_window_split_bitwise(storage, variant):
+    """The split step -- the far sweep beside the body step, then the sweep of
+    the near-body window, a box of rows bounded in z and y -- against
+    whole-lattice sweeps (the traced mode never splits): the same bits for
+    every population, owner and body state.  The swimmer sits across the
+    periodic faces in y and z, so the window wraps on both axes, and crosses
+    cells.  The run mixes eager units of both parities with graph replays,
+    consecutive lb_step calls (the last step's body kernels left pending
+    across them) and reads in between (which issue them)."""
+    shape = (128, 96, 96)
+    pos, e = (64.3, 2.7, 94.1), (0.3, 0.5, 1.0)
+    runs = []
+    for traced in (False, True):
+        g = Lattice(shape, collision="trt", storage=storage)
+        g.set_sweep_variant(variant)
+        gi = g.add_squirmer(pos, e, 6.0, 0.05, -3.0, mobile=True)
+        if traced:
+            g.profile_begin()
+        seen = []
+        for n, read in ((5, False), (16, True), (3, False), (9, True), (1, True), (8, False), (8, False)):
+            g.step(n)
+            if read:
+                seen.append(g.state(gi))
+        if traced:
+            g.profile_end()
+        runs.append((g.populations(), g.owner(), g.state(gi), seen))
+        g.close()
+    (fa, oa, sa, ra), (fb, ob, sb, rb) = runs
+    assert (oa == ob).all()
+    assert np.array_equal(fa, fb)
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)
+    for u, v in zip(ra, rb):
+        for x, y in zip(u, v):
+            assert np.array_equal(x, y)
+
+
 # ------------------------------------------------------------------ reduced storage
 
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16dev", 2e-2), ("bf16dev", 3e-1)])
