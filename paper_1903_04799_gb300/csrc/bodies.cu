@@ -1108,6 +1108,23 @@ struct Extent {
 // per step).  A z-normal wall spans every row.  Stored in win[P] for the
 // sweeps two steps later (see api.cu); the whole lattice when the bodies
 // spread over more than 3/5 of the planes.
+__device__ __forceinline__ void add_sphere_extent(const Lattice& L, const BodyParams& q, const double* pos, Extent& ez,
+                                                  Extent& ey) {
+    ez.add((int)floor(pos[2] - q.R) - 4, q.box_w[2] + 4, L.nz);
+    ey.add((int)floor(pos[1] - q.R) - 4, q.box_w[1] + 4, L.ny);
+}
+
+// The window when the lattice's only body is the sphere q at pos (as
+// near_window computes it then).
+__device__ void sphere_window(const Lattice& L, const BodyParams& q, const double* pos, int* win) {
+    Extent ez, ey;
+    add_sphere_extent(L, q, pos, ez, ey);
+    int w[4] = {0, L.nz, 0, L.ny};
+    ez.window(L.nz, w);
+    if (w[1] < L.nz) ey.window(L.ny, w + 2);
+    for (int i = 0; i < 4; ++i) win[i] = w[i];
+}
+
 template <int P>
 __device__ void near_window(const Bodies& B) {
     const Lattice& L = B.lats[0];
@@ -1116,9 +1133,7 @@ __device__ void near_window(const Bodies& B) {
     for (int j = L.body_begin; j < L.body_begin + L.body_count && !full; ++j) {
         const BodyParams& q = B.par[j];
         if (q.kind == BODY_SPHERE) {
-            const double* pos = B.state[1 - P][j].pos;
-            ez.add((int)floor(pos[2] - q.R) - 4, q.box_w[2] + 4, L.nz);
-            ey.add((int)floor(pos[1] - q.R) - 4, q.box_w[1] + 4, L.ny);
+            add_sphere_extent(L, q, B.state[1 - P][j].pos, ez, ey);
         } else if (q.wall_axis == 2) {
             ez.add(q.wall_index - 3, 3 + 4, L.nz);
             all_rows = true;
@@ -1376,6 +1391,8 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
     __shared__ int s_dryMode;
     __shared__ ShellGeo s_geo;
     __shared__ uint32_t s_stc[kStcBuf];
+    __shared__ uint32_t s_emask[kStcBuf];  // phase A's link mask of each stencil entry, for phase B
+    __shared__ int s_updated;              // rank 0: s_new holds this launch's new state
     __shared__ int s_lo[3];
     __shared__ long long sml[kFT / 32];
     __shared__ long long s_count, s_before;
@@ -1384,6 +1401,7 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i0 = B.fused_first[cls], nitems = B.n_fused[cls];
     if (threadIdx.x < 12) s_zero[threadIdx.x] = 0.0;
+    if (threadIdx.x == 0) s_updated = 0;
     for (int it = cid; it < nitems; it += ncl) {
         // everything of this body and lattice that the step reads, in one go
         // (the sweep streams the whole lattice through L2 between two steps,
@@ -1442,7 +1460,10 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
             if (threadIdx.x < 32)
                 update_body<P>(L, B, k, p, s0, s_A, sm + 12 * KC, &B.acc[k], &B.state[1 - P][k], &s_new, &s_mode);
             __syncthreads();
-            if (threadIdx.x == 0) s_mode = s_mode ? (near ? 2 : 1) : 0;
+            if (threadIdx.x == 0) {
+                s_mode = s_mode ? (near ? 2 : 1) : 0;
+                s_updated = 1;
+            }
             __syncthreads();
             if (s_mode == 2) append_items(B.box_items, B.n_box, B.box_cap, k, p.g_box, B.err, &s_base);
         }
@@ -1498,6 +1519,7 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
         for (long long r0 = b0; r0 < b1; r0 += kFT) {
             const long long b = r0 + threadIdx.x;
             int uncover = 0, ox = 0, oy = 0, oz = 0;
+            uint32_t emask = 0;
             float s32;
             if (b < b1) decode_off(entry(b), ox, oy, oz);
             if (b < b1 && geo_take(G, ox, oy, oz, s32)) {
@@ -1508,12 +1530,19 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
                 if (now != was) {
                     int x, y, z;
                     const int64_t n = geo_cell(L, G, ox, oy, oz, x, y, z);
+                    // the owner, committed at once: nothing of this step reads it
                     L.own[n] = now ? id : 0;
+                    L.own_prev[n] = now ? id : 0;
                     if (now) covered_momentum<true>(L, s, x, y, z, q, cacc);  // fluid -> solid: to the body
                     else uncover = 1;
                 }
-                if (!now) lcount += __popc(geo_mask(G, ox, oy, oz));
+                if (!now) {
+                    emask = geo_mask(G, ox, oy, oz);
+                    lcount += __popc(emask);
+                }
             }
+            // each thread reads back only its own entries in phase B
+            if (b - b0 < kStcBuf) s_emask[b - b0] = emask;
             // uncovered nodes of this round, refilled one per warp
             int nu;
             const int pos = block_scan<kFT>(uncover, &nu, s_scan);
@@ -1589,17 +1618,18 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
             const long long b = r0 + threadIdx.x;
             uint32_t mask = 0;
             int64_t n = 0;
-            int ox = 0, oy = 0, oz = 0;
-            float s32;
-            if (b < b1) decode_off(entry(b), ox, oy, oz);
-            if (b < b1 && geo_take(G, ox, oy, oz, s32)) {
+            if (b < b1) {
+                int ox, oy, oz;
+                decode_off(entry(b), ox, oy, oz);
+                if (b - b0 < kStcBuf) {
+                    mask = s_emask[b - b0];
+                } else {  // beyond the buffer: as phase A computed it
+                    float s32;
+                    if (geo_take(G, ox, oy, oz, s32) && !geo_inside(G, s32, G.pos, ox, oy, oz))
+                        mask = geo_mask(G, ox, oy, oz);
+                }
                 int x, y, z;
-                n = geo_cell(L, G, ox, oy, oz, x, y, z);
-                const bool now = geo_inside(G, s32, G.pos, ox, oy, oz);
-                const bool was =
-                    geo_inside(G, d2_off(ox + G.sh[0], oy + G.sh[1], oz + G.sh[2], G.fo), G.old, ox, oy, oz);
-                if (now != was) L.own_prev[n] = now ? id : 0;
-                if (!now) mask = geo_mask(G, ox, oy, oz);
+                if (mask) n = geo_cell(L, G, ox, oy, oz, x, y, z);
             }
             int tot;
             const int off = block_scan<kFT>(__popc(mask), &tot, s_scan);
@@ -1620,6 +1650,10 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
     // cluster to finish computes the near-body window of the coming sweeps,
     // as the rebuild kernel does otherwise.
     if (tail && B.win && rank == 0 && threadIdx.x == 0) {
+        if (ncl == 1 && s_updated) {  // one cluster: the window from the state it holds
+            sphere_window(s_L, s_p, s_new.pos, B.win + 4 * P);
+            return;
+        }
         __threadfence();
         if (atomicAdd(B.fused_done, 1) == ncl - 1) {
             *B.fused_done = 0;
