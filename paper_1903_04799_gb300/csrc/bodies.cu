@@ -752,25 +752,31 @@ __device__ __forceinline__ float classify_cell(const Lattice& L, const BodyParam
 template <bool CG>
 __device__ __noinline__ void covered_momentum(const Lattice& L, const BodyState& s, int x, int y, int z, int q,
                                               double* acc) {
+    // all 19 loads before the first add (one memory latency, not 19); the
+    // sums run in direction order
     double m[3] = {0.0, 0.0, 0.0};
     if (L.storage == ST_F64) {
-#pragma unroll 1
+        double f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = load_abs<CG>(L, read_slot(L, i, x, y, z, q), i);
+#pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double fi = load_abs<CG>(L, read_slot(L, i, x, y, z, q), i);
-            m[0] += fi * cx(i);
-            m[1] += fi * cy(i);
-            m[2] += fi * cz(i);
+            m[0] += f[i] * cx(i);
+            m[1] += f[i] * cy(i);
+            m[2] += f[i] * cz(i);
         }
     } else {
         // sum_i c_i w_i rho0 = 0: the momentum is that of the stored deviations,
         // summed in FP32 (their own precision)
+        float g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = load_dev<CG>(L, read_slot(L, i, x, y, z, q));
         float mf[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll 1
+#pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float gi = load_dev<CG>(L, read_slot(L, i, x, y, z, q));
-            mf[0] += gi * (float)cx(i);
-            mf[1] += gi * (float)cy(i);
-            mf[2] += gi * (float)cz(i);
+            mf[0] += g[i] * (float)cx(i);
+            mf[1] += g[i] * (float)cy(i);
+            mf[2] += g[i] * (float)cz(i);
         }
         for (int a = 0; a < 3; ++a) m[a] = (double)mf[a];
     }
@@ -918,19 +924,27 @@ __device__ __forceinline__ double warp_tree_sum(double v) {
 
 // Density of node (x, y, z) from its populations in the read slots of parity
 // q.  Reduced storages: rho0 plus the FP32 sum of the stored deviations (the
-// stored values carry FP32 precision or less), one FP64 add in all.
+// stored values carry FP32 precision or less), one FP64 add in all.  All 19
+// loads are issued before the first add (one memory latency, not 19); the
+// sum runs in direction order.
 template <bool CG>
 __device__ __forceinline__ double node_density(const Lattice& L, int x, int y, int z, int q) {
     if (L.storage == ST_F64) {
+        double f[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) f[j] = ld<CG>((const double*)L.F + read_slot(L, j, x, y, z, q));
         double r = 0.0;
-#pragma unroll 1
-        for (int j = 0; j < Q; ++j) r += ld<CG>((const double*)L.F + read_slot(L, j, x, y, z, q));
+#pragma unroll
+        for (int j = 0; j < Q; ++j) r += f[j];
         return r;
     }
-    float g = 0.0f;
-#pragma unroll 1
-    for (int j = 0; j < Q; ++j) g += load_dev<CG>(L, read_slot(L, j, x, y, z, q));
-    return L.rho0 + (double)g;
+    float g[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) g[j] = load_dev<CG>(L, read_slot(L, j, x, y, z, q));
+    float t = 0.0f;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) t += g[j];
+    return L.rho0 + (double)t;
 }
 
 // 1/k for k = 1..18, correctly rounded (the mean of k neighbour densities is
@@ -1332,13 +1346,26 @@ __device__ __forceinline__ int64_t geo_cell(const Lattice& L, const ShellGeo& G,
 }
 
 // Links from the fluid node ip + o to the sphere at its new centre, as a bit
-// mask over directions.
+// mask over directions.  The 18 FP32 tests are independent and unrolled, so
+// they overlap; the neighbours in the band, for which geo_inside takes the
+// exact test, follow one by one (rare).
 __device__ __forceinline__ uint32_t geo_mask(const ShellGeo& G, int ox, int oy, int oz) {
-    uint32_t mask = 0;
-#pragma unroll 1
+    const float f[3] = {G.fn[0], G.fn[1], G.fn[2]};
+    const float R2f = G.R2f, band = G.band;
+    uint32_t mask = 0, amb = 0;
+#pragma unroll
     for (int i = 1; i < Q; ++i) {
+        const float s = d2_off(ox + cx(i), oy + cy(i), oz + cz(i), f);
+        if (fabsf(s - R2f) > band) mask |= s < R2f ? 1u << i : 0u;
+        else amb |= 1u << i;
+    }
+    while (amb) {
+        const int i = __ffs(amb) - 1;
+        amb &= amb - 1;
         const int a = ox + cx(i), b = oy + cy(i), c = oz + cz(i);
-        if (geo_inside(G, d2_off(a, b, c, G.fn), G.pos, a, b, c)) mask |= 1u << i;
+        if (inside_exact(G.n3[0], G.n3[1], G.n3[2], G.pos, G.R, wrap1(G.ip[0] + a, G.n3[0]),
+                         wrap1(G.ip[1] + b, G.n3[1]), wrap1(G.ip[2] + c, G.n3[2])))
+            mask |= 1u << i;
     }
     return mask;
 }
@@ -1596,20 +1623,26 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
                 }
             }
         }
-        if (rank == 0 && threadIdx.x >= 32 && threadIdx.x < 38) {  // conversion force, blocks in rank order
-            const int c = threadIdx.x - 32;
-            double t = 0.0;
-            for (int r = 0; r < KC; ++r) t += cl.map_shared_rank(s_conv, r)[c];
-            // the update of this step consumed (zeroed) the previous booking
-            if (c < 3) A.Fc[c] = t;
-            else A.Tc[c - 3] = t;
+        // conversion force: the blocks' partials, all fetched at once (sm is
+        // free here), summed in rank order after the barrier
+        if (rank == 0 && threadIdx.x >= 32 && threadIdx.x < 32 + 6 * KC) {
+            const int t = threadIdx.x - 32;
+            sm[t] = cl.map_shared_rank(s_conv, t / 6)[t % 6];
         }
-        if (rank == 0 && threadIdx.x >= 64 && threadIdx.x < 67) {
-            const int a = threadIdx.x - 64;
+        if (rank == 0 && threadIdx.x >= 192 && threadIdx.x < 195) {  // threads clear of the fetch
+            const int a = threadIdx.x - 192;
             A.box_lo[a] = s_lo[a];
             A.r_class[a] = s.pos[a];
         }
         __syncthreads();
+        if (rank == 0 && threadIdx.x >= 32 && threadIdx.x < 38) {
+            const int c = threadIdx.x - 32;
+            double t = 0.0;
+            for (int r = 0; r < KC; ++r) t += sm[6 * r + c];
+            // the update of this step consumed (zeroed) the previous booking
+            if (c < 3) A.Fc[c] = t;
+            else A.Tc[c - 3] = t;
+        }
         const long long before = s_before;
         uint32_t* links = B.links + p.link_off;
         const long long cap = p.link_cap;

@@ -42,36 +42,83 @@ __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i
 
 enum Storage : int { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
-// Storage traits: the stored type, the arithmetic type of the collision, and
-// whether the store holds a deviation from w_i rho0.
+// Population traffic of the sweeps, marked evict-first in L2 (ld/st.global.cs).
+// A sweep reads and writes every population once, and a lattice larger than
+// L2 would otherwise evict everything else between two steps, the body
+// kernels' code and tables included.  With the hint those stay resident, and
+// a sweep still reuses the planes the previous sweep wrote last.
+template <class U>
+__device__ __forceinline__ U ld_stream(const U* p) {
+    U v;
+    if constexpr (sizeof(U) == 2) {
+        const unsigned short r = __ldcs(reinterpret_cast<const unsigned short*>(p));
+        memcpy(&v, &r, 2);
+    } else if constexpr (sizeof(U) == 4) {
+        const unsigned int r = __ldcs(reinterpret_cast<const unsigned int*>(p));
+        memcpy(&v, &r, 4);
+    } else if constexpr (sizeof(U) == 8) {
+        const uint2 r = __ldcs(reinterpret_cast<const uint2*>(p));
+        memcpy(&v, &r, 8);
+    } else {
+        static_assert(sizeof(U) == 16, "2, 4, 8 or 16 bytes");
+        const uint4 r = __ldcs(reinterpret_cast<const uint4*>(p));
+        memcpy(&v, &r, 16);
+    }
+    return v;
+}
+template <class U>
+__device__ __forceinline__ void st_stream(U* p, const U& v) {
+    if constexpr (sizeof(U) == 2) {
+        unsigned short r;
+        memcpy(&r, &v, 2);
+        __stcs(reinterpret_cast<unsigned short*>(p), r);
+    } else if constexpr (sizeof(U) == 4) {
+        unsigned int r;
+        memcpy(&r, &v, 4);
+        __stcs(reinterpret_cast<unsigned int*>(p), r);
+    } else if constexpr (sizeof(U) == 8) {
+        uint2 r;
+        memcpy(&r, &v, 8);
+        __stcs(reinterpret_cast<uint2*>(p), r);
+    } else {
+        static_assert(sizeof(U) == 16, "2, 4, 8 or 16 bytes");
+        uint4 r;
+        memcpy(&r, &v, 16);
+        __stcs(reinterpret_cast<uint4*>(p), r);
+    }
+}
+
+// Storage traits: the stored type, the arithmetic type of the collision,
+// whether the store holds a deviation from w_i rho0, and the sweeps'
+// (streaming) element access.
 template <int S> struct StoreT;
 template <> struct StoreT<ST_F64> {
     using T = double;
     using R = double;
     static constexpr bool dev = false;
-    __device__ static R load(const T* p, R) { return *p; }
-    __device__ static void store(T* p, R v, R) { *p = v; }
+    __device__ static R load(const T* p, R) { return ld_stream(p); }
+    __device__ static void store(T* p, R v, R) { st_stream(p, v); }
 };
 template <> struct StoreT<ST_F32> {
     using T = float;
     using R = float;
     static constexpr bool dev = true;
-    __device__ static R load(const T* p, R) { return *p; }
-    __device__ static void store(T* p, R v, R) { *p = v; }
+    __device__ static R load(const T* p, R) { return ld_stream(p); }
+    __device__ static void store(T* p, R v, R) { st_stream(p, v); }
 };
 template <> struct StoreT<ST_F16> {
     using T = __half;
     using R = float;
     static constexpr bool dev = true;
-    __device__ static R load(const T* p, R inv_scale) { return __half2float(*p) * inv_scale; }
-    __device__ static void store(T* p, R v, R scale) { *p = __float2half_rn(v * scale); }
+    __device__ static R load(const T* p, R inv_scale) { return __half2float(ld_stream(p)) * inv_scale; }
+    __device__ static void store(T* p, R v, R scale) { st_stream(p, __float2half_rn(v * scale)); }
 };
 template <> struct StoreT<ST_BF16> {
     using T = __nv_bfloat16;
     using R = float;
     static constexpr bool dev = true;
-    __device__ static R load(const T* p, R inv_scale) { return __bfloat162float(*p) * inv_scale; }
-    __device__ static void store(T* p, R v, R scale) { *p = __float2bfloat16_rn(v * scale); }
+    __device__ static R load(const T* p, R inv_scale) { return __bfloat162float(ld_stream(p)) * inv_scale; }
+    __device__ static void store(T* p, R v, R scale) { st_stream(p, __float2bfloat16_rn(v * scale)); }
 };
 
 inline int storage_bytes(int s) { return s == ST_F64 ? 8 : (s == ST_F32 ? 4 : 2); }

@@ -335,21 +335,21 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (P == 0) {
-            const V v = *reinterpret_cast<const V*>(F + (int64_t)i * Np + row(0, 0) + x0);
+            const V v = ld_stream(reinterpret_cast<const V*>(F + (int64_t)i * Np + row(0, 0) + x0));
             g0[i] = dec<S>(PV::lo(v), isc);
             g1[i] = dec<S>(PV::hi(v), isc);
         } else {
             const T* base = F + (int64_t)opp(i) * Np + row(-cy(i), -cz(i));
             if (cx(i) == 0) {
-                const V v = *reinterpret_cast<const V*>(base + x0);
+                const V v = ld_stream(reinterpret_cast<const V*>(base + x0));
                 g0[i] = dec<S>(PV::lo(v), isc);
                 g1[i] = dec<S>(PV::hi(v), isc);
             } else if (cx(i) == 1) {  // sources x0 - 1 and x0
-                g0[i] = dec<S>(base[xm0], isc);
-                g1[i] = dec<S>(base[x0], isc);
+                g0[i] = dec<S>(ld_stream(base + xm0), isc);
+                g1[i] = dec<S>(ld_stream(base + x0), isc);
             } else {  // sources x0 + 1 and x0 + 2
-                g0[i] = dec<S>(base[x0 + 1], isc);
-                g1[i] = dec<S>(base[xp1], isc);
+                g0[i] = dec<S>(ld_stream(base + x0 + 1), isc);
+                g1[i] = dec<S>(ld_stream(base + xp1), isc);
             }
         }
     }
@@ -358,17 +358,17 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (P == 0) {
-            *reinterpret_cast<V*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0) = enc2<S>(g0[i], g1[i], sc);
+            st_stream(reinterpret_cast<V*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0), enc2<S>(g0[i], g1[i], sc));
         } else {
             T* base = F + (int64_t)i * Np + row(cy(i), cz(i));
             if (cx(i) == 0) {
-                *reinterpret_cast<V*>(base + x0) = enc2<S>(g0[i], g1[i], sc);
+                st_stream(reinterpret_cast<V*>(base + x0), enc2<S>(g0[i], g1[i], sc));
             } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
-                base[x0 + 1] = enc<S>(g0[i], sc);
-                base[xp1] = enc<S>(g1[i], sc);
+                st_stream(base + x0 + 1, enc<S>(g0[i], sc));
+                st_stream(base + xp1, enc<S>(g1[i], sc));
             } else {  // targets x0 - 1 and x0
-                base[xm0] = enc<S>(g0[i], sc);
-                base[x0] = enc<S>(g1[i], sc);
+                st_stream(base + xm0, enc<S>(g0[i], sc));
+                st_stream(base + x0, enc<S>(g1[i], sc));
             }
         }
     }
@@ -412,12 +412,12 @@ __device__ __forceinline__ void sweep_two16(const SweepArgs& a, int x0, int y, i
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (P == 0) {
-            g[i] = *reinterpret_cast<const unsigned int*>(F + ((unsigned)i * Np + row(0, 0) + ux0));
+            g[i] = ld_stream(reinterpret_cast<const unsigned int*>(F + ((unsigned)i * Np + row(0, 0) + ux0)));
         } else {
             const unsigned int base = (unsigned)opp(i) * Np + row(-cy(i), -cz(i));
-            if (cx(i) == 0) g[i] = *reinterpret_cast<const unsigned int*>(F + (base + ux0));
-            else if (cx(i) == 1) g[i] = (unsigned int)F[base + xm0] | ((unsigned int)F[base + ux0] << 16);
-            else g[i] = (unsigned int)F[base + ux0 + 1] | ((unsigned int)F[base + xp1] << 16);
+            if (cx(i) == 0) g[i] = ld_stream(reinterpret_cast<const unsigned int*>(F + (base + ux0)));
+            else if (cx(i) == 1) g[i] = (unsigned int)ld_stream(F + (base + xm0)) | ((unsigned int)ld_stream(F + (base + ux0)) << 16);
+            else g[i] = (unsigned int)ld_stream(F + (base + ux0 + 1)) | ((unsigned int)ld_stream(F + (base + xp1)) << 16);
         }
     }
 #pragma unroll
@@ -435,17 +435,17 @@ __device__ __forceinline__ void sweep_two16(const SweepArgs& a, int x0, int y, i
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (P == 0) {
-            *reinterpret_cast<unsigned int*>(F + ((unsigned)opp(i) * Np + row(0, 0) + ux0)) = g[i];
+            st_stream(reinterpret_cast<unsigned int*>(F + ((unsigned)opp(i) * Np + row(0, 0) + ux0)), g[i]);
         } else {
             const unsigned int base = (unsigned)i * Np + row(cy(i), cz(i));
             if (cx(i) == 0) {
-                *reinterpret_cast<unsigned int*>(F + (base + ux0)) = g[i];
+                st_stream(reinterpret_cast<unsigned int*>(F + (base + ux0)), g[i]);
             } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
-                F[base + ux0 + 1] = (unsigned short)(g[i] & 0xffffu);
-                F[base + xp1] = (unsigned short)(g[i] >> 16);
+                st_stream(F + (base + ux0 + 1), (unsigned short)(g[i] & 0xffffu));
+                st_stream(F + (base + xp1), (unsigned short)(g[i] >> 16));
             } else {  // targets x0 - 1 and x0
-                F[base + xm0] = (unsigned short)(g[i] & 0xffffu);
-                F[base + ux0] = (unsigned short)(g[i] >> 16);
+                st_stream(F + (base + xm0), (unsigned short)(g[i] & 0xffffu));
+                st_stream(F + (base + ux0), (unsigned short)(g[i] >> 16));
             }
         }
     }
@@ -471,12 +471,12 @@ __device__ __forceinline__ void load_pair16(const SweepArgs& a, int x0, int y, i
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (P == 0) {
-            g[i] = __ldg(reinterpret_cast<const unsigned int*>(F + (int64_t)i * Np + row(0, 0) + x0));
+            g[i] = ld_stream(reinterpret_cast<const unsigned int*>(F + (int64_t)i * Np + row(0, 0) + x0));
         } else {
             const unsigned short* base = F + (int64_t)opp(i) * Np + row(-cy(i), -cz(i));
-            if (cx(i) == 0) g[i] = __ldg(reinterpret_cast<const unsigned int*>(base + x0));
-            else if (cx(i) == 1) g[i] = (unsigned int)__ldg(base + xm0) | ((unsigned int)__ldg(base + x0) << 16);
-            else g[i] = (unsigned int)__ldg(base + x0 + 1) | ((unsigned int)__ldg(base + xp1) << 16);
+            if (cx(i) == 0) g[i] = ld_stream(reinterpret_cast<const unsigned int*>(base + x0));
+            else if (cx(i) == 1) g[i] = (unsigned int)ld_stream(base + xm0) | ((unsigned int)ld_stream(base + x0) << 16);
+            else g[i] = (unsigned int)ld_stream(base + x0 + 1) | ((unsigned int)ld_stream(base + xp1) << 16);
         }
     }
 }
@@ -507,17 +507,17 @@ __device__ __forceinline__ void collide_store_pair16(const SweepArgs& a, int x0,
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (P == 0) {
-            *reinterpret_cast<unsigned int*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0) = g[i];
+            st_stream(reinterpret_cast<unsigned int*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0), g[i]);
         } else {
             unsigned short* base = F + (int64_t)i * Np + row(cy(i), cz(i));
             if (cx(i) == 0) {
-                *reinterpret_cast<unsigned int*>(base + x0) = g[i];
+                st_stream(reinterpret_cast<unsigned int*>(base + x0), g[i]);
             } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
-                base[x0 + 1] = (unsigned short)(g[i] & 0xffffu);
-                base[xp1] = (unsigned short)(g[i] >> 16);
+                st_stream(base + x0 + 1, (unsigned short)(g[i] & 0xffffu));
+                st_stream(base + xp1, (unsigned short)(g[i] >> 16));
             } else {  // targets x0 - 1 and x0
-                base[xm0] = (unsigned short)(g[i] & 0xffffu);
-                base[x0] = (unsigned short)(g[i] >> 16);
+                st_stream(base + xm0, (unsigned short)(g[i] & 0xffffu));
+                st_stream(base + x0, (unsigned short)(g[i] >> 16));
             }
         }
     }
@@ -550,19 +550,19 @@ __device__ __forceinline__ void sweep_four(const SweepArgs& a, int x0, int y, in
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (P == 0) {
-            g[i] = *reinterpret_cast<const uint2*>(F + ((unsigned)i * Np + row(0, 0) + x0));
+            g[i] = ld_stream(reinterpret_cast<const uint2*>(F + ((unsigned)i * Np + row(0, 0) + x0)));
         } else {
             const unsigned int base = (unsigned)opp(i) * Np + row(-cy(i), -cz(i));
-            const uint2 c = *reinterpret_cast<const uint2*>(F + (base + x0));
+            const uint2 c = ld_stream(reinterpret_cast<const uint2*>(F + (base + x0)));
             if (cx(i) == 0) {
                 g[i] = c;
             } else if (cx(i) == 1) {  // sources x0 - 1 .. x0 + 2
                 unsigned int prev = __shfl_up_sync(kAll, c.y, 1) >> 16;
-                if (lane == 0) prev = F[base + xl];
+                if (lane == 0) prev = ld_stream(F + (base + xl));
                 g[i] = make_uint2(prev | (c.x << 16), (c.x >> 16) | (c.y << 16));
             } else {  // sources x0 + 1 .. x0 + 4
                 unsigned int next = __shfl_down_sync(kAll, c.x, 1) & 0xffffu;
-                if (lane == 31) next = F[base + xr];
+                if (lane == 31) next = ld_stream(F + (base + xr));
                 g[i] = make_uint2((c.x >> 16) | (c.y << 16), (c.y >> 16) | (next << 16));
             }
         }
@@ -588,31 +588,31 @@ __device__ __forceinline__ void sweep_four(const SweepArgs& a, int x0, int y, in
     for (int i = 0; i < Q; ++i) {
         const uint2 o = g[i];  // post-collision f_i of cells x0 .. x0 + 3
         if (P == 0) {
-            *reinterpret_cast<uint2*>(F + ((unsigned)opp(i) * Np + row(0, 0) + x0)) = o;
+            st_stream(reinterpret_cast<uint2*>(F + ((unsigned)opp(i) * Np + row(0, 0) + x0)), o);
         } else {
             const unsigned int base = (unsigned)i * Np + row(cy(i), cz(i));
             if (cx(i) == 0) {
-                *reinterpret_cast<uint2*>(F + (base + x0)) = o;
+                st_stream(reinterpret_cast<uint2*>(F + (base + x0)), o);
             } else if (cx(i) == 1) {  // targets x0 + 1 .. x0 + 4
                 const unsigned int prev3 = __shfl_up_sync(kAll, o.y, 1) >> 16;
                 if (lane != 0) {
-                    *reinterpret_cast<uint2*>(F + (base + x0)) =
-                        make_uint2(prev3 | (o.x << 16), (o.x >> 16) | (o.y << 16));
+                    st_stream(reinterpret_cast<uint2*>(F + (base + x0)),
+                              make_uint2(prev3 | (o.x << 16), (o.x >> 16) | (o.y << 16)));
                 } else {  // element x0 comes from the warp to the left
-                    F[base + x0 + 1] = (unsigned short)(o.x & 0xffffu);
-                    *reinterpret_cast<unsigned int*>(F + (base + x0 + 2)) = (o.x >> 16) | (o.y << 16);
+                    st_stream(F + (base + x0 + 1), (unsigned short)(o.x & 0xffffu));
+                    st_stream(reinterpret_cast<unsigned int*>(F + (base + x0 + 2)), (o.x >> 16) | (o.y << 16));
                 }
-                if (lane == 31) F[base + xr] = (unsigned short)(o.y >> 16);
+                if (lane == 31) st_stream(F + (base + xr), (unsigned short)(o.y >> 16));
             } else {  // targets x0 - 1 .. x0 + 2
                 const unsigned int next0 = __shfl_down_sync(kAll, o.x, 1) & 0xffffu;
                 if (lane != 31) {
-                    *reinterpret_cast<uint2*>(F + (base + x0)) =
-                        make_uint2((o.x >> 16) | (o.y << 16), (o.y >> 16) | (next0 << 16));
+                    st_stream(reinterpret_cast<uint2*>(F + (base + x0)),
+                              make_uint2((o.x >> 16) | (o.y << 16), (o.y >> 16) | (next0 << 16)));
                 } else {  // element x0 + 3 comes from the warp to the right
-                    *reinterpret_cast<unsigned int*>(F + (base + x0)) = (o.x >> 16) | (o.y << 16);
-                    F[base + x0 + 2] = (unsigned short)(o.y >> 16);
+                    st_stream(reinterpret_cast<unsigned int*>(F + (base + x0)), (o.x >> 16) | (o.y << 16));
+                    st_stream(F + (base + x0 + 2), (unsigned short)(o.y >> 16));
                 }
-                if (lane == 0) F[base + xl] = (unsigned short)(o.x & 0xffffu);
+                if (lane == 0) st_stream(F + (base + xl), (unsigned short)(o.x & 0xffffu));
             }
         }
     }
@@ -645,14 +645,14 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (P == 0) {
-            if (active) g[i] = *reinterpret_cast<const uint2*>(F + (int64_t)i * Np + row(0, 0) + x0);
+            if (active) g[i] = ld_stream(reinterpret_cast<const uint2*>(F + (int64_t)i * Np + row(0, 0) + x0));
         } else {
             const unsigned short* base = F + (int64_t)opp(i) * Np + row(-cy(i), -cz(i));
             if (cx(i) == 0) {
-                if (active) g[i] = *reinterpret_cast<const uint2*>(base + x0);
+                if (active) g[i] = ld_stream(reinterpret_cast<const uint2*>(base + x0));
             } else {
                 if (active)
-                    *reinterpret_cast<uint2*>(rowbuf + d * dstride + x0) = *reinterpret_cast<const uint2*>(base + x0);
+                    *reinterpret_cast<uint2*>(rowbuf + d * dstride + x0) = ld_stream(reinterpret_cast<const uint2*>(base + x0));
                 ++d;
             }
         }
@@ -695,9 +695,9 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
     for (int i = 0; i < Q; ++i) {
         const uint2 o = g[i];
         if (P == 0) {
-            if (active) *reinterpret_cast<uint2*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0) = o;
+            if (active) st_stream(reinterpret_cast<uint2*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0), o);
         } else if (cx(i) == 0) {
-            if (active) *reinterpret_cast<uint2*>(F + (int64_t)i * Np + row(cy(i), cz(i)) + x0) = o;
+            if (active) st_stream(reinterpret_cast<uint2*>(F + (int64_t)i * Np + row(cy(i), cz(i)) + x0), o);
         } else {
             // targets x0 + 1 .. x0 + 4 (c_x = +1) or x0 - 1 .. x0 + 2 (c_x = -1)
             unsigned short* r = rowbuf + d * dstride;
@@ -718,8 +718,8 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
             const unsigned short* r = rowbuf + d * dstride;
             ++d;
             if (active)
-                *reinterpret_cast<uint2*>(F + (int64_t)i * Np + row(cy(i), cz(i)) + x0) =
-                    *reinterpret_cast<const uint2*>(r + x0);
+                st_stream(reinterpret_cast<uint2*>(F + (int64_t)i * Np + row(cy(i), cz(i)) + x0),
+                          *reinterpret_cast<const uint2*>(r + x0));
         }
     }
 }
