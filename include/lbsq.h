@@ -229,7 +229,10 @@ int64_t lb_kernel_launches(const lb_ctx* c);
  * thread on four consecutive planes, the loads of the next plane issued
  * before the collision of the current one (else as 2), 6 = FP16 / BF16: four
  * cells per thread in blocks of whole rows, the odd-step x-shifts through
- * shared memory (nx a multiple of 4 up to 768; else as 2).  Results are
+ * shared memory (nx a multiple of 4 up to 768; else as 2), 7 = FP16 / BF16:
+ * persistent CTAs whose loads are staged in shared memory by asynchronous
+ * 16-byte copies (cp.async), several rows ahead (nx a multiple of 8 up to 512
+ * and a 16-byte aligned array; else as 2).  Results are
  * identical bit for bit; only the speed differs.  LB_ERR_INVALID for another
  * value. */
 lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant);

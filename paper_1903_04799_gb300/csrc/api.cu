@@ -238,6 +238,7 @@ bool check_device_error(lb_ctx* c, lb_status* out) {
         const char* what = h == LB_ERR_OVERLAP    ? "a body overlaps another body or a wall"
                            : h == LB_ERR_DIVERGED ? "a body reached |v| >= 1/2"
                            : h == LB_ERR_CAPACITY ? "a boundary-link list outgrew its capacity"
+                           : h == LB_ERR_TIMEOUT  ? "a bounded device wait ran out"
                                                   : "device error";
         *out = fail(c, (lb_status)h, what);
         return true;
@@ -991,7 +992,7 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
 }
 
 lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant) {
-    if (!c || variant < 0 || variant > 6) return LB_ERR_INVALID;
+    if (!c || variant < 0 || variant > 7) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
     settle(c);
     c->sweep_variant = variant;

@@ -57,6 +57,10 @@ struct SweepArgs {
     // planes the previous sweep wrote last, which are still in L2.  Any plane
     // order gives the same result (each cell touches only its own slots).
     int reverse;
+    int* err;  // the lattice's device error word (bounded waits that run out)
+    // two-cell form: the plane, this many planes ahead in sweep order, whose
+    // sources each thread prefetches into L2 (0: none; see sweep_two)
+    int pf;
 };
 
 // Plane of plane slot bz (grid z index, or a block's k-th plane in the
@@ -331,6 +335,24 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
     const float isc = kScaled<S> ? 1.0f : a.inv_scale, sc = kScaled<S> ? 1.0f : a.scale;
     const R rho0 = kScaled<S> ? (R)a.rho0 * (R)a.scale : (R)a.rho0;
     auto row = [&](int dy, int dz) -> int64_t { return (int64_t)nx * (ys[1 + dy] + (int64_t)ny * zs[1 + dz]); };
+    // Prefetch into L2 what this thread's cells will read a.pf planes ahead in
+    // sweep order: the block that sweeps that plane starts later, when the
+    // blocks resident now (about a.pf - 2 planes of them) are done, and finds
+    // its sources in L2.  A prefetch holds no register, so it adds to the bytes
+    // in flight that the loads below are short of.
+    if (a.pf) {
+        const int zp = z + (a.reverse ? -a.pf : a.pf);
+        if (zp >= 0 && zp < nz) {
+            const int zsp[3] = {zp == 0 ? nz - 1 : zp - 1, zp, zp == nz - 1 ? 0 : zp + 1};
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const T* src = P == 0 ? F + (int64_t)i * Np + (int64_t)nx * (y + (int64_t)ny * zp) + x0
+                                      : F + (int64_t)opp(i) * Np +
+                                            (int64_t)nx * (ys[1 - cy(i)] + (int64_t)ny * zsp[1 - cz(i)]) + x0;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(src));
+            }
+        }
+    }
     R g0[Q], g1[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -741,6 +763,8 @@ __host__ __device__ inline SweepArgs sweep_args(const Lattice& L, double lambda_
     a.zmode = 0;
     a.win = nullptr;
     a.reverse = 0;
+    a.err = L.err;
+    a.pf = 0;
     return a;
 }
 
