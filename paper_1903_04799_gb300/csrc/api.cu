@@ -95,7 +95,9 @@ struct lb_ctx {
     std::string msg;
     std::vector<std::pair<void*, size_t>> allocs;
     // graph of two steps (even then odd)
-    cudaGraphExec_t graph = nullptr;
+    // graphs of 8 steps: [0] whole steps, or (split lattices) 8 units from t =
+    // 1 (mod 4); [1] split lattices, 8 units from t = 3 (mod 4)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_launches = 0;  // kernel launches in one replay
     int sweep_variant = 0;
     // overlap of the body kernels of step t with the far sweep of step t+1:
@@ -104,7 +106,7 @@ struct lb_ctx {
     cudaStream_t side = nullptr, hi = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     cudaEvent_t ev_started = nullptr;  // every block of the fused body kernel has begun (see enqueue_unit)
-    int* d_win = nullptr;  // [2][4] near-body windows (z0, z length, y0, y length) by step parity
+    int* d_win = nullptr;  // [4][4] near-body windows (z0, z length, y0, y length) by step (mod 4)
     bool split = false;    // whether steps are split into far and near sweeps
     int win_max = 0;       // upper bound of the window's z length (planes)
     int ywin_max = 0;      // upper bound of its y length (rows)
@@ -163,8 +165,10 @@ T* dalloc_t(lb_ctx* c, size_t n) {
 }
 
 void drop_graph(lb_ctx* c) {
-    if (c->graph) cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
+    for (auto& g : c->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
 }
 
 Bodies bodies_view(const lb_ctx* c) {
@@ -190,13 +194,25 @@ Bodies bodies_view(const lb_ctx* c) {
     B.rel_cap = c->list_cap;
     B.done = c->d_counts + 3;
     B.err = c->d_err;
-    B.win = c->split ? c->d_win : nullptr;
+    B.win = nullptr;  // see bodies_for_step
     B.gstep = nullptr;
     B.fused_items = c->d_fused_items;
     B.n_fused = c->d_counts + 4;
     B.fused_first = c->d_counts + 7;
     B.stencil = c->d_stencil;
     B.fused_done = c->d_counts + 10;
+    return B;
+}
+
+// Window slot of the sweeps of step s.  Four slots by step: the body kernels
+// of step t write slot t + 2 while the far sweep of step t, which reads slot t,
+// may still run beside them (see enqueue_unit).
+int* win_slot(const lb_ctx* c, int64_t s) { return c->d_win + 4 * (int)(s & 3); }
+
+// The view for the body kernels of step t: they write the window of step t + 2.
+Bodies bodies_for_step(const lb_ctx* c, int64_t t) {
+    Bodies B = bodies_view(c);
+    if (c->split) B.win = win_slot(c, t + 2);
     return B;
 }
 
@@ -414,7 +430,13 @@ lb_status relayout(lb_ctx* c) {
     c->ywin_max = ymax * 5 < 3 * c->L.ny ? ymax : c->L.ny;
     c->split = !across && nb > 0 && wmax * 5 < 3 * c->L.nz;
     // whole lattice until the first rebuild
-    const int win_init[8] = {0, c->L.nz, 0, c->L.ny, 0, c->L.nz, 0, c->L.ny};
+    int win_init[16];
+    for (int k = 0; k < 4; ++k) {
+        win_init[4 * k] = 0;
+        win_init[4 * k + 1] = c->L.nz;
+        win_init[4 * k + 2] = 0;
+        win_init[4 * k + 3] = c->L.ny;
+    }
     CK(cudaMemcpyAsync(c->d_win, win_init, sizeof(win_init), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));  // host vectors above are transient
     drop_graph(c);
@@ -452,6 +474,7 @@ lb_status relink_all(lb_ctx* c) {
     lb_status s = set_list(c, 2, all);
     if (s != LB_OK) return s;
     Bodies B = bodies_view(c);
+    if (c->split) B.win = win_slot(c, c->step + 1);  // the first split sweep, of step + 1
     launch_set_flags(c->d_acc, nb, -1, 0, c->stream);
     launch_body_kernel(3, B, 1 - cur, 1, c->grid_box, nullptr, c->stream);
     launch_body_kernel(4, B, 1 - cur, 1, c->grid_box, nullptr, c->stream);
@@ -552,7 +575,7 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     c->d_count = dalloc_t<int>(c, 2);
     c->d_lat = dalloc_t<Lattice>(c, 1);
     c->d_counts = dalloc_t<int>(c, 11);
-    c->d_win = dalloc_t<int>(c, 8);
+    c->d_win = dalloc_t<int>(c, 16);
     int prio_lo = 0, prio_hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) return bail(LB_ERR_CUDA);
     if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
@@ -848,7 +871,7 @@ static void enqueue_traced_step(lb_ctx* c) {
             sweep_all(c, parity, c->stream);
             c->launches += 1;
         } else if (k == 1) {
-            const Bodies B = bodies_view(c);
+            const Bodies B = bodies_for_step(c, c->step);
             if (c->n_fused > 0) {
                 launch_body_fused(B, parity, c->fused_cls, c->n_fused, c->stream, 0);
                 c->launches += 1;
@@ -858,7 +881,8 @@ static void enqueue_traced_step(lb_ctx* c) {
                 c->launches += 1;
             }
         } else {
-            launch_body_kernel(k, bodies_view(c), parity, c->n_link_items, c->grid_box, nullptr, c->stream);
+            launch_body_kernel(k, bodies_for_step(c, c->step), parity, c->n_link_items, c->grid_box, nullptr,
+                               c->stream);
             c->launches += 1;
         }
         cudaEventRecord(pool_event(c, e0 + 1), c->stream);
@@ -881,51 +905,74 @@ static void enqueue_steps(lb_ctx* c, int64_t n) {
 }
 
 // When the bodies occupy a thin box of rows, steps run as a pipeline of
-// units.  Unit t: the body kernels of step t (whose sweep is done) on `hi`,
-// beside the far sweep of step t+1 (every cell outside the near-body window,
-// none of whose slots the body kernels touch) on `side`; then the near sweep
-// of step t+1.  After a unit the body kernels of step t+1 are pending.
+// units on two chains.  Unit t issues the body kernels of step t (whose sweep
+// is done) and the near sweep of step t+1 (the window) on `hi`, and the far
+// sweep of step t+1 (every cell outside the window) on `side`.
+//   - near(t+1) waits for body(t) (stream order) and far(t): a sweep's cells
+//     touch only their own slots, so it does not wait for far(t+1);
+//   - far(t+1) waits for far(t) (stream order) and near(t), and for the
+//     clusters of body(t) to be placed (see below), not for body(t) to end:
+//     the window of step t+1, computed two steps ahead with two cells to
+//     spare, holds every cell the body kernels of steps t and t+1 touch.
+// The far sweeps run back to back and set the pace; body and near sweep run
+// beside them.  After a unit the body kernels of step t+1 are pending:
 // lb_step returns with them pending, so that consecutive calls keep the
-// overlap; every call that reads or changes the context issues them first.
-static void enqueue_unit(lb_ctx* c) {
-    const int parity = (int)((c->step - 1) & 1), q = 1 - parity;
-    const Bodies B = bodies_view(c);
-    const int* win = c->d_win + 4 * q;
+// overlap, and every call that reads or changes the context issues them
+// first (settle).
+
+// Start of a run of units: both chains wait for everything issued so far.
+static void begin_units(lb_ctx* c) {
     cudaEventRecord(c->ev_fork, c->stream);
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     cudaStreamWaitEvent(c->hi, c->ev_fork, 0);
+    cudaEventRecord(c->ev_join, c->stream);   // "the last far sweep"
+    cudaEventRecord(c->ev_join2, c->stream);  // "the last near sweep"
+}
+
+static void enqueue_unit(lb_ctx* c) {
+    const int64_t t = c->step - 1;
+    const int parity = (int)(t & 1), q = 1 - parity;
+    const int* win = win_slot(c, t + 1);
     // the far sweep starts once the fused kernel's clusters are placed: started
     // first, it would fill every SM, and a cluster waits for SMs of one GPC to
     // drain together
     const bool fused = c->solo || c->n_fused > 0;
-    c->launches += body_step(c, B, parity, c->hi, fused ? c->ev_started : nullptr);
+    c->launches += body_step(c, bodies_for_step(c, t), parity, c->hi, fused ? c->ev_started : nullptr);
+    cudaStreamWaitEvent(c->hi, c->ev_join, 0);  // far(t), before near(t+1)
     if (fused) cudaStreamWaitEvent(c->side, c->ev_started, 0);
+    cudaStreamWaitEvent(c->side, c->ev_join2, 0);  // near(t), before far(t+1)
     launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 1, win, c->L.nz, c->L.ny, c->side);
     cudaEventRecord(c->ev_join, c->side);
+    launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 2, win, c->win_max, c->ywin_max, c->hi);
     cudaEventRecord(c->ev_join2, c->hi);
-    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-    cudaStreamWaitEvent(c->stream, c->ev_join2, 0);
-    launch_sweep(c->L, c->lambda_e, c->lambda_o, q, c->sweep_variant, 2, win, c->win_max, c->ywin_max, c->stream);
     c->launches += 2;
     c->step++;
+}
+
+// End of a run of units: the context's stream waits for both chains.
+static void end_units(lb_ctx* c) {
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    cudaStreamWaitEvent(c->stream, c->ev_join2, 0);
 }
 
 // Issue the pending body kernels, if any: the context then holds whole steps.
 static void settle(lb_ctx* c) {
     if (!c->pending) return;
-    c->launches += body_step(c, bodies_view(c), (int)((c->step - 1) & 1), c->stream);
+    c->launches += body_step(c, bodies_for_step(c, c->step - 1), (int)((c->step - 1) & 1), c->stream);
     c->pending = false;
 }
 
 constexpr int kGraphSteps = 8;
 
-static lb_status build_graph(lb_ctx* c) {
+static lb_status build_graph(lb_ctx* c, int which) {
     cudaGraph_t g = nullptr;
     const int64_t saved_launches = c->launches, saved_step = c->step;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     if (c->split) {
-        c->step = 2;  // 8 units from t = 1
+        c->step = 2 + 2 * which;  // 8 units from t = 1 or 3 (the window slots repeat every 4 steps)
+        begin_units(c);
         for (int k = 0; k < kGraphSteps; ++k) enqueue_unit(c);
+        end_units(c);
     } else {
         c->step = 0;  // 8 steps from an even step
         enqueue_steps(c, kGraphSteps);
@@ -935,10 +982,10 @@ static lb_status build_graph(lb_ctx* c) {
     c->launches = saved_launches;
     c->step = saved_step;
     if (e != cudaSuccess) return cuda_fail(c, e, "capture");
-    e = cudaGraphInstantiate(&c->graph, g, 0);
+    e = cudaGraphInstantiate(&c->graph[which], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        c->graph = nullptr;
+        c->graph[which] = nullptr;
         return cuda_fail(c, e, "instantiate");
     }
     return LB_OK;
@@ -963,7 +1010,9 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
             left--;
         }
         if (left > 0 && ((c->step - 1) & 1) == 0) {  // graphs start on a unit of odd t
+            begin_units(c);
             enqueue_unit(c);
+            end_units(c);
             left--;
         }
     } else if (left > 0 && (c->step & 1)) {  // graphs start on even steps
@@ -971,19 +1020,23 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
         left--;
     }
     if (left >= kGraphSteps) {
-        if (!c->graph) {
-            lb_status s = build_graph(c);
+        // split lattices: t = step - 1 is odd here; t = 3 (mod 4) takes graph 1
+        const int which = c->split ? (int)(((c->step - 1) >> 1) & 1) : 0;
+        if (!c->graph[which]) {
+            lb_status s = build_graph(c, which);
             if (s != LB_OK) return s;
         }
         while (left >= kGraphSteps) {
-            CK(cudaGraphLaunch(c->graph, c->stream));
+            CK(cudaGraphLaunch(c->graph[which], c->stream));
             c->launches += c->graph_launches;
             c->step += kGraphSteps;
             left -= kGraphSteps;
         }
     }
-    if (c->split) {
+    if (c->split && left > 0) {
+        begin_units(c);
         for (; left > 0; --left) enqueue_unit(c);
+        end_units(c);
     } else if (left > 0) {
         enqueue_steps(c, left);
     }

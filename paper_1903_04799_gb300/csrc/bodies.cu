@@ -1116,11 +1116,11 @@ struct Extent {
     }
 };
 
-// Window of lattice 0 that holds every cell the body kernels of the next step
-// can touch: the z- and y-extent of every body's scan box at the new
+// Window of lattice 0 that holds every cell the body kernels of the next two
+// steps can touch: the z- and y-extent of every body's scan box at the new
 // positions, two more cells on each side (a body moves less than half a cell
-// per step).  A z-normal wall spans every row.  Stored in win[P] for the
-// sweeps two steps later (see api.cu); the whole lattice when the bodies
+// per step).  A z-normal wall spans every row.  Stored at B.win, the slot of
+// the sweeps two steps later (see api.cu); the whole lattice when the bodies
 // spread over more than 3/5 of the planes.
 __device__ __forceinline__ void add_sphere_extent(const Lattice& L, const BodyParams& q, const double* pos, Extent& ez,
                                                   Extent& ey) {
@@ -1160,7 +1160,7 @@ __device__ void near_window(const Bodies& B) {
         ez.window(L.nz, w);
         if (w[1] < L.nz && !all_rows) ey.window(L.ny, w + 2);
     }
-    for (int i = 0; i < 4; ++i) B.win[4 * P + i] = w[i];
+    for (int i = 0; i < 4; ++i) B.win[i] = w[i];
 }
 
 template <int P>
@@ -1684,7 +1684,7 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
     // as the rebuild kernel does otherwise.
     if (tail && B.win && rank == 0 && threadIdx.x == 0) {
         if (ncl == 1 && s_updated) {  // one cluster: the window from the state it holds
-            sphere_window(s_L, s_p, s_new.pos, B.win + 4 * P);
+            sphere_window(s_L, s_p, s_new.pos, B.win);
             return;
         }
         __threadfence();
@@ -1753,10 +1753,10 @@ void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaS
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (started) {
-        attr[1].id = cudaLaunchAttributeLaunchCompletionEvent;
-        attr[1].val.launchCompletionEvent.event = started;
-        attr[1].val.launchCompletionEvent.flags = 0;
-        cfg.numAttrs = 2;
+        attr[cfg.numAttrs].id = cudaLaunchAttributeLaunchCompletionEvent;
+        attr[cfg.numAttrs].val.launchCompletionEvent.event = started;
+        attr[cfg.numAttrs].val.launchCompletionEvent.flags = 0;
+        cfg.numAttrs++;
     }
     if (parity == 0) cudaLaunchKernelEx(&cfg, k_body_fused<0>, B, cls, tail);
     else cudaLaunchKernelEx(&cfg, k_body_fused<1>, B, cls, tail);

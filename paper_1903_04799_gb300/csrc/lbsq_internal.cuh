@@ -307,7 +307,7 @@ struct Bodies {
     int rel_cap;
     int* done;             // blocks of the rebuild kernel that finished (self-resetting)
     int* err;              // error word for list overflow (shared)
-    int* win;              // near-body windows [2][4] of lattice 0 (z0, z length, y0, y length) by step parity, or null
+    int* win;              // near-body window (z0, z length, y0, y length) of lattice 0 this launch writes, or null
     long long* gstep;      // server: global step counter, advanced by the rebuild kernel (or null)
     // spheres advanced by k_body_fused (body, lattice), grouped by cluster
     // class: class c holds items [fused_first[c], fused_first[c] + n_fused[c])
