@@ -213,6 +213,34 @@ lb_status lb_get_mass(lb_ctx* c, double* mass, double mom[3]);
  * the number of links.  Synchronises. */
 lb_status lb_get_links(lb_ctx* c, int32_t id, int64_t* out, int64_t cap, int64_t* count);
 
+/* Checkpoint and resume.  The paper's method has no counterpart: this saves a
+ * run so that it can continue later, bit for bit.
+ *
+ * lb_checkpoint_size writes the bytes a checkpoint of the context takes now.
+ * lb_checkpoint writes the checkpoint into the caller's host buffer buf of
+ * `bytes` bytes (at least lb_checkpoint_size).  It holds:
+ *   - the populations in the lattice's own storage;
+ *   - both owner fields;
+ *   - per body, its two state buffers, its accumulators (force, torque,
+ *     stresslet, conversion force, averages) and its link list;
+ *   - the near-body windows and the step count.
+ * Pending body kernels are issued first (see lb_step).
+ *
+ * lb_restore loads a checkpoint into a context set up the same way: the
+ * same lb_params and the same bodies, added in the same order (their
+ * positions may differ: the checkpoint's replace them).  Stepping it then
+ * gives the bits the checkpointed context would have given.  The caller's
+ * buffer is not kept.  The format is that of this build of the library
+ * (host byte order, the library's structure layouts).
+ *
+ * Errors: LB_ERR_INVALID (NULL, buffer too small, not a checkpoint, or one of
+ * another lattice, other bodies, or a link list larger than this context
+ * holds; nothing is changed then), LB_ERR_STATE (the context holds a device
+ * error), LB_ERR_CUDA. */
+lb_status lb_checkpoint_size(lb_ctx* c, size_t* bytes);
+lb_status lb_checkpoint(lb_ctx* c, void* buf, size_t bytes);
+lb_status lb_restore(lb_ctx* c, const void* buf, size_t bytes);
+
 /* Message of the last failing call on c, or "" -- valid until the next call on c. */
 const char* lb_last_error(const lb_ctx* c);
 

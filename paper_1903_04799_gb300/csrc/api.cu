@@ -1229,4 +1229,194 @@ lb_status lb_get_links(lb_ctx* c, int32_t id, int64_t* out, int64_t cap, int64_t
     return LB_OK;
 }
 
+
+// ---------------------------------------------------------------- checkpoint
+
+namespace {
+
+constexpr char kCkptMagic[8] = {'L', 'B', 'S', 'Q', 'C', 'K', 'P', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, storage;
+    int32_t nx, ny, nz, nbodies;
+    double lambda_e, lambda_o, rho0;
+    double scale;
+    int64_t step;
+    uint64_t bodies_hash;  // the bodies' defining parameters (see bodies_hash)
+    uint64_t bytes;        // the whole checkpoint
+};
+
+// FNV-1a over the parameters that define the bodies (not the derived layout).
+uint64_t bodies_hash(const lb_ctx* c) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t k = 0; k < n; ++k) h = (h ^ b[k]) * 1099511628211ull;
+    };
+    for (size_t k = 0; k < c->par.size(); ++k) {
+        const BodyParams& q = c->par[k];
+        mix(&c->kind[k], sizeof(int));
+        mix(&q.kind, sizeof(q.kind));
+        mix(&q.mobile, sizeof(q.mobile));
+        mix(&q.R, sizeof(q.R));
+        mix(&q.B1, sizeof(q.B1));
+        mix(&q.B2, sizeof(q.B2));
+        mix(&q.mass, sizeof(q.mass));
+        mix(&q.inertia, sizeof(q.inertia));
+        mix(q.wall_vel, sizeof(q.wall_vel));
+        mix(&q.wall_axis, sizeof(q.wall_axis));
+        mix(&q.wall_index, sizeof(q.wall_index));
+    }
+    mix(&c->wca_sigma, sizeof(double));
+    mix(&c->wca_eps, sizeof(double));
+    return h;
+}
+
+size_t pop_bytes(const lb_ctx* c) { return (size_t)Q * c->L.Np * storage_bytes(c->p.storage); }
+
+// The bodies' accumulators (link counts included), read after the step work.
+lb_status read_accs(lb_ctx* c, std::vector<BodyAcc>& acc) {
+    acc.resize(c->par.size());
+    if (!acc.empty())
+        CK(cudaMemcpyAsync(acc.data(), c->d_acc, sizeof(BodyAcc) * acc.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+size_t ckpt_bytes(const lb_ctx* c, const std::vector<BodyAcc>& acc) {
+    size_t n = sizeof(CkptHeader) + pop_bytes(c) + 2 * sizeof(int32_t) * (size_t)c->L.N + 16 * sizeof(int);
+    for (const BodyAcc& a : acc) n += 2 * sizeof(BodyState) + sizeof(BodyAcc) + sizeof(uint32_t) * (size_t)a.link_count;
+    return n;
+}
+
+}  // namespace
+
+lb_status lb_checkpoint_size(lb_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
+    lb_status s = sync_checked(c);
+    if (s != LB_OK) return s;
+    std::vector<BodyAcc> acc;
+    s = read_accs(c, acc);
+    if (s != LB_OK) return s;
+    *bytes = ckpt_bytes(c, acc);
+    return LB_OK;
+}
+
+lb_status lb_checkpoint(lb_ctx* c, void* buf, size_t bytes) {
+    if (!c || !buf) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
+    lb_status s = sync_checked(c);
+    if (s != LB_OK) return s;
+    std::vector<BodyAcc> acc;
+    s = read_accs(c, acc);
+    if (s != LB_OK) return s;
+    const size_t need = ckpt_bytes(c, acc);
+    if (bytes < need) return fail(c, LB_ERR_INVALID, "checkpoint buffer too small (see lb_checkpoint_size)");
+    unsigned char* o = static_cast<unsigned char*>(buf);
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.storage = (uint32_t)c->p.storage;
+    h.nx = c->L.nx;
+    h.ny = c->L.ny;
+    h.nz = c->L.nz;
+    h.nbodies = (int32_t)c->par.size();
+    h.lambda_e = c->lambda_e;
+    h.lambda_o = c->lambda_o;
+    h.rho0 = c->L.rho0;
+    h.scale = c->L.scale;
+    h.step = c->step;
+    h.bodies_hash = bodies_hash(c);
+    h.bytes = need;
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    const size_t N = (size_t)c->L.N;
+    CK(cudaMemcpyAsync(o, c->L.F, pop_bytes(c), cudaMemcpyDeviceToHost, c->stream));
+    o += pop_bytes(c);
+    CK(cudaMemcpyAsync(o, c->own, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, c->stream));
+    o += sizeof(int32_t) * N;
+    CK(cudaMemcpyAsync(o, c->own_prev, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, c->stream));
+    o += sizeof(int32_t) * N;
+    CK(cudaMemcpyAsync(o, c->d_win, 16 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    o += 16 * sizeof(int);
+    for (size_t k = 0; k < acc.size(); ++k) {
+        CK(cudaMemcpyAsync(o, c->d_state[0] + k, sizeof(BodyState), cudaMemcpyDeviceToHost, c->stream));
+        o += sizeof(BodyState);
+        CK(cudaMemcpyAsync(o, c->d_state[1] + k, sizeof(BodyState), cudaMemcpyDeviceToHost, c->stream));
+        o += sizeof(BodyState);
+        std::memcpy(o, &acc[k], sizeof(BodyAcc));
+        o += sizeof(BodyAcc);
+        const size_t nl = (size_t)acc[k].link_count;
+        if (nl)
+            CK(cudaMemcpyAsync(o, c->d_links + c->par[k].link_off, sizeof(uint32_t) * nl, cudaMemcpyDeviceToHost,
+                               c->stream));
+        o += sizeof(uint32_t) * nl;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_restore(lb_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf || bytes < sizeof(CkptHeader)) return LB_ERR_INVALID;
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) return fail(c, LB_ERR_INVALID, "not a checkpoint");
+    if (h.bytes != bytes) return fail(c, LB_ERR_INVALID, "checkpoint size differs from its header");
+    if (h.storage != (uint32_t)c->p.storage || h.nx != c->L.nx || h.ny != c->L.ny || h.nz != c->L.nz ||
+        h.lambda_e != c->lambda_e || h.lambda_o != c->lambda_o || h.rho0 != c->L.rho0 ||
+        h.scale != (double)c->L.scale)
+        return fail(c, LB_ERR_INVALID, "checkpoint of a lattice with other parameters");
+    if (h.nbodies != (int32_t)c->par.size() || h.bodies_hash != bodies_hash(c))
+        return fail(c, LB_ERR_INVALID, "checkpoint of other bodies (add the same bodies in the same order)");
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
+    lb_status s = sync_checked(c);
+    if (s != LB_OK) return s;
+    // walk the sections once to check the link counts before anything is written
+    const unsigned char* base = static_cast<const unsigned char*>(buf);
+    const size_t N = (size_t)c->L.N;
+    const size_t fixed = sizeof(CkptHeader) + pop_bytes(c) + 2 * sizeof(int32_t) * N + 16 * sizeof(int);
+    std::vector<BodyAcc> acc(c->par.size());
+    std::vector<size_t> at(c->par.size());
+    size_t off = fixed;
+    for (size_t k = 0; k < acc.size(); ++k) {
+        if (off + 2 * sizeof(BodyState) + sizeof(BodyAcc) > bytes) return fail(c, LB_ERR_INVALID, "truncated checkpoint");
+        at[k] = off;
+        std::memcpy(&acc[k], base + off + 2 * sizeof(BodyState), sizeof(BodyAcc));
+        if (acc[k].link_count < 0 || acc[k].link_count > c->par[k].link_cap)
+            return fail(c, LB_ERR_INVALID, "checkpoint link list larger than this context holds");
+        off += 2 * sizeof(BodyState) + sizeof(BodyAcc) + sizeof(uint32_t) * (size_t)acc[k].link_count;
+    }
+    if (off != bytes) return fail(c, LB_ERR_INVALID, "checkpoint size differs from its sections");
+    const unsigned char* o = base + sizeof(CkptHeader);
+    CK(cudaMemcpyAsync(c->L.F, o, pop_bytes(c), cudaMemcpyHostToDevice, c->stream));
+    o += pop_bytes(c);
+    CK(cudaMemcpyAsync(c->own, o, sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->stream));
+    o += sizeof(int32_t) * N;
+    CK(cudaMemcpyAsync(c->own_prev, o, sizeof(int32_t) * N, cudaMemcpyHostToDevice, c->stream));
+    o += sizeof(int32_t) * N;
+    CK(cudaMemcpyAsync(c->d_win, o, 16 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    for (size_t k = 0; k < acc.size(); ++k) {
+        const unsigned char* b = base + at[k];
+        CK(cudaMemcpyAsync(c->d_state[0] + k, b, sizeof(BodyState), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->d_state[1] + k, b + sizeof(BodyState), sizeof(BodyState), cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->d_acc + k, b + 2 * sizeof(BodyState), sizeof(BodyAcc), cudaMemcpyHostToDevice,
+                           c->stream));
+        const size_t nl = (size_t)acc[k].link_count;
+        if (nl)
+            CK(cudaMemcpyAsync(c->d_links + c->par[k].link_off, b + 2 * sizeof(BodyState) + sizeof(BodyAcc),
+                               sizeof(uint32_t) * nl, cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));  // the caller's buffer may go once we return
+    c->step = h.step;
+    c->pending = false;
+    drop_graph(c);
+    return LB_OK;
+}
+
 }  // extern "C"

@@ -100,6 +100,9 @@ SIGNATURES = {
     "lb_get_stresslet": (C.c_int, [_CTX, C.c_int32, _DP]),
     "lb_get_mass": (C.c_int, [_CTX, _DP, _DP]),
     "lb_get_links": (C.c_int, [_CTX, C.c_int32, _LP, C.c_int64, _LP]),
+    "lb_checkpoint_size": (C.c_int, [_CTX, C.POINTER(C.c_size_t)]),
+    "lb_checkpoint": (C.c_int, [_CTX, C.c_void_p, C.c_size_t]),
+    "lb_restore": (C.c_int, [_CTX, C.c_void_p, C.c_size_t]),
     "lb_last_error": (C.c_char_p, [_CTX]),
     "lb_kernel_launches": (C.c_int64, [_CTX]),
     "lb_set_sweep_variant": (C.c_int, [_CTX, C.c_int32]),
@@ -279,6 +282,19 @@ def lb_get_links(ctx, oid: int = 0) -> np.ndarray:
         _check(ctx, load().lb_get_links(ctx, int(oid), out.ctypes.data_as(_LP), cnt.value,
                                         C.byref(cnt)), "lb_get_links")
     return out
+
+
+def lb_checkpoint(ctx) -> bytes:
+    n = C.c_size_t()
+    _check(ctx, load().lb_checkpoint_size(ctx, C.byref(n)), "lb_checkpoint_size")
+    buf = C.create_string_buffer(n.value)
+    _check(ctx, load().lb_checkpoint(ctx, buf, n.value), "lb_checkpoint")
+    return buf.raw
+
+
+def lb_restore(ctx, blob: bytes) -> None:
+    buf = C.create_string_buffer(bytes(blob), len(blob))
+    _check(ctx, load().lb_restore(ctx, buf, len(blob)), "lb_restore")
 
 
 def lb_last_error(ctx) -> str:
@@ -565,6 +581,14 @@ class Lattice:
 
     def links(self, oid=0):
         return lb_get_links(self.ctx, oid)
+
+    def checkpoint(self):
+        """The run so far as bytes (see lb_checkpoint)."""
+        return lb_checkpoint(self.ctx)
+
+    def restore(self, blob):
+        """Continue from a checkpoint of a lattice set up the same way."""
+        lb_restore(self.ctx, blob)
 
     def set_sweep_variant(self, variant):
         lb_set_sweep_variant(self.ctx, variant)
