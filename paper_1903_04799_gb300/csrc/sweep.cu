@@ -20,13 +20,13 @@ __global__ void __launch_bounds__(256) k_sweep(const SweepArgs a) {
     sweep_one<S, P>(a, x, y, z);
 }
 
-template <int S, int P>
+template <int S, int P, bool O32>
 __global__ void __launch_bounds__(256, 2) k_sweep2(const SweepArgs a) {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int z = sweep_plane(a);
     const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
     if (x0 >= a.nx || y < 0) return;
-    sweep_two<S, P>(a, x0, y, z);
+    sweep_two<S, P, O32>(a, x0, y, z);
 }
 
 // 16-bit storages: the packed two-cell form, three blocks per SM.
@@ -180,8 +180,13 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy
             }
             SweepArgs b = a;
             b.pf = prefetch_ahead(a, S, grid);
-            if (parity == 0) k_sweep2<S, 0><<<grid, block, 0, st>>>(b);
-            else k_sweep2<S, 1><<<grid, block, 0, st>>>(b);
+            if (19 * a.Np < (int64_t(1) << 32)) {  // element offsets fit 32 bits
+                if (parity == 0) k_sweep2<S, 0, true><<<grid, block, 0, st>>>(b);
+                else k_sweep2<S, 1, true><<<grid, block, 0, st>>>(b);
+            } else {
+                if (parity == 0) k_sweep2<S, 0, false><<<grid, block, 0, st>>>(b);
+                else k_sweep2<S, 1, false><<<grid, block, 0, st>>>(b);
+            }
             return;
         }
     }
