@@ -80,13 +80,13 @@ __global__ void __launch_bounds__(256, 2) k_sweep2z(const SweepArgs a, int slots
 // 16-bit storages with nx % 4 == 0, nx <= 768: blocks of whole rows, four
 // cells per thread (see sweep_four_rows); dynamic shared memory of
 // 10 x rows x nx elements on odd steps.
-template <int S, int P>
+template <int S, int P, bool O32>
 __global__ void __launch_bounds__(P == 0 ? 256 : 192, 2) k_sweep4r(const SweepArgs a) {
     extern __shared__ unsigned short rowbuf[];
     const int z = sweep_plane(a);
     if (z < 0) return;  // the whole block
     const int y = sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
-    sweep_four_rows<S, P>(a, y < 0 ? 0 : y, z, y >= 0, rowbuf);
+    sweep_four_rows<S, P, O32>(a, y < 0 ? 0 : y, z, y >= 0, rowbuf);
 }
 
 static int sm_count() {
@@ -143,11 +143,14 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy
             // odd steps (more live values) in blocks of at most 192 threads
             const int tx = a.nx / 4, ty = (parity == 0 ? 256 : 192) / tx > 0 ? (parity == 0 ? 256 : 192) / tx : 1;
             dim3 block(tx, ty), grid(1, (gy + ty - 1) / ty, gz);
+            const bool o32 = 19 * a.Np < (int64_t(1) << 32);  // element offsets fit 32 bits
             if (parity == 0) {
-                k_sweep4r<S, 0><<<grid, block, 0, st>>>(a);
+                if (o32) k_sweep4r<S, 0, true><<<grid, block, 0, st>>>(a);
+                else k_sweep4r<S, 0, false><<<grid, block, 0, st>>>(a);
             } else {
                 const size_t smem = (size_t)10 * ty * a.nx * sizeof(unsigned short);
-                k_sweep4r<S, 1><<<grid, block, smem, st>>>(a);
+                if (o32) k_sweep4r<S, 1, true><<<grid, block, smem, st>>>(a);
+                else k_sweep4r<S, 1, false><<<grid, block, smem, st>>>(a);
             }
             return;
         }

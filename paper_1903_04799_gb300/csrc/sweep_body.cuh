@@ -654,16 +654,18 @@ __device__ __forceinline__ void sweep_four(const SweepArgs& a, int x0, int y, in
 // write the shifted results there and store the aligned chunks.  `buf` holds
 // 10 x blockDim.y x nx elements.  All threads of the block take part in the
 // barriers (`active`: the thread's row exists).
-template <int S, int P>
+// O32: element offsets in 32-bit arithmetic (the launch checks 19 Np < 2^32).
+template <int S, int P, bool O32 = false>
 __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z, bool active, unsigned short* buf) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x0 = 4 * threadIdx.x;
     const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y >= ny - 1 ? 0 : y + 1};
     const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
     unsigned short* F = (unsigned short*)a.F;
-    const int64_t Np = a.Np;
+    using Off = typename std::conditional<O32, uint32_t, int64_t>::type;
+    const Off Np = (Off)a.Np;
     const float rho0 = (float)a.rho0 * a.scale;  // scaled units (see kScaled)
-    auto row = [&](int dy, int dz) -> int64_t { return (int64_t)nx * (ys[1 + dy] + (int64_t)ny * zs[1 + dz]); };
+    auto row = [&](int dy, int dz) -> Off { return (Off)nx * ((Off)ys[1 + dy] + (Off)ny * (Off)zs[1 + dz]); };
     unsigned short* rowbuf = buf + (int64_t)threadIdx.y * nx;  // + d * blockDim.y * nx for shifted direction d
     const int dstride = blockDim.y * nx;
     auto at = [&](int x) -> int { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
@@ -672,9 +674,9 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (P == 0) {
-            if (active) g[i] = ld_stream(reinterpret_cast<const uint2*>(F + (int64_t)i * Np + row(0, 0) + x0));
+            if (active) g[i] = ld_stream(reinterpret_cast<const uint2*>(F + ((Off)i * Np + row(0, 0) + (Off)x0)));
         } else {
-            const unsigned short* base = F + (int64_t)opp(i) * Np + row(-cy(i), -cz(i));
+            const unsigned short* base = F + ((Off)opp(i) * Np + row(-cy(i), -cz(i)));
             if (cx(i) == 0) {
                 if (active) g[i] = ld_stream(reinterpret_cast<const uint2*>(base + x0));
             } else {
@@ -722,9 +724,9 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
     for (int i = 0; i < Q; ++i) {
         const uint2 o = g[i];
         if (P == 0) {
-            if (active) st_stream(reinterpret_cast<uint2*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0), o);
+            if (active) st_stream(reinterpret_cast<uint2*>(F + ((Off)opp(i) * Np + row(0, 0) + (Off)x0)), o);
         } else if (cx(i) == 0) {
-            if (active) st_stream(reinterpret_cast<uint2*>(F + (int64_t)i * Np + row(cy(i), cz(i)) + x0), o);
+            if (active) st_stream(reinterpret_cast<uint2*>(F + ((Off)i * Np + row(cy(i), cz(i)) + (Off)x0)), o);
         } else {
             // targets x0 + 1 .. x0 + 4 (c_x = +1) or x0 - 1 .. x0 + 2 (c_x = -1)
             unsigned short* r = rowbuf + d * dstride;
@@ -745,7 +747,7 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
             const unsigned short* r = rowbuf + d * dstride;
             ++d;
             if (active)
-                st_stream(reinterpret_cast<uint2*>(F + (int64_t)i * Np + row(cy(i), cz(i)) + x0),
+                st_stream(reinterpret_cast<uint2*>(F + ((Off)i * Np + row(cy(i), cz(i)) + (Off)x0)),
                           *reinterpret_cast<const uint2*>(r + x0));
         }
     }
