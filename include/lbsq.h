@@ -133,7 +133,12 @@ lb_status lb_add_squirmer(lb_ctx* c, const double pos[3], const double e[3], dou
  *   kind 1, square tube along z: params = {} -- plane walls at x = 0,
  *           x = nx-1, y = 0, y = ny-1 (four ids; *id receives the first);
  *   kind 2, fixed sphere obstacle: params = {x, y, z, radius} -- a body that
- *           never moves and has no slip (Sec. V B obstacle).
+ *           never moves and has no slip (Sec. V B obstacle);
+ *   kind 3, round tube along z: params = {cx, cy, r} -- every node with
+ *           (x - cx)^2 + (y - cy)^2 >= r^2 (in FP64) is a wall at rest, for
+ *           the paper's tube flow (Sec. V; r > 1, the axis inside the box).
+ *           Squirmers meet it in the contact force (lb_set_contact) at the
+ *           surface r - 1/2 from the axis.
  * Errors: LB_ERR_INVALID, LB_ERR_OVERLAP. */
 lb_status lb_add_wall(lb_ctx* c, int32_t kind, const double* params, int32_t nparams, int32_t* id);
 

@@ -192,7 +192,8 @@ typedef struct {
     double R, B1, B2, mass, inertia;
     double pos[3], vel[3], omega[3], e[3];
     double wall_vel[3];        /* plane walls: velocity of the wall */
-    int wall_axis, wall_index; /* plane walls */
+    int wall_axis, wall_index; /* plane walls; wall_axis -1: a round tube */
+    double tube_c[2], tube_r;  /* round tube along z: axis (x, y) and radius */
     double Fbb[3], Tbb[3], Sbb[6];
     double Fc[3], Tc[3];             /* conversion force booked for the next update */
     double Fapplied[3], Tapplied[3]; /* hydrodynamic force/torque of the last update */
@@ -409,6 +410,43 @@ int32_t osim_add_plane_wall(osim* s, int32_t axis, int32_t index, const double* 
     return id;
 }
 
+/* Whether node (x, y) lies in the solid of a round tube along z with axis
+ * (cx, cy) and radius r: (x - cx)^2 + (y - cy)^2 >= r^2, evaluated in FP64 as
+ * written (no contraction). */
+static int tube_solid(int x, int y, double cx, double cy, double r) {
+    const double dx = (double)x - cx, dy = (double)y - cy;
+    return dx * dx + dy * dy >= r * r;
+}
+
+/* Round tube along z (the paper's tube flow, Sec. V): every node at distance
+ * >= r from the axis (cx, cy) is a wall at rest, bounced back like a plane
+ * wall.  Returns the object id, -OERR_OVERLAP if a sphere holds such a node. */
+int32_t osim_add_tube(osim* s, double cx, double cy, double r) {
+    if (!(r > 1.0) || !(cx >= 0.0) || !(cy >= 0.0) || !(cx <= s->nx - 1) || !(cy <= s->ny - 1)) return -OERR_INVALID;
+    for (long c = 0; c < s->N; ++c) {
+        int x, y, z;
+        coords(s, c, &x, &y, &z);
+        if (tube_solid(x, y, cx, cy, r) && s->owner[c] != 0 && s->obj[s->owner[c] - 1].kind == OBJ_SPHERE)
+            return -OERR_OVERLAP;
+    }
+    oobj* o = new_object(s);
+    o->kind = OBJ_WALL;
+    o->wall_axis = -1;
+    o->wall_index = 0;
+    o->tube_c[0] = cx;
+    o->tube_c[1] = cy;
+    o->tube_r = r;
+    for (int k = 0; k < 3; ++k) o->wall_vel[k] = 0.0;
+    int id = s->nobj + 1;
+    for (long c = 0; c < s->N; ++c) {
+        int x, y, z;
+        coords(s, c, &x, &y, &z);
+        if (tube_solid(x, y, cx, cy, r) && s->owner[c] == 0) s->owner[c] = id;
+    }
+    s->nobj++;
+    return id;
+}
+
 /* Boundary velocity of object o on the link from fluid node (x,y,z) along c_i,
  * taken at the link midpoint (x,y,z) + c_i/2: walls move rigidly; spheres:
  * v + omega x d (Eq. "vb") plus the squirmer slip (Eq. "squirmer"), with d the
@@ -460,6 +498,17 @@ static void contact_force(const osim* s, int a, double* F) {
             double f = oracle_wca(dist - oa->R - ob->R, s->wca_sigma, s->wca_eps);
             if (f != 0.0)
                 for (int k = 0; k < 3; ++k) F[k] += f * d[k] / dist;
+        } else if (ob->wall_axis < 0) {
+            /* round tube: its surface taken half a cell inside the first solid
+             * radius, as for a plane wall; the force points to the axis */
+            double dx = oa->pos[0] - ob->tube_c[0], dy = oa->pos[1] - ob->tube_c[1];
+            double rho = sqrt(dx * dx + dy * dy);
+            double gap = (ob->tube_r - 0.5) - rho - oa->R;
+            double f = oracle_wca(gap, s->wca_sigma, s->wca_eps);
+            if (f != 0.0 && rho > 0.0) {
+                F[0] -= f * dx / rho;
+                F[1] -= f * dy / rho;
+            }
         } else {
             int ax = ob->wall_axis;
             double dd = min_image(oa->pos[ax] - (double)ob->wall_index, n[ax]);

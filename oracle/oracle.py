@@ -68,6 +68,7 @@ def load_oracle():
             "osim_error": (C.c_int32, [C.c_void_p]),
             "osim_step_count": (C.c_int64, [C.c_void_p]),
             "osim_set_body_force": (None, [C.c_void_p, _DP]),
+            "osim_add_tube": (C.c_int32, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
             "osim_set_contact": (None, [C.c_void_p, C.c_double, C.c_double]),
             "osim_set_equilibrium": (None, [C.c_void_p, _DP, _DP]),
             "osim_set_populations": (None, [C.c_void_p, _DP]),
@@ -210,6 +211,14 @@ class OracleSim:
         rc = self._lib.osim_add_plane_wall(self._h, axis, index, vp)
         if rc < 0:
             raise ValueError(f"add_plane_wall failed ({-rc})")
+        return int(rc)
+
+    def add_tube(self, cx: float, cy: float, r: float):
+        """Round tube along z: nodes at distance >= r from the axis (cx, cy) are
+        a wall at rest (the paper's tube flow, Sec. V)."""
+        rc = self._lib.osim_add_tube(self._h, float(cx), float(cy), float(r))
+        if rc < 0:
+            raise ValueError(f"add_tube failed ({-rc})")
         return int(rc)
 
     def set_body_force(self, g):

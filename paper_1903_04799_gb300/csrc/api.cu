@@ -34,6 +34,9 @@ void launch_sphere_overlap(const Lattice& L, const int32_t* own, const double* p
 void launch_plane_overlap(const Lattice& L, const int32_t* own, const int* kind, int axis, int index, int* count,
                           cudaStream_t st);
 void launch_plane_claim(const Lattice& L, int32_t* own, int axis, int index, int id, cudaStream_t st);
+void launch_tube_overlap(const Lattice& L, const int32_t* own, const int* kind, const BodyParams& q, int* count,
+                         cudaStream_t st);
+void launch_tube_claim(const Lattice& L, int32_t* own, const BodyParams& q, int id, cudaStream_t st);
 void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, cudaStream_t st);
 }  // namespace lbsq
 
@@ -499,6 +502,48 @@ lb_status new_body(lb_ctx* c, const BodyParams& bp, const BodyState& st, int kin
     return LB_OK;
 }
 
+// Round tube along z (lb_add_wall kind 3).
+lb_status add_round_tube(lb_ctx* c, const double* params, int32_t nparams, int32_t* id) {
+    if (!params || nparams != 3) return fail(c, LB_ERR_INVALID, "round tube needs cx, cy, radius");
+    const double cx = params[0], cy = params[1], r = params[2];
+    if (!(r > 1.0) || !(cx >= 0.0) || !(cy >= 0.0) || !(cx <= c->L.nx - 1) || !(cy <= c->L.ny - 1))
+        return fail(c, LB_ERR_INVALID, "round tube: radius > 1 and the axis inside the box");
+    BodyParams bp{};
+    bp.kind = BODY_WALL;
+    bp.mobile = 0;
+    bp.wall_axis = -1;
+    bp.tube[0] = cx;
+    bp.tube[1] = cy;
+    bp.tube[2] = r;
+    CK(cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream));
+    if (!c->par.empty()) {
+        launch_tube_overlap(c->L, c->own, c->d_kind, bp, c->d_count, c->stream);
+        c->launches += 1;
+    }
+    int hcount = 0;
+    CK(cudaMemcpyAsync(&hcount, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hcount != 0) return fail(c, LB_ERR_OVERLAP, "the tube overlaps a sphere");
+    // links: the fluid nodes next to the solid, about 10 per unit of
+    // circumference and plane at most
+    bp.link_cap = (int64_t)(10.0 * (6.2832 * r + 16.0)) * c->L.nz + 64;
+    bp.box_w[0] = c->L.nx;
+    bp.box_w[1] = c->L.ny;
+    bp.box_w[2] = c->L.nz;
+    BodyState st{};  // a tube has no position, velocity or orientation of its own
+    int32_t nid = 0;
+    lb_status s = new_body(c, bp, st, BODY_WALL, &nid);
+    if (s != LB_OK) return s;
+    launch_tube_claim(c->L, c->own, bp, nid, c->stream);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    s = relayout(c);
+    if (s == LB_OK) s = relink_all(c);
+    if (s != LB_OK) return s;
+    *id = nid;
+    return LB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -706,6 +751,7 @@ lb_status lb_add_wall(lb_ctx* c, int32_t kind, const double* params, int32_t npa
         const double e[3] = {0.0, 0.0, 1.0};
         return lb_add_squirmer(c, params, e, params[3], 0.0, 0.0, 0, 1.0, id);
     }
+    if (kind == 3) return add_round_tube(c, params, nparams, id);
     if (kind == 1) {
         // square tube along z: plane walls x = 0, x = nx-1, y = 0, y = ny-1
         const double walls[4][2] = {{0, 0}, {0, (double)(n3[0] - 1)}, {1, 0}, {1, (double)(n3[1] - 1)}};
@@ -1267,6 +1313,7 @@ uint64_t bodies_hash(const lb_ctx* c) {
         mix(q.wall_vel, sizeof(q.wall_vel));
         mix(&q.wall_axis, sizeof(q.wall_axis));
         mix(&q.wall_index, sizeof(q.wall_index));
+        mix(q.tube, sizeof(q.tube));
     }
     mix(&c->wca_sigma, sizeof(double));
     mix(&c->wca_eps, sizeof(double));

@@ -320,6 +320,16 @@ __device__ __noinline__ void wca_sum(const Lattice& L, const Bodies& B, int k, c
             const double f = wca_force(dist - p.R - q.R, L.wca_sigma, L.wca_eps);
             if (f != 0.0)
                 for (int b = 0; b < 3; ++b) fw[b] += f * dd[b] / dist;
+        } else if (q.wall_axis < 0) {
+            // round tube: its surface half a cell inside the first solid
+            // radius, as for a plane wall; the force points to the axis
+            const double dx = s.pos[0] - q.tube[0], dy = s.pos[1] - q.tube[1];
+            const double rho = sqrt(dx * dx + dy * dy);
+            const double f = wca_force((q.tube[2] - 0.5) - rho - p.R, L.wca_sigma, L.wca_eps);
+            if (f != 0.0 && rho > 0.0) {
+                fw[0] -= f * dx / rho;
+                fw[1] -= f * dy / rho;
+            }
         } else {
             const int ax = q.wall_axis;
             const double dd = min_image(s.pos[ax] - (double)q.wall_index, n3[ax]);

@@ -246,7 +246,8 @@ struct BodyParams {
     int kind, mobile;
     double R, B1, B2, mass, inertia;
     double wall_vel[3];
-    int wall_axis, wall_index;
+    int wall_axis, wall_index;  // plane walls; wall_axis -1: a round tube along z
+    double tube[3];             // round tube: axis (x, y) and radius
     int64_t link_off;  // first slot of this body's link segment
     int64_t link_cap;  // capacity of the segment
     int box_w[3];      // scan box extent (spheres: W = ceil(2R)+6 per axis)
@@ -348,12 +349,23 @@ __device__ __forceinline__ void body_box(const Lattice& L, const BodyParams& p, 
             lo[a] = 0;
             w[a] = n[a];
         }
-        // a plane wall's links come from the two layers next to it
-        lo[p.wall_axis] = p.wall_index - 1;
-        w[p.wall_axis] = n[p.wall_axis] < 3 ? n[p.wall_axis] : 3;
+        // a plane wall's links come from the two layers next to it (a round
+        // tube's from anywhere in the lattice)
+        if (p.wall_axis >= 0) {
+            lo[p.wall_axis] = p.wall_index - 1;
+            w[p.wall_axis] = n[p.wall_axis] < 3 ? n[p.wall_axis] : 3;
+        }
     }
 }
 
 __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+// Whether node (x, y) lies in the solid of the round tube q (wall_axis -1):
+// (x - cx)^2 + (y - cy)^2 >= r^2 in FP64, every operation rounded as written
+// (no contraction), so that the oracle's evaluation gives the same answer.
+__device__ __forceinline__ bool tube_solid(const BodyParams& q, int x, int y) {
+    const double dx = __dsub_rn((double)x, q.tube[0]), dy = __dsub_rn((double)y, q.tube[1]);
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) >= __dmul_rn(q.tube[2], q.tube[2]);
+}
 
 }  // namespace lbsq

@@ -160,6 +160,24 @@ __global__ void k_plane_claim(const Lattice L, int32_t* own, int axis, int index
     if (c[axis] == index && own[n] == 0) own[n] = id;
 }
 
+// A round tube along z (BodyParams::tube): solid nodes already held by a
+// sphere, counted; free solid nodes claimed for body `id`.
+__global__ void k_tube_overlap(const Lattice L, const int32_t* own, const int* kind, const BodyParams q, int* count) {
+    int64_t n;
+    int c[3];
+    if (!grid_cell(L, n, c[0], c[1], c[2])) return;
+    if (!tube_solid(q, c[0], c[1])) return;
+    const int o = own[n];
+    if (o != 0 && kind[o - 1] == BODY_SPHERE) atomicAdd(count, 1);
+}
+
+__global__ void k_tube_claim(const Lattice L, int32_t* own, const BodyParams q, int id) {
+    int64_t n;
+    int c[3];
+    if (!grid_cell(L, n, c[0], c[1], c[2])) return;
+    if (tube_solid(q, c[0], c[1]) && own[n] == 0) own[n] = id;
+}
+
 // Work flag for set-up passes: body k (or all if k < 0) re-classifies (and
 // its node margin restarts) or not.
 __global__ void k_set_flags(BodyAcc* acc, int nb, int k, int reclass) {
@@ -201,6 +219,13 @@ void launch_plane_overlap(const Lattice& L, const int32_t* own, const int* kind,
 }
 void launch_plane_claim(const Lattice& L, int32_t* own, int axis, int index, int id, cudaStream_t st) {
     k_plane_claim<<<grid_for(L.N), kB, 0, st>>>(L, own, axis, index, id);
+}
+void launch_tube_overlap(const Lattice& L, const int32_t* own, const int* kind, const BodyParams& q, int* count,
+                         cudaStream_t st) {
+    k_tube_overlap<<<grid_for(L.N), kB, 0, st>>>(L, own, kind, q, count);
+}
+void launch_tube_claim(const Lattice& L, int32_t* own, const BodyParams& q, int id, cudaStream_t st) {
+    k_tube_claim<<<grid_for(L.N), kB, 0, st>>>(L, own, q, id);
 }
 void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, cudaStream_t st) {
     k_set_flags<<<(nb + kB - 1) / kB, kB, 0, st>>>(acc, nb, k, reclass);

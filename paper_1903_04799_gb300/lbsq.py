@@ -533,6 +533,11 @@ class Lattice:
     def add_obstacle(self, pos, radius):
         return lb_add_wall(self.ctx, 2, [*pos, radius])
 
+    def add_round_tube(self, cx, cy, radius):
+        """Round tube along z: nodes at distance >= radius from (cx, cy) are a
+        wall at rest (lb_add_wall kind 3)."""
+        return lb_add_wall(self.ctx, 3, [cx, cy, radius])
+
     def set_contact(self, sigma, eps):
         lb_set_contact(self.ctx, sigma, eps)
 

@@ -218,6 +218,27 @@ def test_walls_couette_and_tube():
         _compare_bodies(g, o, [gs, gob], [os_, oob])
 
 
+def test_round_tube_swimmer_f64():
+    """Sec. V tube flow: a squirmer swimming toward the wall of a round tube
+    (lb_add_wall kind 3), with the contact force on (Eq. "wca"), which it
+    reaches after about 100 steps.  Owners and link sets bit-exact; fields,
+    body state, and the squirmer's and the tube's force, torque and stresslet
+    within 1e-12 of the oracle."""
+    shape = (24, 24, 28)
+    g, o = make_pair(shape, "trt", 1.0)
+    tg = g.add_round_tube(11.5, 11.5, 10.0)
+    to = o.add_tube(11.5, 11.5, 10.0)
+    args = ((16.4, 12.1, 13.7), (0.8, 0.3, 0.5), 3.0, 0.012, -2.0)
+    gi = g.add_squirmer(*args, mobile=True)
+    oi = o.add_sphere(*args, mobile=True)
+    g.set_contact(1.0, 0.05)
+    o.set_contact(1.0, 0.05)
+    for _ in range(4):
+        g.step(40)
+        o.step(40)
+        _compare_bodies(g, o, [gi, tg], [oi, to], R=10.0)
+
+
 def test_two_swimmers_f64():
     shape = (40, 24, 24)
     g, o = make_pair(shape, "trt", 1.0)

@@ -428,3 +428,65 @@ def test_wca_force_is_minus_gradient_and_cut():
     assert O.wca(rc, sig, eps) == 0.0
     assert abs(O.wca(rc - 1e-9, sig, eps)) < 1e-6
     assert U(rc) == pytest.approx(0.0, abs=1e-15)
+
+
+# --------------------------------------------------------------- Sec. V: round tube
+
+def test_round_tube_poiseuille():
+    """Sec. V tube flow geometry: a round tube along z (nodes at distance >= r
+    from the axis are wall), driven by a test-only body force.  Pins:
+      * the node set and the flow are mirror-symmetric (x -> 19 - x, x <-> y
+        for an axis at (9.5, 9.5)), so the steady velocity is too, to
+        roundoff: a wrong index or sign in the tube or its links breaks it;
+      * momentum balance at steady state: the force on the tube equals the
+        body force fed to the fluid, g per fluid node and step;
+      * Hagen-Poiseuille, u = g (a^2 - rho^2) / (4 nu): half-way bounce-back
+        puts the wall at the midpoint of each fluid-to-solid link, and a link
+        (at most sqrt 2 long) that crosses radius r has its midpoint within
+        sqrt(2)/2 of r, so the centre speed lies between the values for
+        a = r -/+ sqrt(2)/2."""
+    n, r, g, le = 20, 8.0, 1e-6, 1.0
+    s = O.OracleSim(n, n, 4, lambda_e=le, collision="trt", magic=3 / 16)
+    tid = s.add_tube(9.5, 9.5, r)
+    own = s.owner().reshape(4, n, n)
+    x = np.arange(n)
+    d2 = (x[None, :] - 9.5) ** 2 + (x[:, None] - 9.5) ** 2
+    assert ((own[0] != 0) == (d2 >= r * r)).all()
+    s.set_body_force([0.0, 0.0, g])
+    s.step(6000)
+    rho, u = s.fields()
+    rho, uz = rho.reshape(4, n, n)[1], u[2].reshape(4, n, n)[1]
+    fluid = own[1] == 0  # wall nodes report rho = 0
+    uz = np.where(fluid, (uz * rho + g / 2) / np.where(fluid, rho, 1.0), 0.0)
+    scale = np.abs(uz).max()
+    assert np.abs(uz - uz[:, ::-1]).max() <= 1e-12 * scale
+    assert np.abs(uz - uz.T).max() <= 1e-12 * scale
+    F, _ = s.force_torque(tid)
+    nfluid = int((own == 0).sum())
+    assert F[2] == pytest.approx(g * nfluid, rel=1e-9)
+    # no transverse force: a cancelling sum of link terms, so its roundoff
+    # scales with their gross momentum flux 2 w_i rho0 |c_i|
+    d = s.links(tid) % 32
+    flux = float((2 * np.where(d < 7, 1 / 18, 1 / 36) * np.where(d < 7, 1.0, np.sqrt(2.0))).sum())
+    assert abs(F[0]) < 1e-13 * flux and abs(F[1]) < 1e-13 * flux
+    nu = (1 / le - 0.5) / 3
+    centre = uz[9, 9]  # rho^2 = 0.5 from the axis
+    h = math.sqrt(2.0) / 2
+    lo = g * ((r - h) ** 2 - 0.5) / (4 * nu)
+    hi = g * ((r + h) ** 2 - 0.5) / (4 * nu)
+    assert lo < centre < hi
+
+
+def test_round_tube_contact_points_to_the_axis():
+    """Eq. "wca" against the round tube: a passive sphere at rest in fluid at
+    rest, closer to the tube's surface than the cut-off, is pushed toward the
+    axis; on the mirror line y = cy the push has no y part."""
+    n = 24
+    s = O.OracleSim(n, n, 16, lambda_e=1.0, collision="trt")
+    s.add_tube(11.5, 11.5, 10.0)
+    sid = s.add_sphere((17.3, 11.5, 8.0), (0.0, 0.0, 1.0), 3.0, 0.0, 0.0, mobile=True)
+    s.set_contact(1.0, 0.01)
+    s.step(1)
+    _, v, _, _ = s.state(sid)
+    assert v[0] < 0.0
+    assert abs(v[1]) <= 1e-12 * abs(v[0])
