@@ -455,3 +455,31 @@ def test_c2_full_size_parity(storage, tol):
     _, uo = o.fields()
     assert rel(ug, uo) < tol
     assert np.abs(g.state(gi)[1] - o.state(oi)[1]).max() < tol * np.abs(o.state(oi)[1]).max()
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5), ("f16dev", 2e-2)])
+def test_c3_full_size_parity(storage, tol):
+    """The 256^3 pusher (R = 16, beta = -3) at full size, in the launch
+    configuration bench.py times for each storage (split near/far steps; for
+    FP16 the alternating four-cell and two-cell sweeps): 12 steps against the
+    oracle, whole fields.  Reduced-storage tolerances as in the small free
+    swimmer test; the body velocity is compared relative to its own size."""
+    wl = W.c3_pusher()
+    b = wl.bodies[0]
+    g = Lattice(wl.shape, collision="trt", storage=storage)
+    o = OracleSim(*wl.shape, lambda_e=1.0, collision="trt")
+    # off-node start, tilted axis and a larger B1 so that cells change
+    pos, e = (128.4, 127.7, 128.2), (0.1, -0.2, 1.0)
+    gi = g.add_squirmer(pos, e, b.R, 0.05, b.beta, mobile=True)
+    oi = o.add_sphere(pos, e, b.R, 0.05, b.beta, mobile=True)
+    g.step(12)
+    o.step(12)
+    og, oo = g.owner(), o.owner()
+    if storage != "f16dev":
+        assert (og == oo).all()
+    _, ug = g.fields()
+    _, uo = o.fields()
+    both = (og == 0) & (oo == 0)
+    assert rel(ug[:, both], uo[:, both]) < tol
+    vg, vo = g.state(gi)[1], o.state(oi)[1]
+    assert np.abs(vg - vo).max() < tol * np.abs(vo).max()
