@@ -61,7 +61,7 @@ typedef enum {
     LB_ERR_OOM = 2,      /* device allocation failed */
     LB_ERR_CUDA = 3,     /* a CUDA runtime call failed (message in lb_last_error) */
     LB_ERR_OVERLAP = 4,  /* a body overlaps another body or a wall */
-    LB_ERR_DIVERGED = 5, /* a body reached |v| >= 1/2 (the scheme needs |v| << 1) */
+    LB_ERR_DIVERGED = 5, /* a body reached |v| >= 1/2 (the scheme needs |v| << 1); it is held in place */
     LB_ERR_TIMEOUT = 6,  /* a bounded device wait ran out */
     LB_ERR_STATE = 7,    /* the context holds an earlier device error */
     LB_ERR_CAPACITY = 8  /* a boundary-link list outgrew its capacity */

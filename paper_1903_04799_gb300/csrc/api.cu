@@ -412,26 +412,35 @@ lb_status relayout(lb_ctx* c) {
                        c->stream));
     lb_status s = upload_lattice(c);
     if (s != LB_OK) return s;
-    // near-body window: upper bounds of its z and y lengths from the box
-    // sizes (a z-normal wall spans every row); the split pays only when the
-    // window leaves most of the planes outside
-    int wmax = 0, ymax = 0;
+    // near-body window: upper bounds of its z and y lengths, which size the
+    // near sweep's grid.  The window is one periodic box around every body's
+    // range (near_window), so with one body it is that body's range; with
+    // several it also spans the gaps between them and may be any length up
+    // to the whole lattice.  The split pays only when the summed ranges leave
+    // most of the planes outside (a z-normal wall spans every row).
+    int wmax = 0, ymax = 0, ranges = 0;
     bool across = false;
     for (auto& b : c->par) {
         if (b.kind == BODY_SPHERE) {
             wmax += b.box_w[2] + 5;
             ymax += b.box_w[1] + 5;
+            ++ranges;
         } else if (b.wall_axis == 2) {
             wmax += 3 + 5;
             ymax += c->L.ny;
+            ++ranges;
         } else {
             across = true;
         }
     }
+    c->split = !across && nb > 0 && wmax * 5 < 3 * c->L.nz;
+    if (ranges > 1) {
+        wmax = c->L.nz;
+        ymax = c->L.ny;
+    }
     c->win_max = std::min(wmax, c->L.nz);
     // the device takes every row once the extent may reach 3/5 of them
     c->ywin_max = ymax * 5 < 3 * c->L.ny ? ymax : c->L.ny;
-    c->split = !across && nb > 0 && wmax * 5 < 3 * c->L.nz;
     // whole lattice until the first rebuild
     int win_init[16];
     for (int k = 0; k < 4; ++k) {

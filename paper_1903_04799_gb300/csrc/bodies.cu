@@ -399,9 +399,20 @@ __device__ __noinline__ void update_body(const Lattice& L, const Bodies& B, int 
         }
         v = v + (Fa + Fw) * p.inv_mass;
         w = w + Ta * p.inv_inertia;
-        x = x + v;
-        if (x >= (double)n3[a]) x -= (double)n3[a];
-        else if (x < 0.0) x += (double)n3[a];
+        const double sp = sum3(v * v);
+        // The geometry of the next step (node-crossing stencils, the near
+        // window) assumes a move of under half a cell.  A body at |v| >= 1/2
+        // (or NaN) has left the scheme: the error is flagged and the body
+        // stays where it is, so no later kernel indexes outside its tables.
+        const bool ok = sp < 0.25;
+        if (ok) {
+            x = x + v;
+            if (x >= (double)n3[a]) x -= (double)n3[a];
+            else if (x < 0.0) x += (double)n3[a];
+        } else {
+            v = 0.0;
+            w = 0.0;
+        }
         // Rotation of e about w by the angle th = |w| (Rodrigues), renormalised:
         //   e' = e cos(th) + (w x e) sin(th)/th + w (w.e) (1 - cos(th))/th^2.
         // A body turns by far less than 0.01 rad per step, where the Taylor
@@ -427,7 +438,7 @@ __device__ __noinline__ void update_body(const Lattice& L, const Bodies& B, int 
             const double inr = fabs(n2 - 1.0) < 1e-8 ? 1.5 - 0.5 * n2 : inv_sqrt(n2);
             e = r * inr;
         }
-        const double ve = sum3(v * e), sp = sum3(v * v);
+        const double ve = sum3(v * e);
         const double dd = min_image(x - rc, n3[a]);
         const double disp2 = sum3(dd * dd);
         __syncwarp();
@@ -435,7 +446,7 @@ __device__ __noinline__ void update_body(const Lattice& L, const Bodies& B, int 
         if (lane == 0) {
             A.vesum = ves + ve;
             A.nsum = ns + 1;
-            if (!(sp < 0.25)) set_error(L.err, 5);
+            if (!ok) set_error(L.err, 5);
         }
         // Node crossing test: every node of the box kept its side of the surface
         // if the centre moved less than the distance of the nearest node to the

@@ -98,6 +98,21 @@ def c4_suspension(n: int = 256, count: int = 200, R: float = 6.0, min_dist: floa
     return Workload(f"c4_suspension_{n}_{count}", (n, n, n), "trt", 1.0, steps, bodies)
 
 
+def two_squirmers_passing(d: float = 27.0, n: int = 250, R: float = 9.0, beta: float = 5.0,
+                          B1: float = 0.003, steps: int = 60000) -> Workload:
+    """Two pullers (beta = 5, R = 9) in a 250^3 periodic box, facing each other
+    12R apart along z with lateral offset d along y: centres
+    (c, c + d/2, c - 6R) with e = +z and (c, c - d/2, c + 6R) with e = -z,
+    c = n/2.  The pair is symmetric under the half turn about the x axis
+    through (c, c), which maps the lattice onto itself.  B1 = 0.003 gives
+    v0 = 0.002 and a Reynolds number 2 v0 R / nu of 0.22; 60 000 steps carry
+    each sphere about 120 lattice units, past the other."""
+    c = n / 2.0
+    return Workload(f"two_squirmers_passing_{n}_d{d:g}", (n, n, n), "trt", 1.0, steps,
+                    [Body((c, c + d / 2, c - 6 * R), (0.0, 0.0, 1.0), R, B1, beta, True),
+                     Body((c, c - d / 2, c + 6 * R), (0.0, 0.0, -1.0), R, B1, beta, True)])
+
+
 def smooth_fields(shape, seed: int, drho: float = 0.01, umax: float = 0.02):
     """Smooth periodic random density and velocity fields (x-fastest, flattened):
     rho = 1 + drho * (sum of a few low Fourier modes), u likewise."""

@@ -356,6 +356,54 @@ def test_near_window_split_bitwise(storage, variant):
             assert np.array_equal(x, y)
 
 
+def _far_apart(g):
+    # two isolated spheres 65 planes apart: the window spans the gap
+    return [g.add_squirmer((48.3, 30.2, 40.1), (0.2, 0.1, 1.0), 5.0, 0.05, -3.0, mobile=True),
+            g.add_squirmer((47.6, 70.4, 105.3), (-0.1, 0.2, -1.0), 5.0, 0.05, 4.0, mobile=True)]
+
+
+def _close_pair(g):
+    # two spheres 3.9 cells apart (the multi-kernel body path), swimming apart
+    return [g.add_squirmer((48.3, 48.2, 60.1), (0.0, 0.1, -1.0), 5.0, 0.05, -3.0, mobile=True),
+            g.add_squirmer((48.1, 48.4, 74.0), (0.1, 0.0, 1.0), 5.0, 0.05, 2.0, mobile=True)]
+
+
+def _sphere_and_z_wall(g):
+    # a z-normal wall at z = 0 and a sphere 60 planes away: the window spans
+    # every row and the planes between them
+    ids = [g.add_squirmer((48.3, 47.7, 62.2), (0.3, 0.2, 1.0), 5.0, 0.05, -2.0, mobile=True)]
+    g.add_plane_wall(2, 0)
+    return ids
+
+
+@pytest.mark.parametrize("bodies", [_far_apart, _close_pair, _sphere_and_z_wall])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev"])
+def test_near_window_split_several_bodies_bitwise(bodies, storage):
+    """Split steps with more than one body, against whole-lattice sweeps: the
+    window is one box around every body's range, so it also spans the gap
+    between them and can be far longer than any one body's range.  The same
+    bits for every population, owner and body state."""
+    shape = (96, 96, 160)
+    runs = []
+    for traced in (False, True):
+        g = Lattice(shape, collision="trt", storage=storage)
+        ids = bodies(g)
+        if traced:
+            g.profile_begin()
+        for n in (5, 16, 3, 9, 1, 8, 8):
+            g.step(n)
+        if traced:
+            g.profile_end()
+        runs.append((g.populations(), g.owner(), [g.state(i) for i in ids]))
+        g.close()
+    (fa, oa, sa), (fb, ob, sb) = runs
+    assert (oa == ob).all()
+    assert np.array_equal(fa, fb)
+    for u, v in zip(sa, sb):
+        for x, y in zip(u, v):
+            assert np.array_equal(x, y)
+
+
 # ------------------------------------------------------------------ reduced storage
 
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16dev", 2e-2), ("bf16dev", 3e-1)])
