@@ -148,6 +148,17 @@ lb_status lb_add_wall(lb_ctx* c, int32_t kind, const double* params, int32_t npa
  * clamped below at 0.05 sigma).  eps = 0 (default) switches it off. */
 lb_status lb_set_contact(lb_ctx* c, double sigma, double eps);
 
+/* Ladd's two-step force average (Sec. III): with on = 1, every body's update
+ * applies (F_bb(t) + F_bb(t-1)) / 2 and (T_bb(t) + T_bb(t-1)) / 2 instead of
+ * this step's momentum exchange, F_bb(t-1) = 0 before a body's first step;
+ * the conversion force is not averaged.  The paper leaves the average off
+ * (on = 0, the default) and names it a remedy for forces that oscillate
+ * between consecutive steps.  The fluid still gives up F_bb(t) each step, so
+ * fluid plus body momentum plus F_bb(t)/2 is what stays constant.
+ * lb_get_force_torque reports the force that entered the update.
+ * Errors: LB_ERR_INVALID (on not 0 or 1). */
+lb_status lb_set_force_average(lb_ctx* c, int32_t on);
+
 /* Set every cell's populations to the equilibrium of host fields rho[N] and
  * u[3][N] (SoA, x-fastest).  Solid cells are overwritten too (harmless). */
 lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u);
@@ -233,7 +244,8 @@ lb_status lb_get_links(lb_ctx* c, int32_t id, int64_t* out, int64_t cap, int64_t
  *
  * lb_restore loads a checkpoint into a context set up the same way: the
  * same lb_params and the same bodies, added in the same order (their
- * positions may differ: the checkpoint's replace them).  Stepping it then
+ * positions may differ: the checkpoint's replace them), and the same
+ * lb_set_contact and lb_set_force_average settings (not checked).  Stepping it then
  * gives the bits the checkpointed context would have given.  The caller's
  * buffer is not kept.  The format is that of this build of the library
  * (host byte order, the library's structure layouts).

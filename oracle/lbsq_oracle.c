@@ -197,6 +197,7 @@ typedef struct {
     double Fbb[3], Tbb[3], Sbb[6];
     double Fc[3], Tc[3];             /* conversion force booked for the next update */
     double Fapplied[3], Tapplied[3]; /* hydrodynamic force/torque of the last update */
+    double Fbb_last[3], Tbb_last[3]; /* F_bb, T_bb of the previous step (two-step average) */
 } oobj;
 
 typedef struct {
@@ -210,6 +211,7 @@ typedef struct {
     int32_t* owner_prev;
     double g[3]; /* test-only body force, 0 on the method's path */
     double wca_sigma, wca_eps;
+    int force_avg; /* 1: Ladd's two-step average of F_bb and T_bb */
     int nobj, capobj;
     oobj* obj; /* obj[k] has id k+1 */
     long step;
@@ -301,6 +303,12 @@ void osim_set_contact(osim* s, double sigma, double eps) {
     s->wca_sigma = sigma;
     s->wca_eps = eps;
 }
+
+/* Ladd's coupling averages the momentum exchange over two consecutive steps;
+ * Sec. III names the option and leaves it off.  on = 1: every update applies
+ * (F_bb(t) + F_bb(t-1)) / 2 and the same for T_bb, with F_bb(t-1) = 0 before
+ * an object's first step. */
+void osim_set_force_average(osim* s, int on) { s->force_avg = on ? 1 : 0; }
 
 /* Populations to the equilibrium of the given fields (rho[N], u as SoA [3][N]). */
 void osim_set_equilibrium(osim* s, const double* rho, const double* u) {
@@ -628,8 +636,15 @@ static void integrate(osim* s) {
     for (int k = 0; k < s->nobj; ++k) {
         oobj* o = &s->obj[k];
         for (int a = 0; a < 3; ++a) {
-            o->Fapplied[a] = o->Fbb[a] + o->Fc[a];
-            o->Tapplied[a] = o->Tbb[a] + o->Tc[a];
+            double Fh = o->Fbb[a], Th = o->Tbb[a];
+            if (s->force_avg) {
+                Fh = 0.5 * (o->Fbb[a] + o->Fbb_last[a]);
+                Th = 0.5 * (o->Tbb[a] + o->Tbb_last[a]);
+            }
+            o->Fbb_last[a] = o->Fbb[a];
+            o->Tbb_last[a] = o->Tbb[a];
+            o->Fapplied[a] = Fh + o->Fc[a];
+            o->Tapplied[a] = Th + o->Tc[a];
             o->Fc[a] = 0.0;
             o->Tc[a] = 0.0;
         }

@@ -70,6 +70,7 @@ def load_oracle():
             "osim_set_body_force": (None, [C.c_void_p, _DP]),
             "osim_add_tube": (C.c_int32, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
             "osim_set_contact": (None, [C.c_void_p, C.c_double, C.c_double]),
+            "osim_set_force_average": (None, [C.c_void_p, C.c_int32]),
             "osim_set_equilibrium": (None, [C.c_void_p, _DP, _DP]),
             "osim_set_populations": (None, [C.c_void_p, _DP]),
             "osim_get_populations": (None, [C.c_void_p, _DP]),
@@ -227,6 +228,9 @@ class OracleSim:
 
     def set_contact(self, sigma: float, eps: float):
         self._lib.osim_set_contact(self._h, sigma, eps)
+
+    def set_force_average(self, on: bool = True):
+        self._lib.osim_set_force_average(self._h, 1 if on else 0)
 
     def set_equilibrium(self, rho, u):
         rho, rp = _d(np.reshape(rho, -1))

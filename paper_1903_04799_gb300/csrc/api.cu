@@ -84,6 +84,7 @@ struct lb_ctx {
     int n_sm = 152;
     Lattice* d_lat = nullptr;  // the one lattice descriptor on the device
     double wca_sigma = 1.0, wca_eps = 0.0;
+    int force_avg = 0;  // lb_set_force_average
     // scratch
     double* d_mass_part = nullptr;
     double* d_small = nullptr;  // 8 doubles
@@ -226,6 +227,7 @@ lb_status upload_lattice(lb_ctx* c) {
     L.lambda_o = c->lambda_o;
     L.wca_sigma = c->wca_sigma;
     L.wca_eps = c->wca_eps;
+    L.force_avg = c->force_avg;
     L.body_begin = 0;
     L.body_count = (int)c->par.size();
     L.active = 1;
@@ -820,6 +822,18 @@ lb_status lb_set_contact(lb_ctx* c, double sigma, double eps) {
     c->wca_eps = eps;
     drop_graph(c);
     CK(cudaSetDevice(c->p.device));
+    lb_status s = upload_lattice(c);
+    if (s != LB_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_set_force_average(lb_ctx* c, int32_t on) {
+    if (!c || (on != 0 && on != 1)) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
+    c->force_avg = on;
+    drop_graph(c);
     lb_status s = upload_lattice(c);
     if (s != LB_OK) return s;
     CK(cudaStreamSynchronize(c->stream));

@@ -370,7 +370,13 @@ __device__ __noinline__ void update_body(const Lattice& L, const Bodies& B, int 
     const int a = lane < 3 ? lane : 0;  // lanes >= 3 shadow component 0 and store nothing
     const bool own = lane < 3;
     BodyAcc& A = *Ao;
-    const double Fa = tot[a] + Ai.Fc[a], Ta = tot[3 + a] + Ai.Tc[a];
+    // Ladd's coupling averages the momentum exchange over this step and the
+    // last (Sec. III names the option; the paper's runs leave it off).  Ai.Fbb
+    // and Ai.Tbb still hold the last step's values here (0 before a body's
+    // first step).
+    const double Fh = L.force_avg ? 0.5 * (tot[a] + Ai.Fbb[a]) : tot[a];
+    const double Th = L.force_avg ? 0.5 * (tot[3 + a] + Ai.Tbb[a]) : tot[3 + a];
+    const double Fa = Fh + Ai.Fc[a], Ta = Th + Ai.Tc[a];
     const double rc = Ai.r_class[a], vs = Ai.vsum[a], ves = Ai.vesum;
     const long long ns = Ai.nsum;
     const unsigned long long mbits = Ai.margin_bits;

@@ -86,6 +86,7 @@ SIGNATURES = {
                                   C.c_double, _IP]),
     "lb_add_wall": (C.c_int, [_CTX, C.c_int32, _DP, C.c_int32, _IP]),
     "lb_set_contact": (C.c_int, [_CTX, C.c_double, C.c_double]),
+    "lb_set_force_average": (C.c_int, [_CTX, C.c_int32]),
     "lb_set_fields": (C.c_int, [_CTX, _DP, _DP]),
     "lb_set_populations": (C.c_int, [_CTX, _DP]),
     "lb_get_populations": (C.c_int, [_CTX, _DP]),
@@ -199,6 +200,10 @@ def lb_add_wall(ctx, kind: int, params=()) -> int:
 
 def lb_set_contact(ctx, sigma: float, eps: float):
     _check(ctx, load().lb_set_contact(ctx, float(sigma), float(eps)), "lb_set_contact")
+
+
+def lb_set_force_average(ctx, on: bool):
+    _check(ctx, load().lb_set_force_average(ctx, int(bool(on))), "lb_set_force_average")
 
 
 def lb_set_fields(ctx, rho, u):
@@ -540,6 +545,9 @@ class Lattice:
 
     def set_contact(self, sigma, eps):
         lb_set_contact(self.ctx, sigma, eps)
+
+    def set_force_average(self, on=True):
+        lb_set_force_average(self.ctx, on)
 
     def set_fields(self, rho, u):
         lb_set_fields(self.ctx, np.reshape(rho, -1), np.reshape(u, (3, -1)))

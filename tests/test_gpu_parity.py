@@ -252,6 +252,34 @@ def test_two_swimmers_f64():
         _compare_bodies(g, o, gids, oids)
 
 
+@pytest.mark.parametrize("setup", ["free", "split", "pair"])
+def test_force_average_f64(setup):
+    """Ladd's two-step force average (lb_set_force_average) against the
+    oracle's: fields, links, forces and body states within 1e-12, on the
+    single-sphere fused path, on split steps (a sphere in a large box, across
+    the periodic faces) and on the multi-kernel path of two spheres near each
+    other; checked after every block of steps."""
+    if setup == "free":
+        shape, bodies, blocks = (28, 26, 30), [((13.3, 12.7, 14.1), (0.3, -0.4, 1.0), 4.5, 0.03, -2.0)], (7, 30)
+    elif setup == "split":
+        shape, bodies, blocks = (128, 96, 96), [((64.3, 2.7, 94.1), (0.3, 0.5, 1.0), 6.0, 0.05, -3.0)], (5, 16, 9)
+    else:
+        shape = (40, 24, 24)
+        # 1.5 cells apart, swimming apart
+        bodies = [((15.2, 12.1, 11.8), (-1.0, 0.1, 0.0), 4.0, 0.03, -3.0),
+                  ((24.7, 11.6, 12.3), (1.0, 0.05, 0.1), 4.0, 0.03, 3.0)]
+        blocks = (9, 20)
+    g, o = make_pair(shape, "trt", 1.0)
+    g.set_force_average(True)
+    o.set_force_average(True)
+    gids = [g.add_squirmer(*b, mobile=True) for b in bodies]
+    oids = [o.add_sphere(*b, mobile=True) for b in bodies]
+    for n in blocks:
+        g.step(n)
+        o.step(n)
+        _compare_bodies(g, o, gids, oids, R=bodies[0][2])
+
+
 def _random_spheres(rng, shape, count, R, min_dist):
     """`count` sphere centres by random sequential addition (minimum-image
     distance >= min_dist), random unit axes, beta ~ U[-4, 4]."""

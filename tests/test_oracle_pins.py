@@ -363,6 +363,36 @@ def test_momentum_balance_free_swimmer():
     assert changed > 0
 
 
+def test_two_step_force_average_momentum_invariant():
+    """Sec. III, Ladd's two-step average (named, not used, by the paper): the
+    body receives (F_bb(t) + F_bb(t-1)) / 2 while the fluid gives up F_bb(t),
+    so the imbalance telescopes and fluid + body momentum + booked conversion
+    force + F_bb(t)/2 stays zero (F_bb(-1) = 0).  F_bb(t) is recovered from
+    the force that entered each update, F_app(t) = (F_bb(t) + F_bb(t-1)) / 2
+    + Fc(t-1).  A missing 1/2, an average that is not applied, or one that
+    uses the wrong step breaks the balance."""
+    n = 20
+    s = O.OracleSim(n, n, n, lambda_e=1.0, collision="trt")
+    s.set_force_average(True)
+    oid = s.add_sphere((9.7, 10.2, 10.1), (0.3, 0.2, 1.0), 4.0, B1=0.02, beta=-3.0, mobile=True)
+    M = 4 / 3 * math.pi * 4 ** 3
+    F_last = np.zeros(3)
+    Fc_last = np.zeros(3)
+    worst = 0.0
+    for _ in range(200):
+        s.step(1)
+        F_app, _ = s.force_torque(oid)
+        F_bb = 2 * (F_app - Fc_last) - F_last
+        _, P = fluid_totals(s)
+        _, v, _, _ = s.state(oid)
+        Fc, _ = s.pending_conversion(oid)
+        np.testing.assert_allclose(P + M * v + Fc + F_bb / 2, 0.0, rtol=0, atol=1e-11)
+        worst = max(worst, float(np.abs(P + M * v + Fc).max()))
+        F_last, Fc_last = F_bb, Fc
+    # the unaveraged balance does not hold here: the term F_bb/2 is real
+    assert worst > 1e-6
+
+
 def test_swim_speed_matches_fig_resolution():
     """Eq. "squirmer-speed" and Fig. "resolution": a free squirmer of R = 4 in a
     periodic box L = 10R swims at the speed the paper prints, 0.9737 v0
