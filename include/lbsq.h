@@ -75,6 +75,15 @@ typedef enum { LB_BGK = 0, LB_TRT = 1 } lb_collision;
  * the Newton-Euler update are FP64 for every storage. */
 typedef enum { LB_F64 = 0, LB_F32 = 1, LB_F16DEV = 2, LB_BF16DEV = 3 } lb_storage;
 
+/* Equilibrium (Sec. III).  LB_EQ_COMPRESSIBLE: f_i^eq = w_i rho (1 + 3 c.u +
+ * 9/2 (c.u)^2 - 3/2 u.u) with u = j / rho, the reading of the paper used for
+ * every result here.  LB_EQ_INCOMPRESSIBLE: the model in which the printed
+ * u = sum f_i c_i holds as written (for rho0 = 1), f_i^eq = w_i (rho + rho0
+ * (3 c.u + 9/2 (c.u)^2 - 3/2 u.u)) with u = j / rho0; it applies to the
+ * collision, the refill of uncovered cells, lb_set_fields and the exported
+ * velocity. */
+typedef enum { LB_EQ_COMPRESSIBLE = 0, LB_EQ_INCOMPRESSIBLE = 1 } lb_equilibrium;
+
 /* Optional device allocator (for example a caching allocator of the host
  * framework).  alloc returns a device pointer of at least `bytes` bytes on
  * the context's device, or NULL; free receives the same pointer and size. */
@@ -99,10 +108,12 @@ typedef struct {
     int32_t device;      /* CUDA device ordinal */
     void* stream;        /* cudaStream_t to run on; NULL = a stream the context creates */
     const lb_allocator* allocator; /* NULL = cudaMalloc / cudaFree */
+    int32_t equilibrium; /* lb_equilibrium */
 } lb_params;
 
 /* Fill *p with: 32^3, BGK, lambda_e = 1, magic = 3/16, rho0 = 1, FP64,
- * default FP16 scale, device 0, own stream, cudaMalloc. */
+ * default FP16 scale, device 0, own stream, cudaMalloc, compressible
+ * equilibrium. */
 void lb_params_default(lb_params* p);
 
 /* Create a lattice with every population at rest equilibrium w_i rho0 and

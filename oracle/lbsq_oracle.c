@@ -109,6 +109,17 @@ void oracle_feq(double rho, const double* u, double* feq) {
     }
 }
 
+/* Incompressible equilibrium (He and Luo), the model in which Sec. III's
+ * printed velocity u = sum f_i c_i holds as written (with rho0 = 1):
+ * f_i^eq = w_i (rho + rho0 (3 c.u + 9/2 (c.u)^2 - 3/2 u.u)), u = j / rho0. */
+void oracle_feq_inc(double rho, double rho0, const double* u, double* feq) {
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < Q; ++i) {
+        double cu = CX[i] * u[0] + CY[i] * u[1] + CZ[i] * u[2];
+        feq[i] = WT[i] * (rho + rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+    }
+}
+
 /* Moments (Sec. III): rho = sum f_i, j = sum f_i c_i, u = j / rho. */
 void oracle_moments(const double* f, double* rho, double* j) {
     double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
@@ -138,6 +149,24 @@ void oracle_collide(const double* f, double lambda_e, double lambda_o, double* f
     u[1] = j[1] / rho;
     u[2] = j[2] / rho;
     oracle_feq(rho, u, feq);
+    for (int i = 0; i < Q; ++i) {
+        int ib = opposite(i);
+        double fp = 0.5 * (f[i] + f[ib]);
+        double fm = 0.5 * (f[i] - f[ib]);
+        double ep = 0.5 * (feq[i] + feq[ib]);
+        double em = 0.5 * (feq[i] - feq[ib]);
+        fpost[i] = f[i] - lambda_e * (fp - ep) - lambda_o * (fm - em);
+    }
+}
+
+/* TRT collision of one cell towards the incompressible equilibrium, u = j / rho0. */
+void oracle_collide_inc(const double* f, double lambda_e, double lambda_o, double rho0, double* fpost) {
+    double rho, j[3], u[3], feq[Q];
+    oracle_moments(f, &rho, j);
+    u[0] = j[0] / rho0;
+    u[1] = j[1] / rho0;
+    u[2] = j[2] / rho0;
+    oracle_feq_inc(rho, rho0, u, feq);
     for (int i = 0; i < Q; ++i) {
         int ib = opposite(i);
         double fp = 0.5 * (f[i] + f[ib]);
@@ -212,6 +241,7 @@ typedef struct {
     double g[3]; /* test-only body force, 0 on the method's path */
     double wca_sigma, wca_eps;
     int force_avg; /* 1: Ladd's two-step average of F_bb and T_bb */
+    int inc;       /* 1: incompressible equilibrium (oracle_feq_inc) throughout */
     int nobj, capobj;
     oobj* obj; /* obj[k] has id k+1 */
     long step;
@@ -310,12 +340,17 @@ void osim_set_contact(osim* s, double sigma, double eps) {
  * an object's first step. */
 void osim_set_force_average(osim* s, int on) { s->force_avg = on ? 1 : 0; }
 
+/* Incompressible equilibrium (oracle_feq_inc) in the collision, the refill,
+ * osim_set_equilibrium and the exported velocity u = j / rho0. */
+void osim_set_incompressible(osim* s, int on) { s->inc = on ? 1 : 0; }
+
 /* Populations to the equilibrium of the given fields (rho[N], u as SoA [3][N]). */
 void osim_set_equilibrium(osim* s, const double* rho, const double* u) {
     for (long n = 0; n < s->N; ++n) {
         double uu[3] = {u[n], u[s->N + n], u[2 * s->N + n]};
         double feq[Q];
-        oracle_feq(rho[n], uu, feq);
+        if (s->inc) oracle_feq_inc(rho[n], s->rho0, uu, feq);
+        else oracle_feq(rho[n], uu, feq);
         for (int i = 0; i < Q; ++i) s->f[i * s->N + n] = feq[i];
     }
 }
@@ -537,7 +572,8 @@ static void collide_all(osim* s) {
         if (s->owner[n] != 0) continue;
         double f[Q], fp[Q];
         for (int i = 0; i < Q; ++i) f[i] = s->f[i * N + n];
-        oracle_collide(f, s->lambda_e, s->lambda_o, fp);
+        if (s->inc) oracle_collide_inc(f, s->lambda_e, s->lambda_o, s->rho0, fp);
+        else oracle_collide(f, s->lambda_e, s->lambda_o, fp);
         if (s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0)
             for (int i = 0; i < Q; ++i) fp[i] += 3.0 * WT[i] * (CX[i] * s->g[0] + CY[i] * s->g[1] + CZ[i] * s->g[2]);
         for (int i = 0; i < Q; ++i) s->fpost[i * N + n] = fp[i];
@@ -742,7 +778,8 @@ static void remap(osim* s) {
             cross(o->omega, d, w);
             for (int a = 0; a < 3; ++a) u[a] = o->vel[a] + w[a];
             double feq[Q], m[3] = {0.0, 0.0, 0.0}, t[3];
-            oracle_feq(rb, u, feq);
+            if (s->inc) oracle_feq_inc(rb, s->rho0, u, feq);
+            else oracle_feq(rb, u, feq);
             for (int i = 0; i < Q; ++i) {
                 s->f[i * N + c] = feq[i];
                 m[0] += feq[i] * CX[i];
@@ -785,9 +822,10 @@ void osim_get_fields(const osim* s, double* rho, double* u) {
         }
         if (rho) rho[n] = r;
         if (u) {
-            u[n] = r != 0.0 ? j[0] / r : 0.0;
-            u[N + n] = r != 0.0 ? j[1] / r : 0.0;
-            u[2 * N + n] = r != 0.0 ? j[2] / r : 0.0;
+            const double den = s->inc ? s->rho0 : r; /* u = j / rho0 in the incompressible model */
+            u[n] = r != 0.0 ? j[0] / den : 0.0;
+            u[N + n] = r != 0.0 ? j[1] / den : 0.0;
+            u[2 * N + n] = r != 0.0 ? j[2] / den : 0.0;
         }
     }
 }

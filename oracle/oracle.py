@@ -54,6 +54,8 @@ def load_oracle():
             "oracle_weights": (None, [_DP]),
             "oracle_opposite": (C.c_int32, [C.c_int32]),
             "oracle_feq": (None, [C.c_double, _DP, _DP]),
+            "oracle_feq_inc": (None, [C.c_double, C.c_double, _DP, _DP]),
+            "oracle_collide_inc": (None, [_DP, C.c_double, C.c_double, C.c_double, _DP]),
             "oracle_moments": (None, [_DP, _DP, _DP]),
             "oracle_lambda_odd": (C.c_double, [C.c_double, C.c_double]),
             "oracle_collide": (None, [_DP, C.c_double, C.c_double, _DP]),
@@ -71,6 +73,7 @@ def load_oracle():
             "osim_add_tube": (C.c_int32, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
             "osim_set_contact": (None, [C.c_void_p, C.c_double, C.c_double]),
             "osim_set_force_average": (None, [C.c_void_p, C.c_int32]),
+            "osim_set_incompressible": (None, [C.c_void_p, C.c_int32]),
             "osim_set_equilibrium": (None, [C.c_void_p, _DP, _DP]),
             "osim_set_populations": (None, [C.c_void_p, _DP]),
             "osim_get_populations": (None, [C.c_void_p, _DP]),
@@ -128,6 +131,13 @@ def feq(rho: float, u) -> np.ndarray:
     return out
 
 
+def feq_inc(rho: float, rho0: float, u) -> np.ndarray:
+    u, up = _d(u)
+    out = np.zeros(19)
+    load_oracle().oracle_feq_inc(float(rho), float(rho0), up, out.ctypes.data_as(_DP))
+    return out
+
+
 def moments(f):
     f, fp = _d(f)
     rho = np.zeros(1)
@@ -144,6 +154,13 @@ def collide(f, lambda_e: float, lambda_o: float) -> np.ndarray:
     f, fp = _d(f)
     out = np.zeros(19)
     load_oracle().oracle_collide(fp, lambda_e, lambda_o, out.ctypes.data_as(_DP))
+    return out
+
+
+def collide_inc(f, lambda_e: float, lambda_o: float, rho0: float) -> np.ndarray:
+    f, fp = _d(f)
+    out = np.zeros(19)
+    load_oracle().oracle_collide_inc(fp, lambda_e, lambda_o, float(rho0), out.ctypes.data_as(_DP))
     return out
 
 
@@ -231,6 +248,9 @@ class OracleSim:
 
     def set_force_average(self, on: bool = True):
         self._lib.osim_set_force_average(self._h, 1 if on else 0)
+
+    def set_incompressible(self, on: bool = True):
+        self._lib.osim_set_incompressible(self._h, 1 if on else 0)
 
     def set_equilibrium(self, rho, u):
         rho, rp = _d(np.reshape(rho, -1))

@@ -585,6 +585,7 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     if (p->storage < LB_F64 || p->storage > LB_BF16DEV) return LB_ERR_INVALID;
     if (p->collision == LB_TRT && !(p->magic > 0.0)) return LB_ERR_INVALID;
     if (p->dev_scale_log2 < -1 || p->dev_scale_log2 > 40) return LB_ERR_INVALID;
+    if (p->equilibrium != LB_EQ_COMPRESSIBLE && p->equilibrium != LB_EQ_INCOMPRESSIBLE) return LB_ERR_INVALID;
     lb_ctx* c = new (std::nothrow) lb_ctx();
     if (!c) return LB_ERR_OOM;
     c->p = *p;
@@ -616,6 +617,7 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     L.N = N;
     L.Np = (N + 63) / 64 * 64;
     L.storage = p->storage;
+    L.inc = p->equilibrium == LB_EQ_INCOMPRESSIBLE ? 1 : 0;
     L.rho0 = p->rho0;
     // FP16 deviation scale: 2^14 keeps deviations up to 4 representable and
     // the usual 1e-5 .. 1e-2 in FP16's normal range
@@ -1309,6 +1311,7 @@ struct CkptHeader {
     char magic[8];
     uint32_t version, storage;
     int32_t nx, ny, nz, nbodies;
+    int32_t equilibrium, reserved;
     double lambda_e, lambda_o, rho0;
     double scale;
     int64_t step;
@@ -1389,8 +1392,9 @@ lb_status lb_checkpoint(lb_ctx* c, void* buf, size_t bytes) {
     unsigned char* o = static_cast<unsigned char*>(buf);
     CkptHeader h{};
     std::memcpy(h.magic, kCkptMagic, 8);
-    h.version = 1;
+    h.version = 2;
     h.storage = (uint32_t)c->p.storage;
+    h.equilibrium = c->L.inc;
     h.nx = c->L.nx;
     h.ny = c->L.ny;
     h.nz = c->L.nz;
@@ -1434,11 +1438,11 @@ lb_status lb_restore(lb_ctx* c, const void* buf, size_t bytes) {
     if (!c || !buf || bytes < sizeof(CkptHeader)) return LB_ERR_INVALID;
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) return fail(c, LB_ERR_INVALID, "not a checkpoint");
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 2) return fail(c, LB_ERR_INVALID, "not a checkpoint");
     if (h.bytes != bytes) return fail(c, LB_ERR_INVALID, "checkpoint size differs from its header");
     if (h.storage != (uint32_t)c->p.storage || h.nx != c->L.nx || h.ny != c->L.ny || h.nz != c->L.nz ||
         h.lambda_e != c->lambda_e || h.lambda_o != c->lambda_o || h.rho0 != c->L.rho0 ||
-        h.scale != (double)c->L.scale)
+        h.scale != (double)c->L.scale || h.equilibrium != c->L.inc)
         return fail(c, LB_ERR_INVALID, "checkpoint of a lattice with other parameters");
     if (h.nbodies != (int32_t)c->par.size() || h.bodies_hash != bodies_hash(c))
         return fail(c, LB_ERR_INVALID, "checkpoint of other bodies (add the same bodies in the same order)");

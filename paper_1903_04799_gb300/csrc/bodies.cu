@@ -1001,7 +1001,8 @@ __device__ __noinline__ void refill_finish(const Lattice& L, const BodyState& s,
     double fi = 0.0;
     if (lane < Q) {
         const double cu = cx(lane) * u[0] + cy(lane) * u[1] + cz(lane) * u[2];
-        fi = wgt(lane) * rb * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        fi = L.inc ? wgt(lane) * (rb + L.rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu))
+                   : wgt(lane) * rb * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
         store_abs(L, read_slot(L, lane, x, y, z, q), lane, fi);
     }
     // created momentum sum_l c_l f_l: lane l holds its term (zero beyond Q)

@@ -140,6 +140,8 @@ struct Lattice {
     int body_begin, body_count;  // this lattice's bodies in the body table
     int active;                  // 0: not stepped (a free server slot, or being set up)
     int force_avg;               // 1: F_bb and T_bb averaged over this step and the last (Ladd)
+    int inc;                     // 1: incompressible equilibrium, u = j / rho0 (lb_params.equilibrium)
+    int pad;
     const long long* gstep;      // server: global step counter (null for a context)
     long long stop_step;         // server: the lattice is stepped while *gstep < stop_step
 };

@@ -29,7 +29,8 @@ __global__ void k_fill_rest(const Lattice L) {
     for (int i = 0; i < Q; ++i) store_abs(L, (int64_t)i * L.Np + n, i, wgt(i) * L.rho0);
 }
 
-// Equilibrium of given fields, w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u), into
+// Equilibrium of given fields, w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u)
+// (incompressible: w_i (rho + rho0 (3 c.u + 9/2 (c.u)^2 - 3/2 u.u))), into
 // the read slots of parity q.  rho[N], u[3][N] on the device.
 __global__ void k_set_eq(const Lattice L, const double* rho, const double* u, int q) {
     int64_t n;
@@ -39,7 +40,9 @@ __global__ void k_set_eq(const Lattice L, const double* rho, const double* u, in
     const double uu = ux * ux + uy * uy + uz * uz;
     for (int i = 0; i < Q; ++i) {
         const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        store_abs(L, read_slot(L, i, x, y, z, q), i, wgt(i) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+        const double fe = L.inc ? wgt(i) * (r + L.rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu))
+                                : wgt(i) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        store_abs(L, read_slot(L, i, x, y, z, q), i, fe);
     }
 }
 
@@ -58,7 +61,8 @@ __global__ void k_get_pop(const Lattice L, double* f, int q) {
     for (int i = 0; i < Q; ++i) f[(int64_t)i * L.N + n] = load_abs(L, read_slot(L, i, x, y, z, q), i);
 }
 
-// rho = sum f_i and u = j / rho of fluid cells (Sec. III); 0 in solid cells.
+// rho = sum f_i and u = j / rho of fluid cells (Sec. III; incompressible
+// equilibrium: u = j / rho0); 0 in solid cells.
 __global__ void k_fields(const Lattice L, const int32_t* own, double* rho, double* u, int q) {
     int64_t n;
     int x, y, z;
@@ -75,9 +79,10 @@ __global__ void k_fields(const Lattice L, const int32_t* own, double* rho, doubl
     }
     if (rho) rho[n] = r;
     if (u) {
-        u[n] = r != 0.0 ? jx / r : 0.0;
-        u[L.N + n] = r != 0.0 ? jy / r : 0.0;
-        u[2 * L.N + n] = r != 0.0 ? jz / r : 0.0;
+        const double den = L.inc ? L.rho0 : r;
+        u[n] = r != 0.0 ? jx / den : 0.0;
+        u[L.N + n] = r != 0.0 ? jy / den : 0.0;
+        u[2 * L.N + n] = r != 0.0 ? jz / den : 0.0;
     }
 }
 

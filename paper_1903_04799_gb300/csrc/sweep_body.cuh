@@ -29,6 +29,7 @@ namespace lbsq {
 struct TrtK {
     double d[8];
     float f[8];
+    int inc;  // 1: incompressible equilibrium, u = j / rho0 (the quadratic terms take 1/rho0)
 };
 __host__ __device__ inline TrtK trt_constants(double le, double lo) {
     TrtK k;
@@ -38,6 +39,7 @@ __host__ __device__ inline TrtK trt_constants(double le, double lo) {
         k.d[i] = v[i];
         k.f[i] = (float)v[i];
     }
+    k.inc = 0;
     return k;
 }
 struct SweepArgs {
@@ -169,6 +171,8 @@ __device__ __forceinline__ V pair_dot(int i, V x, V y, V z) {
 //   g_i  += E + O,  g_ib += E - O,
 //   E = le (w_i base + 9/2 w_i (c_i.u)(c_i.j)) - le/2 s,  O = 3 lo w_i c_i.j - lo/2 d,
 // base = rho - 3/2 rho u.u (deviations: rho - rho0 - 3/2 rho u.u), u = j / rho.
+// The incompressible equilibrium (K.inc) is the same with rho0 in place of
+// rho in the quadratic terms: base = rho - 3/2 |j|^2 / rho0, u = j / rho0.
 // DEV: g holds deviations f - w rho0 (rho = rho0 + sum g).
 template <class V> __device__ __forceinline__ const V* trt_k(const TrtK& k);
 template <> __device__ __forceinline__ const double* trt_k<double>(const TrtK& k) { return k.d; }
@@ -190,7 +194,7 @@ __device__ __forceinline__ void collide_trt(V g[Q], const TrtK& K, V rho0) {
     for (int p = 1; p <= 9; ++p) sum = A::add(sum, s[p]);
     const V jx = pair_moment<V, 0>(d), jy = pair_moment<V, 1>(d), jz = pair_moment<V, 2>(d);
     const V rho = DEV ? A::add(rho0, sum) : sum;
-    const V inv = A::rcp(rho);
+    const V inv = A::rcp(K.inc ? rho0 : rho);
     // no velocity vector: rho u.u = |j|^2 / rho and (c.u)(c.j) = (c.j)^2 / rho
     const V ju = A::mul(A::fma(jz, jz, A::fma(jy, jy, A::mul(jx, jx))), inv);  // rho u.u
     const V base = A::fma(A::c(-1.5), ju, DEV ? sum : rho);
@@ -764,6 +768,7 @@ __host__ __device__ inline SweepArgs sweep_args(const Lattice& L, double lambda_
     a.lambda_e = lambda_e;
     a.lambda_o = lambda_o;
     a.K = trt_constants(lambda_e, lambda_o);
+    a.K.inc = L.inc;
     a.rho0 = L.rho0;
     a.scale = L.scale;
     a.inv_scale = L.inv_scale;

@@ -39,7 +39,7 @@ class lb_params(C.Structure):
                 ("collision", C.c_int32), ("lambda_e", C.c_double), ("magic", C.c_double),
                 ("rho0", C.c_double), ("storage", C.c_int32), ("dev_scale_log2", C.c_int32),
                 ("device", C.c_int32), ("stream", C.c_void_p),
-                ("allocator", C.POINTER(lb_allocator))]
+                ("allocator", C.POINTER(lb_allocator)), ("equilibrium", C.c_int32)]
 
 
 class lb_server_params(C.Structure):
@@ -481,11 +481,12 @@ class TorchAllocator:
 
 class Lattice:
     """One lattice context.  ``storage`` in {'f64','f32','f16dev','bf16dev'};
-    ``collision`` in {'bgk','trt'}.  With ``use_torch`` the context runs on a
-    torch stream and takes its device memory from torch's caching allocator."""
+    ``collision`` in {'bgk','trt'}; ``equilibrium`` in {'compressible',
+    'incompressible'}.  With ``use_torch`` the context runs on a torch stream
+    and takes its device memory from torch's caching allocator."""
 
     def __init__(self, shape, collision="bgk", lambda_e=1.0, magic=3.0 / 16.0, rho0=1.0,
-                 storage="f64", device=0, use_torch=True, dev_scale_log2=-1):
+                 storage="f64", device=0, use_torch=True, dev_scale_log2=-1, equilibrium="compressible"):
         nx, ny, nz = (int(v) for v in shape)
         self.shape = (nx, ny, nz)
         self.N = nx * ny * nz
@@ -495,6 +496,9 @@ class Lattice:
         p.lambda_e, p.magic, p.rho0 = float(lambda_e), float(magic), float(rho0)
         p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         p.dev_scale_log2 = int(dev_scale_log2)
+        if equilibrium not in ("compressible", "incompressible"):
+            raise ValueError(f"equilibrium {equilibrium!r}")
+        p.equilibrium = 1 if equilibrium == "incompressible" else 0
         p.device = int(device)
         self._stream = None
         self._alloc = None

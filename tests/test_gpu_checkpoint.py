@@ -87,12 +87,15 @@ def test_restore_rejects_other_setups():
     other_shape = Lattice((28, 26, 32), collision="trt", storage="f32")
     other_shape.add_squirmer((13.3, 12.7, 14.1), (0.3, -0.4, 1.0), 4.5, 0.03, -2.0, mobile=True)
     other_storage, _ = _free_swimmer("f64")
+    other_model = Lattice((28, 26, 30), collision="trt", storage="f32", equilibrium="incompressible")
+    other_model.add_squirmer((13.3, 12.7, 14.1), (0.3, -0.4, 1.0), 4.5, 0.03, -2.0, mobile=True)
     other_body = Lattice((28, 26, 30), collision="trt", storage="f32")
     other_body.add_squirmer((13.3, 12.7, 14.1), (0.3, -0.4, 1.0), 4.0, 0.03, -2.0, mobile=True)
     same, ids = _free_swimmer("f32")
     same.step(2)
     before = _snapshot(same, ids)
-    for g, b in ((other_shape, blob), (other_storage, blob), (other_body, blob), (same, blob[:-8]),
+    for g, b in ((other_shape, blob), (other_storage, blob), (other_model, blob), (other_body, blob),
+                 (same, blob[:-8]),
                  (same, b"not a checkpoint" * 8)):
         with pytest.raises(LBError) as err:
             g.restore(b)
@@ -100,5 +103,5 @@ def test_restore_rejects_other_setups():
     after = _snapshot(same, ids)
     for x, y in zip(after, before):
         assert np.array_equal(np.asarray(x), np.asarray(y))
-    for g in (other_shape, other_storage, other_body, same):
+    for g in (other_shape, other_storage, other_model, other_body, same):
         g.close()

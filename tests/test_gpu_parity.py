@@ -93,6 +93,61 @@ def test_mass_momentum_conserved_f64():
     assert np.abs(j1 - j0).max() < 1e-11
 
 
+@pytest.mark.parametrize("collision,lambda_e", [("trt", 1.0), ("trt", 1.3), ("bgk", 0.8)])
+def test_incompressible_bulk_f64_parity(collision, lambda_e):
+    """The incompressible equilibrium (lb_params.equilibrium) against the
+    oracle's, rho0 = 1.15 so that it differs from the compressible model:
+    lb_set_fields, 1 and 26 steps of collision and streaming, and the
+    exported u = j / rho0, within 1e-14."""
+    shape, rho0 = (45, 19, 23), 1.15
+    g = Lattice(shape, collision=collision, lambda_e=lambda_e, rho0=rho0, equilibrium="incompressible")
+    o = OracleSim(*shape, lambda_e=lambda_e, collision=collision, rho0=rho0)
+    o.set_incompressible(True)
+    rho, u = W.smooth_fields(shape, seed=9, drho=0.03, umax=0.05)
+    g.set_fields(rho0 * rho, u)
+    o.set_equilibrium(rho0 * rho, u)
+    for n in (1, 25):
+        g.step(n)
+        o.step(n)
+        assert np.abs(g.populations() - o.populations()).max() < 1e-14
+        rg, ug = g.fields()
+        ro, uo = o.fields()
+        assert np.abs(rg - ro).max() < 1e-14
+        assert np.abs(ug - uo).max() < 1e-14
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5), ("f16dev", 2e-2)])
+def test_incompressible_free_swimmer(storage, tol):
+    """A free squirmer crossing cells with the incompressible equilibrium
+    (collision, refill of uncovered cells, export), rho0 = 1.2: FP64 within
+    1e-12 of the oracle (fields, links, forces, states); reduced storages
+    within the tolerances of the compressible runs."""
+    shape, rho0 = (28, 26, 30), 1.2
+    g = Lattice(shape, collision="trt", rho0=rho0, storage=storage, equilibrium="incompressible")
+    o = OracleSim(*shape, lambda_e=1.0, collision="trt", rho0=rho0)
+    o.set_incompressible(True)
+    args = ((13.3, 12.7, 14.1), (0.3, -0.4, 1.0), 4.5, 0.03, -2.0)
+    gi = g.add_squirmer(*args, mobile=True, density=rho0)
+    oi = o.add_sphere(*args, mobile=True, density=rho0)
+    changed, prev = 0, o.owner()
+    for _ in range(4):
+        g.step(40)
+        o.step(40)
+        own = o.owner()
+        changed += int((own != prev).sum())
+        prev = own
+        if storage == "f64":
+            _compare_bodies(g, o, [gi], [oi])
+    assert changed > 0
+    if storage != "f64":
+        _, ug = g.fields()
+        _, uo = o.fields()
+        both = (g.owner() == 0) & (o.owner() == 0)
+        assert rel(ug[:, both], uo[:, both]) < tol
+        vg, vo = g.state(gi)[1], o.state(oi)[1]
+        assert np.abs(vg - vo).max() / np.abs(vo).max() < tol
+
+
 # ------------------------------------------------------------------ classification
 
 @pytest.mark.parametrize("pos,R", [((16.0, 16.0, 16.0), 4.0), ((0.0, 31.0, 0.5), 5.0),

@@ -235,6 +235,90 @@ def test_trt_poiseuille_exact_with_magic_3_16(le):
     assert np.abs(vb / exact - 1).max() > 1e-3
 
 
+# ------------------------------------ incompressible equilibrium (He and Luo)
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_incompressible_equilibrium_moments(seed):
+    """The incompressible model, in which Sec. III's printed u = sum f c holds
+    with rho0 = 1: sum f_eq = rho, sum f_eq c = rho0 u, sum f_eq c c =
+    rho/3 I + rho0 u u.  rho0 = 1.3 so that a rho0 dropped or put in place of
+    rho shows."""
+    rng = np.random.default_rng(seed)
+    rho0 = 1.3
+    rho = rho0 * (1.0 + 0.05 * rng.standard_normal())
+    u = 0.05 * rng.standard_normal(3)
+    f = O.feq_inc(rho, rho0, u)
+    c = O.velocities().astype(float)
+    assert abs(f.sum() - rho) < 1e-15
+    np.testing.assert_allclose(f @ c, rho0 * u, rtol=0, atol=1e-16)
+    P = np.einsum("i,ia,ib->ab", f, c, c)
+    np.testing.assert_allclose(P, rho / 3 * np.eye(3) + rho0 * np.outer(u, u), rtol=0, atol=1e-15)
+
+
+def test_incompressible_collision_relaxes_to_its_equilibrium():
+    """The TRT step towards the incompressible equilibrium conserves rho and
+    j, and relaxes the even and odd parts at their own rates around
+    f_eq(rho, j / rho0)."""
+    rng = np.random.default_rng(4)
+    rho0 = 1.2
+    f = rho0 * O.weights() * (1.0 + 0.3 * rng.random(19))
+    le, lo = 0.8, 1.7
+    g = O.collide_inc(f, le, lo, rho0)
+    rho, j = O.moments(f)
+    r1, j1 = O.moments(g)
+    assert abs(r1 - rho) < 1e-14
+    np.testing.assert_allclose(j1, j, rtol=0, atol=1e-15)
+    e = O.feq_inc(rho, rho0, j / rho0)
+    for i in range(19):
+        k = O.opposite(i)
+        fp, fm = (f[i] + f[k]) / 2, (f[i] - f[k]) / 2
+        gp, gm = (g[i] + g[k]) / 2, (g[i] - g[k]) / 2
+        ep, em = (e[i] + e[k]) / 2, (e[i] - e[k]) / 2
+        assert abs((gp - ep) - (1 - le) * (fp - ep)) < 1e-15
+        assert abs((gm - em) - (1 - lo) * (fm - em)) < 1e-15
+
+
+def test_incompressible_uniform_state_is_a_fixed_point():
+    """A uniform state (rho != rho0, u) set through the simulation's own
+    equilibrium stays put under its step and reads back as (rho, u): the
+    collision relaxes towards the incompressible equilibrium and the export is
+    u = j / rho0.  The compressible equilibrium in either place moves it (it
+    differs from the incompressible one by w (rho - rho0)(3 c.u + ...))."""
+    n, rho0 = 6, 1.1
+    s = O.OracleSim(n, n, n, lambda_e=1.0, collision="trt", rho0=rho0)
+    s.set_incompressible(True)
+    N = n ** 3
+    rho = np.full(N, 1.04)
+    u = np.tile(np.array([[0.03], [-0.02], [0.01]]), (1, N))
+    s.set_equilibrium(rho, u)
+    f0 = s.populations()
+    s.step(3)
+    np.testing.assert_allclose(s.populations(), f0, rtol=0, atol=1e-15)
+    r, v = s.fields()
+    np.testing.assert_allclose(r, rho, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(v, u, rtol=0, atol=1e-15)
+
+
+def test_incompressible_poiseuille_exact_and_velocity_is_j_over_rho0():
+    """The magic-parameter Poiseuille channel (see above) with the
+    incompressible equilibrium: the same exact parabola, read from the
+    exported velocity u = j / rho0 (rho0 = 1.25; the compressible export j /
+    rho would be off by the density ratio)."""
+    ny, g, le, rho0 = 18, 1e-6, 1.0, 1.25
+    s = O.OracleSim(1, ny, 1, lambda_e=le, collision="trt", magic=3 / 16, rho0=rho0)
+    s.set_incompressible(True)
+    s.add_plane_wall(1, 0)
+    s.add_plane_wall(1, ny - 1)
+    s.set_body_force([g, 0, 0])
+    s.step(40000)
+    _, u = s.fields()
+    nu = (1 / le - 0.5) / 3
+    y = np.arange(1, ny - 1)
+    exact = g / (2 * nu) * (y - 0.5) * (ny - 1.5 - y) / rho0
+    vel = u[0][1:-1] + g / (2 * rho0)
+    np.testing.assert_allclose(vel, exact, rtol=1e-8)
+
+
 # --------------------------------------------------------------- Sec. II: squirmer
 
 def test_slip_closed_form_in_spherical_coordinates():
