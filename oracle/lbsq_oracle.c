@@ -55,6 +55,13 @@
  *     D3Q19 neighbours that are fluid now and were fluid before the remap;
  *   - mass M = density * 4/3 pi R^3, I = 2/5 M R^2, dt = 1, velocity first;
  *   - WCA force is -dU/dr of the shifted LJ potential, r the surface gap.
+ *
+ * Parity unpinned (no pin other than agreement with the CUDA library):
+ *   - the refill density (mean over the previously fluid neighbours) beyond
+ *     the exact momentum balance it takes part in;
+ *   - the trajectories of a squirmer in a tube or near an obstacle (the
+ *     boundary-element data the paper compares with are not in its text);
+ *     the drag of a fixed sphere and the flow of the round tube are pinned.
  */
 #include <math.h>
 #include <stdint.h>
