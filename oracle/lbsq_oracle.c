@@ -57,8 +57,6 @@
  *   - WCA force is -dU/dr of the shifted LJ potential, r the surface gap.
  *
  * Parity unpinned (no pin other than agreement with the CUDA library):
- *   - the refill density (mean over the previously fluid neighbours) beyond
- *     the exact momentum balance it takes part in;
  *   - the trajectories of a squirmer in a tube or near an obstacle (the
  *     boundary-element data the paper compares with are not in its text);
  *     the drag of a fixed sphere and the flow of the round tube are pinned.

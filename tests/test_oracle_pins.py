@@ -425,6 +425,51 @@ def test_momentum_balance_fixed_body():
     assert np.abs(acc).max() > 1e-3
 
 
+def test_refill_is_equilibrium_at_neighbour_mean_density():
+    """Sec. III (Aidun's rule): a cell that a moving sphere uncovers is set to
+    the equilibrium at the average density of the surrounding fluid and the
+    body's velocity there.  Read here as: the mean density of the D3Q19
+    neighbours that are fluid now and were fluid before the step, and the
+    rigid velocity v + omega x d at the cell (d from the new centre).  The
+    remap leaves every other fluid cell as streamed, so the rule can be
+    checked from the state after the step: each uncovered cell against the
+    textbook equilibrium w rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u) of those
+    numbers.  A neighbour set, a mean, a velocity or a centre taken otherwise
+    fails."""
+    n = 20
+    s = O.OracleSim(n, n, n, lambda_e=1.0, collision="trt")
+    oid = s.add_sphere((9.7, 10.2, 10.1), (0.3, 0.2, 1.0), 4.0, B1=0.05, beta=-3.0, mobile=True)
+    c = O.velocities().astype(float)
+    w = O.weights()
+    idx = np.arange(n ** 3)
+    xyz = np.stack([idx % n, (idx // n) % n, idx // (n * n)])
+    checked = 0
+    before = s.owner()
+    for _ in range(120):
+        s.step(1)
+        now = s.owner()
+        new = np.nonzero((before == oid) & (now == 0))[0]
+        if len(new):
+            f = s.populations()
+            rho = f.sum(axis=0)
+            p, v, _, om = s.state(oid)
+            for cell in new:
+                x = xyz[:, cell]
+                nb = [int(((x[0] + c[i, 0]) % n) + n * (((x[1] + c[i, 1]) % n) + n * ((x[2] + c[i, 2]) % n)))
+                      for i in range(1, 19)]
+                ok = [m for m in nb if now[m] == 0 and before[m] == 0]
+                rb = np.mean(rho[ok]) if ok else 1.0
+                d = x - p
+                d -= n * np.round(d / n)
+                u = v + np.cross(om, d)
+                cu = c @ u
+                feq = w * rb * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (u @ u))
+                np.testing.assert_allclose(f[:, cell], feq, rtol=0, atol=1e-15)
+                checked += 1
+        before = now
+    assert checked >= 10
+
+
 def test_momentum_balance_free_swimmer():
     """Sec. III: with conversion forces (Eq. "consforce") and momentum exchange
     the total momentum fluid + body (+ booked conversion force) is conserved
