@@ -25,6 +25,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -291,20 +292,65 @@ def serve_run(torch, device=0, n=256, budget=24 << 30, load=0.8):
             "round_steps": 64, "hbm_budget_gb": budget / 2**30}
 
 
-def cpu_baseline(wl, budget_s=15.0):
-    """The oracle as it stands, on the host cores, a bounded sample of the workload."""
+def host_cpu() -> str:
+    """The host CPU's model as the kernel reports it, with the core count."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part") and not model:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return f"{platform.machine()} {model} x{os.cpu_count()}".replace("  ", " ")
+
+
+def fluid_fraction(wl) -> float:
+    """Fraction of the workload's cells that are fluid at the start: nodes
+    strictly inside a sphere, (dx^2 + dy^2) + dz^2 < R^2 with minimum-image
+    offsets, are solid.  A pure host count (the same rule the library and the
+    oracle classify by)."""
+    n3 = np.array(wl.shape)
+    solid = 0
+    for b in wl.bodies:
+        lo = [int(np.floor(b.pos[a] - b.R)) for a in range(3)]
+        hi = [int(np.ceil(b.pos[a] + b.R)) for a in range(3)]
+        axes = [np.arange(lo[a], hi[a] + 1) for a in range(3)]
+        d = [((ax - b.pos[a]) + n3[a] / 2) % n3[a] - n3[a] / 2 for a, ax in enumerate(axes)]
+        dx, dy, dz = np.meshgrid(d[0], d[1], d[2], indexing="ij")
+        solid += int(((dx * dx + dy * dy) + dz * dz < b.R * b.R).sum())
+    return 1.0 - solid / wl.cells
+
+
+def cpu_baseline(wl, budget_s=15.0, single_budget_s=8.0):
+    """The oracle as it stands, on the host cores, a bounded sample of the
+    workload; then the same on one core."""
     from oracle import oracle as O
     s = O.OracleSim(*wl.shape, lambda_e=wl.lambda_e, collision=wl.collision)
     for b in wl.bodies:
         s.add_sphere(b.pos, b.e, b.R, b.B1, b.beta, b.mobile)
     s.step(1)
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s and n < 10000:
-        s.step(1)
-        n += 1
-    t = time.perf_counter() - t0
-    return {"value": wl.cells * n / t / 1e6, "unit": "MLUPS", "cores": O.num_threads(),
-            "kind": "oracle", "sample": f"{n} full time steps of {wl.name} after 1 warm-up step"}
+
+    def timed(budget):
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget and n < 10000:
+            s.step(1)
+            n += 1
+        return n, time.perf_counter() - t0
+
+    cores = O.num_threads()
+    n, t = timed(budget_s)
+    O.set_num_threads(1)
+    try:
+        n1, t1 = timed(single_budget_s)
+    finally:
+        O.set_num_threads(cores)
+    return {"value": wl.cells * n / t / 1e6, "unit": "MLUPS", "cores": cores,
+            "kind": "oracle", "sample": f"{n} full time steps of {wl.name} after 1 warm-up step",
+            "single_core": {"value": wl.cells * n1 / t1 / 1e6, "unit": "MLUPS",
+                            "sample": f"{n1} more full time steps of {wl.name} on 1 thread"},
+            "host": host_cpu()}
 
 
 def precision_sweep(torch, device=0, steps=None):
@@ -443,6 +489,7 @@ def ours(args):
                      "bytes_per_launch": sweep_bytes,
                      "per_unit": f"2*19*{BYTES[head]} B per cell update", "peak_kind": peak_kind,
                      "sweep_ms": sweep_ms},
+        "fluid_mlups": round(value * fluid_fraction(wl), 1),
         "kernels_ms_per_step": {k: v[0] / max(v[1], 1) * (v[1] / n_traced) for k, v in prof.items()},
         "kernels_note": ("links = k_body_fused (bounce-back, force, Newton-Euler, re-classification, "
                          "conversions and link rebuild of each isolated sphere, one thread-block cluster "
@@ -528,7 +575,7 @@ def reference(args):
         "config": {"workload": wl.name, "shape": list(wl.shape), "storage": "f64 (oracle)"},
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
                          "sample": f"{n} of the requested {args.steps} full time steps of {wl.name} "
-                                   f"(bounded to {budget:.0f} s)"},
+                                   f"(bounded to {budget:.0f} s)", "host": host_cpu()},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

@@ -914,6 +914,16 @@ int32_t oracle_num_threads(void) {
 #endif
 }
 
+/* Threads of the collide and stream loops from now on (n >= 1); no effect
+ * without OpenMP.  The results do not depend on it. */
+void oracle_set_num_threads(int32_t n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Conversion force and torque booked by the last remap, to be applied in the
  * next update. */
 int32_t osim_get_pending_conversion(const osim* s, int32_t id, double* Fc, double* Tc) {

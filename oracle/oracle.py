@@ -64,6 +64,7 @@ def load_oracle():
             "oracle_min_image": (C.c_double, [C.c_double, C.c_int32]),
             "oracle_wca": (C.c_double, [C.c_double, C.c_double, C.c_double]),
             "oracle_num_threads": (C.c_int32, []),
+            "oracle_set_num_threads": (None, [C.c_int32]),
             "osim_create": (C.c_void_p, [C.c_int32, C.c_int32, C.c_int32,
                                          C.c_double, C.c_double, C.c_double]),
             "osim_destroy": (None, [C.c_void_p]),
@@ -187,6 +188,10 @@ def wca(r: float, sigma: float, eps: float) -> float:
 
 def num_threads() -> int:
     return int(load_oracle().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    load_oracle().oracle_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------- simulation
