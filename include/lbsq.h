@@ -258,7 +258,7 @@ lb_status lb_get_links(lb_ctx* c, int32_t id, int64_t* out, int64_t cap, int64_t
  * positions may differ: the checkpoint's replace them), and the same
  * lb_set_contact and lb_set_force_average settings (not checked).  Stepping it then
  * gives the bits the checkpointed context would have given.  The caller's
- * buffer is not kept.  The format is that of this build of the library
+ * buffer is not kept.  The format is that of the library version that wrote it
  * (host byte order, the library's structure layouts).
  *
  * Errors: LB_ERR_INVALID (NULL, buffer too small, not a checkpoint, or one of
