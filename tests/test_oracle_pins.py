@@ -156,6 +156,47 @@ def test_shear_wave_decay_gives_viscosity(le):
     assert e64 < e32 / 3 or e64 < 1e-6
 
 
+@pytest.mark.parametrize("collision,le", [("trt", 1.3), ("bgk", 0.7)])
+def test_bulk_step_against_naive_two_array_step(collision, le):
+    """Sec. III, Eq. "lb" on a tiny ragged periodic lattice with random
+    far-from-equilibrium populations: the oracle's steps against a naive
+    restatement in numpy -- moments, the textbook equilibrium
+    w rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u), even/odd parts over opposite
+    pairs relaxed with lambda_e and lambda_o, then every population pushed to
+    x + c_i with periodic wrap (np.roll) -- within 1e-14 after three steps.
+    Only the velocity order is taken from the oracle; the weights come from
+    the speeds (1/3, 1/18, 1/36).  A stream pushed the wrong way, a swapped
+    rate or an index slip fails."""
+    shape = (5, 4, 3)
+    lo = le if collision == "bgk" else O.lambda_odd(le, 3 / 16)
+    s = O.OracleSim(*shape, lambda_e=le, collision=collision, magic=3 / 16)
+    c = O.velocities().astype(int)
+    w = np.array([{0: 1 / 3, 1: 1 / 18, 2: 1 / 36}[int(v @ v)] for v in c])
+    opp = [int(np.nonzero((c == -c[i]).all(axis=1))[0][0]) for i in range(19)]
+    rng = np.random.default_rng(12)
+    N = int(np.prod(shape))
+    f = w[:, None] * (1.0 + 0.4 * rng.random((19, N)))
+    s.set_populations(f)
+    g = f.reshape(19, shape[2], shape[1], shape[0])  # [i][z][y][x]
+    cf = c.astype(float)
+    for _ in range(3):
+        rho = g.sum(axis=0)
+        j = np.einsum("ia,izyx->azyx", cf, g)
+        u = j / rho
+        uu = (u * u).sum(axis=0)
+        cu = np.einsum("ia,azyx->izyx", cf, u)
+        feq = w[:, None, None, None] * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * uu)
+        post = np.empty_like(g)
+        for i in range(19):
+            k = opp[i]
+            fp, fm = (g[i] + g[k]) / 2, (g[i] - g[k]) / 2
+            ep, em = (feq[i] + feq[k]) / 2, (feq[i] - feq[k]) / 2
+            post[i] = g[i] - le * (fp - ep) - lo * (fm - em)
+        g = np.stack([np.roll(post[i], shift=(c[i, 2], c[i, 1], c[i, 0]), axis=(0, 1, 2)) for i in range(19)])
+    s.step(3)
+    np.testing.assert_allclose(s.populations(), g.reshape(19, N), rtol=0, atol=1e-14)
+
+
 def test_periodic_box_conserves_mass_and_momentum():
     """Sec. I / III: LB conserves mass and momentum to machine precision."""
     n = 12
