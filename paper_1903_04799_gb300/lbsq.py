@@ -19,6 +19,7 @@ from . import build as _build
 
 LB_OK, LB_ERR_INVALID, LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_OVERLAP = 0, 1, 2, 3, 4
 LB_ERR_DIVERGED, LB_ERR_TIMEOUT, LB_ERR_STATE, LB_ERR_CAPACITY = 5, 6, 7, 8
+LB_EQ_COMPRESSIBLE, LB_EQ_INCOMPRESSIBLE = 0, 1
 LB_BGK, LB_TRT = 0, 1
 LB_F64, LB_F32, LB_F16DEV, LB_BF16DEV = 0, 1, 2, 3
 STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16dev": LB_F16DEV, "bf16dev": LB_BF16DEV}
@@ -498,7 +499,7 @@ class Lattice:
         p.dev_scale_log2 = int(dev_scale_log2)
         if equilibrium not in ("compressible", "incompressible"):
             raise ValueError(f"equilibrium {equilibrium!r}")
-        p.equilibrium = 1 if equilibrium == "incompressible" else 0
+        p.equilibrium = LB_EQ_INCOMPRESSIBLE if equilibrium == "incompressible" else LB_EQ_COMPRESSIBLE
         p.device = int(device)
         self._stream = None
         self._alloc = None

@@ -50,8 +50,9 @@ def test_params_default_and_invalid_arguments(lib):
     p = lbsq.lb_params_default()
     assert (p.nx, p.ny, p.nz) == (32, 32, 32) and p.lambda_e == 1.0 and abs(p.magic - 0.1875) < 1e-15
     ctx = C.c_void_p()
+    assert p.equilibrium == lbsq.LB_EQ_COMPRESSIBLE
     for field, bad in [("nx", 0), ("lambda_e", 2.0), ("lambda_e", 0.0), ("rho0", -1.0),
-                       ("storage", 9), ("collision", 5)]:
+                       ("storage", 9), ("collision", 5), ("equilibrium", 2), ("equilibrium", -1)]:
         q = lbsq.lb_params_default()
         setattr(q, field, bad)
         assert lib.lb_create(C.byref(q), C.byref(ctx)) == lbsq.LB_ERR_INVALID
@@ -61,4 +62,5 @@ def test_params_default_and_invalid_arguments(lib):
     assert lib.lb_create(None, C.byref(ctx)) == lbsq.LB_ERR_INVALID
     assert lib.lb_destroy(None) == lbsq.LB_OK
     assert lib.lb_step(None, 1) == lbsq.LB_ERR_INVALID
+    assert lib.lb_set_force_average(None, 1) == lbsq.LB_ERR_INVALID
     assert lib.lb_last_error(None) == b"null context"
