@@ -247,6 +247,7 @@ typedef struct {
     double wca_sigma, wca_eps;
     int force_avg; /* 1: Ladd's two-step average of F_bb and T_bb */
     int inc;       /* 1: incompressible equilibrium (oracle_feq_inc) throughout */
+    double link_at; /* where on a link v_b and the lever arm are taken: 0.5 (midpoint) or 1 (boundary node) */
     int nobj, capobj;
     oobj* obj; /* obj[k] has id k+1 */
     long step;
@@ -302,6 +303,7 @@ osim* osim_create(int32_t nx, int32_t ny, int32_t nz, double lambda_e, double la
     s->lambda_e = lambda_e;
     s->lambda_o = lambda_o;
     s->rho0 = rho0;
+    s->link_at = 0.5; /* link midpoint */
     s->f = (double*)malloc(sizeof(double) * Q * s->N);
     s->fpost = (double*)malloc(sizeof(double) * Q * s->N);
     s->fnew = (double*)malloc(sizeof(double) * Q * s->N);
@@ -348,6 +350,12 @@ void osim_set_force_average(osim* s, int on) { s->force_avg = on ? 1 : 0; }
 /* Incompressible equilibrium (oracle_feq_inc) in the collision, the refill,
  * osim_set_equilibrium and the exported velocity u = j / rho0. */
 void osim_set_incompressible(osim* s, int on) { s->inc = on ? 1 : 0; }
+
+/* Where a link's wall velocity and lever arm are taken: at the midpoint
+ * x + c_i/2 (at_node = 0, the reading used throughout) or at the boundary
+ * node x + c_i that the text of Sec. III names (at_node = 1, kept to show
+ * that this reading misses the speeds printed in Fig. "resolution"). */
+void osim_set_link_at_node(osim* s, int at_node) { s->link_at = at_node ? 1.0 : 0.5; }
 
 /* Populations to the equilibrium of the given fields (rho[N], u as SoA [3][N]). */
 void osim_set_equilibrium(osim* s, const double* rho, const double* u) {
@@ -505,9 +513,9 @@ static void boundary_velocity(const osim* s, const oobj* o, int x, int y, int z,
         d[0] = d[1] = d[2] = 0.0;
         return;
     }
-    d[0] = min_image(((double)x + 0.5 * CX[i]) - o->pos[0], s->nx);
-    d[1] = min_image(((double)y + 0.5 * CY[i]) - o->pos[1], s->ny);
-    d[2] = min_image(((double)z + 0.5 * CZ[i]) - o->pos[2], s->nz);
+    d[0] = min_image(((double)x + s->link_at * CX[i]) - o->pos[0], s->nx);
+    d[1] = min_image(((double)y + s->link_at * CY[i]) - o->pos[1], s->ny);
+    d[2] = min_image(((double)z + s->link_at * CZ[i]) - o->pos[2], s->nz);
     double slip[3];
     oracle_slip(d, o->e, o->B1, o->B2, slip);
     vb[0] = o->vel[0] + (o->omega[1] * d[2] - o->omega[2] * d[1]) + slip[0];

@@ -75,6 +75,7 @@ def load_oracle():
             "osim_set_contact": (None, [C.c_void_p, C.c_double, C.c_double]),
             "osim_set_force_average": (None, [C.c_void_p, C.c_int32]),
             "osim_set_incompressible": (None, [C.c_void_p, C.c_int32]),
+            "osim_set_link_at_node": (None, [C.c_void_p, C.c_int32]),
             "osim_set_equilibrium": (None, [C.c_void_p, _DP, _DP]),
             "osim_set_populations": (None, [C.c_void_p, _DP]),
             "osim_get_populations": (None, [C.c_void_p, _DP]),
@@ -253,6 +254,9 @@ class OracleSim:
 
     def set_force_average(self, on: bool = True):
         self._lib.osim_set_force_average(self._h, 1 if on else 0)
+
+    def set_link_at_node(self, on: bool = True):
+        self._lib.osim_set_link_at_node(self._h, 1 if on else 0)
 
     def set_incompressible(self, on: bool = True):
         self._lib.osim_set_incompressible(self._h, 1 if on else 0)

@@ -610,14 +610,11 @@ def test_two_step_force_average_momentum_invariant():
     assert worst > 1e-6
 
 
-def test_swim_speed_matches_fig_resolution():
-    """Eq. "squirmer-speed" and Fig. "resolution": a free squirmer of R = 4 in a
-    periodic box L = 10R swims at the speed the paper prints, 0.9737 v0
-    (v0 = 2 B1 / 3), within 1.5%."""
-    rows = np.loadtxt(os.path.join(GOLDEN, "fig_resolution_squirmer.txt"))
-    ref = rows[(rows[:, 0] == 4) & (rows[:, 1] == 10)][0, 2]
+def _swim_speed_R4(at_node=False):
     R, L, B1 = 4, 40, 0.01
     s = O.OracleSim(L, L, L, lambda_e=1.0, collision="trt")
+    if at_node:
+        s.set_link_at_node(True)
     oid = s.add_sphere((L / 2 + 0.1, L / 2 + 0.2, L / 2), (0, 0, 1), R, B1=B1, beta=0.0)
     vs = []
     for k in range(1500):
@@ -625,8 +622,21 @@ def test_swim_speed_matches_fig_resolution():
         if k >= 750:
             _, v, e, _ = s.state(oid)
             vs.append(v @ e)
-    ratio = np.mean(vs) / (2 * B1 / 3)
+    return np.mean(vs) / (2 * B1 / 3)
+
+
+def test_swim_speed_matches_fig_resolution():
+    """Eq. "squirmer-speed" and Fig. "resolution": a free squirmer of R = 4 in a
+    periodic box L = 10R swims at the speed the paper prints, 0.9737 v0
+    (v0 = 2 B1 / 3), within 1.5%.  Taking the wall velocity and lever arm at
+    the boundary node, as the text of Sec. III words it, instead of the link
+    midpoint misses the printed speed by far more (reading R6)."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "fig_resolution_squirmer.txt"))
+    ref = rows[(rows[:, 0] == 4) & (rows[:, 1] == 10)][0, 2]
+    ratio = _swim_speed_R4()
     assert abs(ratio / ref - 1) < 0.015, ratio
+    node = _swim_speed_R4(at_node=True)
+    assert abs(node / ref - 1) > 0.08, node
 
 
 def _periodic_drag_ratio(R, L, off, steps, g=1e-7):
