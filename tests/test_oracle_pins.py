@@ -197,6 +197,28 @@ def test_bulk_step_against_naive_two_array_step(collision, le):
     np.testing.assert_allclose(s.populations(), g.reshape(19, N), rtol=0, atol=1e-14)
 
 
+def test_thread_count_does_not_change_a_bit():
+    """The oracle splits its collide and stream loops over threads; every
+    cell's arithmetic is its own and every sum over links or cells runs
+    serially, so one thread and all threads give the same bits (a free
+    swimmer crossing cells, 60 steps)."""
+    runs = []
+    full = O.num_threads()
+    for n in (1, full):
+        O.set_num_threads(n)
+        try:
+            s = O.OracleSim(24, 22, 26, lambda_e=1.0, collision="trt")
+            oid = s.add_sphere((11.3, 10.6, 12.2), (0.3, -0.2, 1.0), 4.2, B1=0.05, beta=-2.0, mobile=True)
+            s.step(60)
+            runs.append((s.populations(), s.owner(), s.state(oid)))
+        finally:
+            O.set_num_threads(full)
+    (fa, oa, sa), (fb, ob, sb) = runs
+    assert np.array_equal(fa, fb) and np.array_equal(oa, ob)
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)
+
+
 def test_periodic_box_conserves_mass_and_momentum():
     """Sec. I / III: LB conserves mass and momentum to machine precision."""
     n = 12
