@@ -121,7 +121,10 @@ void lb_params_default(lb_params* p);
  * LB_ERR_INVALID (sizes, rates, storage), LB_ERR_OOM, LB_ERR_CUDA. */
 lb_status lb_create(const lb_params* p, lb_ctx** out);
 
-/* Free all device memory of the context.  NULL is accepted. */
+/* End a simulation: free all device memory of the context (the paper's
+ * method has no counterpart; the context is this library's container for
+ * the lattice of Sec. III).  Synchronises the context's stream first.  NULL
+ * is accepted.  Errors: LB_ERR_CUDA. */
 lb_status lb_destroy(lb_ctx* c);
 
 /* Add a sphere of radius R centred at pos (wrapped into the box) with unit
@@ -179,7 +182,16 @@ lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u);
 lb_status lb_set_populations(lb_ctx* c, const double* f);
 lb_status lb_get_populations(lb_ctx* c, double* f);
 
-/* Enqueue nsteps >= 0 time steps.  When the bodies occupy a thin box of
+/* Enqueue nsteps >= 0 time steps.  One step is the update of Sec. III in
+ * this order: stream and collide every cell (Eq. "lb"); bounce back every
+ * boundary link with the moving-wall shift of the squirmer surface velocity
+ * (Eq. "vb" with the slip of Eq. "squirmer"), summing the momentum exchange
+ * force and torque (Eqs. "bbforce", "bbtorque"); advance each mobile body by
+ * the symplectic Euler step that closes Sec. III with that force plus the
+ * conversion force of Eq. "consforce" (and the WCA force of Eq. "wca" when
+ * contact is on); re-classify the cells the moved bodies cover or uncover,
+ * booking their momentum and refilling uncovered cells; rebuild the link
+ * lists.  When the bodies occupy a thin box of
  * rows, a step's body kernels run beside the sweep of the cells away from
  * the bodies in the next step; the body kernels of the last step enqueued
  * are then issued by the next call that steps, reads or changes the context
@@ -213,8 +225,12 @@ lb_status lb_get_owner(lb_ctx* c, int32_t* owner);
  * walls the momentum exchange of the last step.  Synchronises. */
 lb_status lb_get_force_torque(lb_ctx* c, int32_t id, double F[3], double T[3]);
 
-/* Position, velocity, orientation and angular velocity of body `id`.
- * Synchronises.  Any pointer may be NULL. */
+/* Position, velocity, orientation and angular velocity of body `id`: the
+ * state the symplectic Euler step at the end of Sec. III advances (r, v, the
+ * unit swimming direction e of Eq. "squirmer", omega), after the last step
+ * enqueued.  FP64, host buffers of 3 doubles each.  Synchronises.  Any
+ * pointer may be NULL.  Errors: LB_ERR_INVALID (id), LB_ERR_CUDA and the
+ * device errors of the steps (see above). */
 lb_status lb_get_object_state(lb_ctx* c, int32_t id, double pos[3], double vel[3], double e[3],
                               double omega[3]);
 
@@ -275,22 +291,19 @@ const char* lb_last_error(const lb_ctx* c);
 /* Number of kernel launches the context has enqueued so far (all kinds). */
 int64_t lb_kernel_launches(const lb_ctx* c);
 
-/* Tuning: the launch shape of the stream-collide kernel.  0 = default
- * (FP16 / BF16 storage: even steps as 6, odd steps as 2; FP32 with even nx:
- * two cells per thread with paired loads; FP64: one cell),
- * 1 = one cell per thread, 2 = two cells per thread where nx is even, 3 =
- * FP16 / BF16 storage: four cells per thread in aligned 8-byte chunks where
- * nx is a multiple of 128 (else as 2), 4 = FP16 / BF16: two cells per thread
- * with the values kept packed (else as 2), 5 = FP16 / BF16: two cells per
- * thread on four consecutive planes, the loads of the next plane issued
- * before the collision of the current one (else as 2), 6 = FP16 / BF16: four
- * cells per thread in blocks of whole rows, the odd-step x-shifts through
- * shared memory (nx a multiple of 4 up to 768; else as 2), 7 = FP16 / BF16:
- * persistent CTAs whose loads are staged in shared memory by asynchronous
- * 16-byte copies (cp.async), several rows ahead (nx a multiple of 8 up to 512
- * and a 16-byte aligned array; else as 2).  Results are
- * identical bit for bit; only the speed differs.  LB_ERR_INVALID for another
- * value. */
+/* Tuning: the form of the stream-collide kernel (Sec. III, Eq. "lb").
+ * 0 = default: FP64 storage collided in double-float arithmetic (pairs of
+ * FP32 numbers, about 47 significant bits), one cell per thread; FP32 with
+ * even nx: two cells per thread with paired loads; FP16 / BF16: even steps
+ * as 3, odd steps as 2.
+ * 1 = one cell per thread; for FP64 storage, FP64 arithmetic.
+ * 2 = two cells per thread where nx is even (not FP64).
+ * 3 = FP16 / BF16: four cells per thread in blocks of whole rows, the
+ *     odd-step x-shifts through shared memory (nx a multiple of 4 up to 768;
+ *     else as 2).
+ * For FP32, FP16 and BF16 the forms give identical bits; for FP64 the two
+ * arithmetics agree to about 1e-14 relative per step.  LB_ERR_INVALID for
+ * another value. */
 lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant);
 
 /* Kernel tracing.  Between lb_profile_begin and lb_profile_end, lb_step
@@ -405,7 +418,13 @@ const char* lb_server_last_error(const lb_server* s);
  *   stream  cudaStream_t, or NULL for the legacy default stream.
  * Runs on the current device, stream-ordered; it does not synchronise.  The
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * (cudaGetSymbolAddress).  Under CUDA's default lazy module loading that
+ * first lookup also loads this entry point's device code and array onto the
+ * device, which takes device memory and may synchronise; so make the first
+ * call on each device during set-up, before the caller's own pool takes the
+ * device memory and before any stream capture.  Later calls allocate
+ * nothing.  A call made while the calling thread already holds a CUDA error
+ * returns LB_ERR_CUDA, launches nothing and leaves that error in place.
  * Every call shares the one array: calls that overlap on the GPU race, so
  * issue them on one stream.  Each call writes every partial it reads, so
  * nothing needs clearing between calls.  Errors: LB_ERR_INVALID (f or out

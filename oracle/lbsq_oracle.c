@@ -36,8 +36,7 @@
  *      and the created/destroyed momentum is booked as conversion force
  *      (Sec. III, last paragraph of the moving-boundary description).
  *
- * Readings of the paper where it is silent or garbled (each is listed in the
- * design notes of the repository):
+ * Readings of the paper where it is silent or garbled:
  *   - f_eq uses the standard second-order D3Q19 coefficients 9/2 and 3/2
  *     (the printed 1/6 cannot satisfy the second-moment identity);
  *   - "lambda_o lambda_e = 3/16" is the TRT magic parameter

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbsq.so")
-SOURCES = ["sweep.cu", "sweep_async.cu", "bodies.cu", "setup.cu", "api.cu", "serve.cu", "static_scratch.cu"]
+SOURCES = ["sweep.cu", "bodies.cu", "setup.cu", "api.cu", "serve.cu", "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

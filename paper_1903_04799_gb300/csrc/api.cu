@@ -1116,7 +1116,7 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
 }
 
 lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant) {
-    if (!c || variant < 0 || variant > 7) return LB_ERR_INVALID;
+    if (!c || variant < 0 || variant > 3) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
     settle(c);
     c->sweep_variant = variant;
@@ -1392,7 +1392,7 @@ lb_status lb_checkpoint(lb_ctx* c, void* buf, size_t bytes) {
     unsigned char* o = static_cast<unsigned char*>(buf);
     CkptHeader h{};
     std::memcpy(h.magic, kCkptMagic, 8);
-    h.version = 2;
+    h.version = 3;  // 3: FP64 populations are stored as deviations f - w rho0
     h.storage = (uint32_t)c->p.storage;
     h.equilibrium = c->L.inc;
     h.nx = c->L.nx;
@@ -1438,7 +1438,7 @@ lb_status lb_restore(lb_ctx* c, const void* buf, size_t bytes) {
     if (!c || !buf || bytes < sizeof(CkptHeader)) return LB_ERR_INVALID;
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 2) return fail(c, LB_ERR_INVALID, "not a checkpoint");
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 3) return fail(c, LB_ERR_INVALID, "not a checkpoint");
     if (h.bytes != bytes) return fail(c, LB_ERR_INVALID, "checkpoint size differs from its header");
     if (h.storage != (uint32_t)c->p.storage || h.nx != c->L.nx || h.ny != c->L.ny || h.nz != c->L.nz ||
         h.lambda_e != c->lambda_e || h.lambda_o != c->lambda_o || h.rho0 != c->L.rho0 ||

@@ -783,9 +783,10 @@ __device__ __noinline__ void covered_momentum(const Lattice& L, const BodyState&
     // sums run in direction order
     double m[3] = {0.0, 0.0, 0.0};
     if (L.storage == ST_F64) {
+        // sum_i c_i w_i rho0 = 0: the momentum is that of the stored deviations
         double f[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[i] = load_abs<CG>(L, read_slot(L, i, x, y, z, q), i);
+        for (int i = 0; i < Q; ++i) f[i] = ld<CG>((const double*)L.F + read_slot(L, i, x, y, z, q));
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             m[0] += f[i] * cx(i);
@@ -957,13 +958,14 @@ __device__ __forceinline__ double warp_tree_sum(double v) {
 template <bool CG>
 __device__ __forceinline__ double node_density(const Lattice& L, int x, int y, int z, int q) {
     if (L.storage == ST_F64) {
+        // rho0 plus the sum of the stored deviations
         double f[Q];
 #pragma unroll
         for (int j = 0; j < Q; ++j) f[j] = ld<CG>((const double*)L.F + read_slot(L, j, x, y, z, q));
         double r = 0.0;
 #pragma unroll
         for (int j = 0; j < Q; ++j) r += f[j];
-        return r;
+        return L.rho0 + r;
     }
     float g[Q];
 #pragma unroll

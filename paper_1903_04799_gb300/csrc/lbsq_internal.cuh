@@ -89,13 +89,13 @@ __device__ __forceinline__ void st_stream(U* p, const U& v) {
 }
 
 // Storage traits: the stored type, the arithmetic type of the collision,
-// whether the store holds a deviation from w_i rho0, and the sweeps'
-// (streaming) element access.
+// whether the store holds a deviation from w_i rho0 (every storage does), and
+// the sweeps' (streaming) element access.
 template <int S> struct StoreT;
 template <> struct StoreT<ST_F64> {
     using T = double;
     using R = double;
-    static constexpr bool dev = false;
+    static constexpr bool dev = true;
     __device__ static R load(const T* p, R) { return ld_stream(p); }
     __device__ static void store(T* p, R v, R) { st_stream(p, v); }
 };
@@ -188,7 +188,7 @@ __device__ __forceinline__ T ld(const T* p) {
 template <bool CG = false>
 __device__ __forceinline__ double load_abs(const Lattice& L, int64_t slot, int i) {
     switch (L.storage) {
-        case ST_F64: return ld<CG>((const double*)L.F + slot);
+        case ST_F64: return wgt(i) * L.rho0 + ld<CG>((const double*)L.F + slot);
         case ST_F32: return wgt(i) * L.rho0 + (double)ld<CG>((const float*)L.F + slot);
         case ST_F16: return wgt(i) * L.rho0 + (double)(__half2float(ld<CG>((const __half*)L.F + slot)) * L.inv_scale);
         default:
@@ -197,10 +197,10 @@ __device__ __forceinline__ double load_abs(const Lattice& L, int64_t slot, int i
     }
 }
 
-// Store an absolute value f_i into a slot (reduced storages keep f_i - w_i rho0).
+// Store an absolute value f_i into a slot (every storage keeps f_i - w_i rho0).
 __device__ __forceinline__ void store_abs(const Lattice& L, int64_t slot, int i, double f) {
     switch (L.storage) {
-        case ST_F64: ((double*)L.F)[slot] = f; break;
+        case ST_F64: ((double*)L.F)[slot] = f - wgt(i) * L.rho0; break;
         case ST_F32: ((float*)L.F)[slot] = (float)(f - wgt(i) * L.rho0); break;
         case ST_F16: ((__half*)L.F)[slot] = __float2half_rn((float)(f - wgt(i) * L.rho0) * L.scale); break;
         default: ((__nv_bfloat16*)L.F)[slot] = __float2bfloat16_rn((float)(f - wgt(i) * L.rho0) * L.scale); break;

@@ -13,7 +13,12 @@
 // The array lives in every GPU that loads the library, until the process
 // exits.  In host code its name is only a host-side stand-in: the device
 // address is obtained once per device with cudaGetSymbolAddress (with that
-// device current) and passed to the kernels.  Every call shares the array, so
+// device current) and passed to the kernels.  Under CUDA's lazy module
+// loading (the default) that first lookup also loads this file's device code
+// and array onto the device, which itself takes device memory and may
+// synchronise: a caller that must never allocate makes its first call on each
+// device during set-up, before its own pool takes the memory and before any
+// stream capture.  Every call shares the array, so
 // calls that overlap on the GPU (two streams at once) race; calls on one
 // stream are ordered and safe.  Each call writes every partial it reads, so
 // nothing needs clearing between calls.
@@ -37,7 +42,9 @@ std::mutex g_scratch_mutex;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Block b sums cells b*T + t, b*T + t + G*T, ... (a fixed assignment) and
-// writes its partial; the layout and tree match the library's own mass sum.
+// writes its partial.  Up to 1024 x 256 cells each thread holds one cell, as
+// in the library's own mass sum; larger fields grid-stride over 1024 blocks,
+// so the order of the additions (and the last bits) then differ from it.
 __global__ void __launch_bounds__(kStaticThreads) k_totals_static_partial(const double* __restrict__ f,
                                                                           const int32_t* __restrict__ owner,
                                                                           int64_t N, double* scratch) {
@@ -112,6 +119,10 @@ extern "C" lb_status lb_fluid_totals_static(const double* f, const int32_t* owne
     double* scratch = nullptr;
     if (scratch_address(device, &scratch) != cudaSuccess) return LB_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
+    // An error the calling thread already holds (from earlier, unrelated work)
+    // is left for its owner to read, and nothing is launched; after the two
+    // launches below, the thread's error state holds only theirs.
+    if (cudaPeekAtLastError() != cudaSuccess) return LB_ERR_CUDA;
     const int64_t want = (n_cells + kStaticThreads - 1) / kStaticThreads;
     const int nblocks = (int)(want < kStaticBlocks ? want : kStaticBlocks);
     k_totals_static_partial<<<nblocks, kStaticThreads, 0, st>>>(f, owner, n_cells, scratch);

@@ -11,13 +11,29 @@
 
 namespace lbsq {
 
-template <int S, int P>
+template <int S, int P, bool NATIVE>
 __global__ void __launch_bounds__(256) k_sweep(const SweepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int z = sweep_plane(a);
     const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y, z);
     if (x >= a.nx || y < 0) return;
-    sweep_one<S, P>(a, x, y, z);
+    sweep_one<S, P, NATIVE>(a, x, y, z);
+}
+
+// FP64 storage, double-float collision (sweep_df.cuh), one cell per thread.
+template <int P, bool O32, bool LE1>
+__global__ void __launch_bounds__(256, 2) k_sweep_df(const SweepArgs a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int z = sweep_plane(a);
+    const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y, z);
+    if (x >= a.nx || y < 0) return;
+    sweep_one_df<P, O32, LE1>(a, x, y, z);
+}
+
+template <bool O32, bool LE1>
+static void launch_df(const SweepArgs& a, int parity, const dim3& grid, int bx, cudaStream_t st) {
+    if (parity == 0) k_sweep_df<0, O32, LE1><<<grid, bx, 0, st>>>(a);
+    else k_sweep_df<1, O32, LE1><<<grid, bx, 0, st>>>(a);
 }
 
 template <int S, int P, bool O32>
@@ -27,54 +43,6 @@ __global__ void __launch_bounds__(256, 2) k_sweep2(const SweepArgs a) {
     const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
     if (x0 >= a.nx || y < 0) return;
     sweep_two<S, P, O32>(a, x0, y, z);
-}
-
-// 16-bit storages: the packed two-cell form, three blocks per SM.
-template <int S, int P>
-__global__ void __launch_bounds__(256, 3) k_sweep2p(const SweepArgs a) {
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int z = sweep_plane(a);
-    const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
-    if (x0 >= a.nx || y < 0) return;
-    sweep_two16<S, P>(a, x0, y, z);
-}
-
-// 16-bit storages with nx % 128 == 0 and 19 Np < 2^31: a warp per 128 cells
-// of a row, eight rows per block (see sweep_four).
-template <int S, int P, int ROWS>
-__global__ void __launch_bounds__(32 * ROWS, 2) k_sweep4(const SweepArgs a) {
-    const int lane = threadIdx.x;
-    const int x0 = 128 * blockIdx.x + 4 * lane;
-    const int z = sweep_plane(a);
-    const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
-    if (y < 0) return;  // a whole warp
-    sweep_four<S, P>(a, x0, y, z, lane);
-}
-
-// 16-bit storages, two cells per thread on kPlanes consecutive plane slots,
-// software-pipelined (see load_pair16).
-constexpr int kPlanes = 4;
-
-template <int S, int P>
-__global__ void __launch_bounds__(256, 2) k_sweep2z(const SweepArgs a, int slots) {
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int ly = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x0 >= a.nx) return;
-    const int p0 = blockIdx.z * kPlanes;
-    unsigned int cur[Q], nxt[Q];
-    int z = sweep_plane_at(a, p0);
-    int y = z < 0 ? -1 : sweep_row(a, ly, z);  // the row depends on the plane in the far sweep
-    if (y >= 0) load_pair16<S, P>(a, x0, y, z, cur);
-    for (int k = 0; k < kPlanes && p0 + k < slots; ++k) {
-        const int zn = (k + 1 < kPlanes && p0 + k + 1 < slots) ? sweep_plane_at(a, p0 + k + 1) : -1;
-        const int yn = zn < 0 ? -1 : sweep_row(a, ly, zn);
-        if (yn >= 0) load_pair16<S, P>(a, x0, yn, zn, nxt);  // in flight during the collision below
-        if (y >= 0) collide_store_pair16<S, P>(a, x0, y, z, cur);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
-        z = zn;
-        y = yn;
-    }
 }
 
 // 16-bit storages with nx % 4 == 0, nx <= 768: blocks of whole rows, four
@@ -114,36 +82,34 @@ static int prefetch_ahead(const SweepArgs& a, int storage, const dim3& grid) {
     return ahead < a.nz ? ahead : 0;
 }
 
-bool sweep_async_supported(const SweepArgs& a, int storage_bytes);
-void launch_sweep_async(const SweepArgs& a, int storage, int parity, int gz, int gy, cudaStream_t st);
-
 template <int S>
 static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy, cudaStream_t st) {
+    const bool o32 = 19 * a.Np < (int64_t(1) << 32);  // element offsets fit 32 bits
+    if constexpr (S == ST_F64) {
+        int bx = ((a.nx + 31) / 32) * 32;
+        if (bx > 256) bx = 256;
+        dim3 grid((a.nx + bx - 1) / bx, gy, gz);
+        if (variant == 1) {  // FP64 arithmetic
+            if (parity == 0) k_sweep<S, 0, true><<<grid, bx, 0, st>>>(a);
+            else k_sweep<S, 1, true><<<grid, bx, 0, st>>>(a);
+        } else if (o32) {
+            if (a.K.df.le1) launch_df<true, true>(a, parity, grid, bx, st);
+            else launch_df<true, false>(a, parity, grid, bx, st);
+        } else {
+            if (a.K.df.le1) launch_df<false, true>(a, parity, grid, bx, st);
+            else launch_df<false, false>(a, parity, grid, bx, st);
+        }
+    } else {
     if constexpr (S == ST_F16 || S == ST_BF16) {
-        if (variant == 7 && sweep_async_supported(a, 2)) {
-            launch_sweep_async(a, S, parity, gz, gy, st);
-            return;
-        }
-        if (variant == 5 && a.nx % 2 == 0) {
-            const int pairs = a.nx / 2;
-            int bx = ((pairs + 31) / 32) * 32;
-            if (bx > 128) bx = 128;
-            const int by = 256 / bx;
-            dim3 block(bx, by), grid((pairs + bx - 1) / bx, (gy + by - 1) / by, (gz + kPlanes - 1) / kPlanes);
-            if (parity == 0) k_sweep2z<S, 0><<<grid, block, 0, st>>>(a, gz);
-            else k_sweep2z<S, 1><<<grid, block, 0, st>>>(a, gz);
-            return;
-        }
         // default: even steps in whole-row four-cell blocks (aligned 8-byte
         // chunks: 0.86 of the copy bandwidth at 256^3, against 0.74 for two
         // cells), odd steps in the two-cell form (0.63; the whole-row form's
         // odd steps, with their x-shifts through shared memory, measured 0.62)
         const bool rows4 = a.nx % 4 == 0 && a.nx <= 768;
-        if ((variant == 6 || (variant == 0 && parity == 0)) && rows4) {
+        if ((variant == 3 || (variant == 0 && parity == 0)) && rows4) {
             // odd steps (more live values) in blocks of at most 192 threads
             const int tx = a.nx / 4, ty = (parity == 0 ? 256 : 192) / tx > 0 ? (parity == 0 ? 256 : 192) / tx : 1;
             dim3 block(tx, ty), grid(1, (gy + ty - 1) / ty, gz);
-            const bool o32 = 19 * a.Np < (int64_t(1) << 32);  // element offsets fit 32 bits
             if (parity == 0) {
                 if (o32) k_sweep4r<S, 0, true><<<grid, block, 0, st>>>(a);
                 else k_sweep4r<S, 0, false><<<grid, block, 0, st>>>(a);
@@ -154,62 +120,38 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy
             }
             return;
         }
-        if (variant == 3 && a.nx % 128 == 0 && 19 * a.Np < (int64_t(1) << 31)) {
-            // odd steps hold more live values (the x-shifted chunks): 6 rows per
-            // block leave them 170 registers a thread at 2 blocks per SM
-            if (parity == 0) {
-                dim3 block(32, 8), grid(a.nx / 128, (gy + 7) / 8, gz);
-                k_sweep4<S, 0, 8><<<grid, block, 0, st>>>(a);
-            } else {
-                dim3 block(32, 6), grid(a.nx / 128, (gy + 5) / 6, gz);
-                k_sweep4<S, 1, 6><<<grid, block, 0, st>>>(a);
-            }
-            return;
-        }
     }
-    if constexpr (S != ST_F64) {
-        if (variant != 1 && a.nx % 2 == 0) {
-            const int pairs = a.nx / 2;
-            int bx = ((pairs + 31) / 32) * 32;
-            if (bx > 128) bx = 128;
-            const int by = 256 / bx;
-            dim3 block(bx, by), grid((pairs + bx - 1) / bx, (gy + by - 1) / by, gz);
-            if constexpr (S == ST_F16 || S == ST_BF16) {
-                if (variant == 4 && 19 * a.Np < (int64_t(1) << 31)) {  // the packed form
-                    if (parity == 0) k_sweep2p<S, 0><<<grid, block, 0, st>>>(a);
-                    else k_sweep2p<S, 1><<<grid, block, 0, st>>>(a);
-                    return;
-                }
-            }
-            SweepArgs b = a;
-            b.pf = prefetch_ahead(a, S, grid);
-            if (19 * a.Np < (int64_t(1) << 32)) {  // element offsets fit 32 bits
-                if (parity == 0) k_sweep2<S, 0, true><<<grid, block, 0, st>>>(b);
-                else k_sweep2<S, 1, true><<<grid, block, 0, st>>>(b);
-            } else {
-                if (parity == 0) k_sweep2<S, 0, false><<<grid, block, 0, st>>>(b);
-                else k_sweep2<S, 1, false><<<grid, block, 0, st>>>(b);
-            }
-            return;
+    if (variant != 1 && a.nx % 2 == 0) {
+        const int pairs = a.nx / 2;
+        int bx = ((pairs + 31) / 32) * 32;
+        if (bx > 128) bx = 128;
+        const int by = 256 / bx;
+        dim3 block(bx, by), grid((pairs + bx - 1) / bx, (gy + by - 1) / by, gz);
+        SweepArgs b = a;
+        b.pf = prefetch_ahead(a, S, grid);
+        if (o32) {
+            if (parity == 0) k_sweep2<S, 0, true><<<grid, block, 0, st>>>(b);
+            else k_sweep2<S, 1, true><<<grid, block, 0, st>>>(b);
+        } else {
+            if (parity == 0) k_sweep2<S, 0, false><<<grid, block, 0, st>>>(b);
+            else k_sweep2<S, 1, false><<<grid, block, 0, st>>>(b);
         }
+        return;
     }
     int bx = ((a.nx + 31) / 32) * 32;
     if (bx > 256) bx = 256;
     dim3 grid((a.nx + bx - 1) / bx, gy, gz);
-    if (parity == 0) k_sweep<S, 0><<<grid, bx, 0, st>>>(a);
-    else k_sweep<S, 1><<<grid, bx, 0, st>>>(a);
+    if (parity == 0) k_sweep<S, 0, false><<<grid, bx, 0, st>>>(a);
+    else k_sweep<S, 1, false><<<grid, bx, 0, st>>>(a);
+    }
 }
 
-// variant: 0 = default (FP16 / BF16: even steps as 6, odd steps as 2; other
-// reduced storages with even nx: two cells per thread; FP64: one), 1 = one
-// cell per thread, 2 = two cells per thread where
-// possible, 3 = FP16 / BF16: four cells per thread where possible (else as
-// 2), 4 = FP16 / BF16: two cells per thread, packed (else as 2), 5 = FP16 /
-// BF16: two cells per thread on kPlanes planes, software-pipelined (else as 2),
-// 6 = FP16 / BF16: four cells per thread in blocks of whole rows, odd-step
-// x-shifts through shared memory (nx % 4 == 0, nx <= 768; else as 2), 7 =
-// FP16 / BF16: persistent CTAs, loads staged in shared memory by asynchronous
-// 16-byte copies (sweep_async.cu; nx % 8 == 0, nx <= 512; else as 2).
+// variant: 0 = default (FP64: double-float collision, one cell per thread;
+// FP32: two cells per thread (even nx); FP16 / BF16: even steps as 3, odd
+// steps as 2), 1 = one cell per thread (FP64: FP64 arithmetic), 2 = two
+// cells per thread where possible (not FP64), 3 = FP16 / BF16: four cells per
+// thread in blocks of whole rows on both parities, odd-step x-shifts through
+// shared memory (nx % 4 == 0, nx <= 768; else as 2).
 // zmode / win / gz / gy: cell selection (see SweepArgs); gz and gy = grid
 // planes and rows (nz and ny for modes 0 and 1, upper bounds of the window's
 // z and y lengths for mode 2).  Odd steps sweep the planes in descending

@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "lbsq_internal.cuh"
+#include "sweep_df.cuh"
 
 namespace lbsq {
 
@@ -30,6 +31,7 @@ struct TrtK {
     double d[8];
     float f[8];
     int inc;  // 1: incompressible equilibrium, u = j / rho0 (the quadratic terms take 1/rho0)
+    DfK df;   // the same constants (and rho0, 1/rho0) as double-float pairs, for FP64 storage
 };
 __host__ __device__ inline TrtK trt_constants(double le, double lo) {
     TrtK k;
@@ -246,9 +248,48 @@ __device__ __forceinline__ void collide_trt(V g[Q], const TrtK& K, V rho0) {
 // a multiply per population.
 template <int S> constexpr bool kScaled = S == ST_F16 || S == ST_BF16;
 
-// One cell (x, y, z).
-template <int S, int P>
+// One cell (x, y, z) with FP64 storage, collided in double-float arithmetic
+// (sweep_df.cuh).  O32: element offsets in 32-bit arithmetic (the launch
+// checks 19 Np < 2^32).
+template <int P, bool O32 = false, bool LE1 = true>
+__device__ __forceinline__ void sweep_one_df(const SweepArgs& a, int x, int y, int z) {
+    using Off = typename std::conditional<O32, uint32_t, int64_t>::type;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+    const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+    uint2* __restrict__ F = (uint2*)a.F;
+    const Off Np = (Off)a.Np;
+    auto cell = [&](int dx, int dy, int dz) -> Off {
+        return (Off)xs[1 + dx] + (Off)nx * ((Off)ys[1 + dy] + (Off)ny * (Off)zs[1 + dz]);
+    };
+    uint2 w[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        w[i] = ld_stream(F + (P == 0 ? (Off)i * Np + cell(0, 0, 0) : (Off)opp(i) * Np + cell(-cx(i), -cy(i), -cz(i))));
+    df g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = df_from_bits(w[i].x, w[i].y);
+    const bool ok = collide_trt_df<LE1>(g, a.K.df, a.K.inc);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) w[i] = df_to_bits(g[i]);
+    if (!ok) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) w[i] = make_uint2(0u, 0x7ff80000u);  // NaN: keep a diverged cell visible
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        st_stream(F + (P == 0 ? (Off)opp(i) * Np + cell(0, 0, 0) : (Off)i * Np + cell(cx(i), cy(i), cz(i))), w[i]);
+}
+
+// One cell (x, y, z).  FP64 storage collides in double-float arithmetic
+// unless NATIVE (FP64 arithmetic, the measured reference form).
+template <int S, int P, bool NATIVE = false>
 __device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int z) {
+    if constexpr (S == ST_F64 && !NATIVE) {
+        if (a.K.df.le1) sweep_one_df<P, false, true>(a, x, y, z);
+        else sweep_one_df<P, false, false>(a, x, y, z);
+    } else {
     using ST = StoreT<S>;
     using T = typename ST::T;
     using R = typename ST::R;
@@ -284,6 +325,7 @@ __device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int 
             off = (int64_t)i * Np + (xs[1 + cx(i)] + (int64_t)nx * (ys[1 + cy(i)] + (int64_t)ny * zs[1 + cz(i)]));
         }
         ST::store(F + off, g[i], sc);
+    }
     }
 }
 
@@ -420,235 +462,6 @@ template <> __device__ __forceinline__ unsigned int enc16<ST_BF16>(float v, floa
     return __bfloat16_as_ushort(__float2bfloat16_rn(v * sc));
 }
 
-// 16-bit storages, two cells (x0, x0 + 1) per thread, x0 even: the 19 values
-// of the pair stay packed (e0 | e1 << 16) in 19 registers and the cells are
-// decoded, collided and encoded back one at a time, so the kernel fits three
-// blocks of 256 threads per SM (the 16-bit sweep is short of warps to hide
-// its latency, not of memory instructions).  Loads and stores as sweep_two,
-// with 32-bit element offsets (requires 19 Np < 2^31).
-template <int S, int P>
-__device__ __forceinline__ void sweep_two16(const SweepArgs& a, int x0, int y, int z) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    // element offsets fit 32 bits (19 Np < 2^31, checked at launch)
-    const unsigned int Np = (unsigned int)a.Np, unx = (unsigned int)nx;
-    const unsigned int ys[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1), (unsigned)y, (unsigned)(y == ny - 1 ? 0 : y + 1)};
-    const unsigned int zs[3] = {(unsigned)(z == 0 ? nz - 1 : z - 1), (unsigned)z, (unsigned)(z == nz - 1 ? 0 : z + 1)};
-    const unsigned int xm0 = x0 == 0 ? nx - 1 : x0 - 1;  // x0 - 1
-    const unsigned int xp1 = x0 + 2 == nx ? 0 : x0 + 2;  // x0 + 2
-    const unsigned int ux0 = (unsigned)x0;
-    unsigned short* F = (unsigned short*)a.F;
-    const float rho0 = (float)a.rho0 * a.scale;  // scaled units (see kScaled)
-    auto row = [&](int dy, int dz) -> unsigned int { return unx * (ys[1 + dy] + (unsigned)ny * zs[1 + dz]); };
-    unsigned int g[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        if (P == 0) {
-            g[i] = ld_stream(reinterpret_cast<const unsigned int*>(F + ((unsigned)i * Np + row(0, 0) + ux0)));
-        } else {
-            const unsigned int base = (unsigned)opp(i) * Np + row(-cy(i), -cz(i));
-            if (cx(i) == 0) g[i] = ld_stream(reinterpret_cast<const unsigned int*>(F + (base + ux0)));
-            else if (cx(i) == 1) g[i] = (unsigned int)ld_stream(F + (base + xm0)) | ((unsigned int)ld_stream(F + (base + ux0)) << 16);
-            else g[i] = (unsigned int)ld_stream(F + (base + ux0 + 1)) | ((unsigned int)ld_stream(F + (base + xp1)) << 16);
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        float gc[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) gc[i] = dec16<S>(c ? (g[i] >> 16) : (g[i] & 0xffffu), 1.0f);
-        collide_trt<float, true>(gc, a.K, rho0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const unsigned int e = enc16<S>(gc[i], 1.0f);
-            g[i] = c ? ((g[i] & 0xffffu) | (e << 16)) : ((g[i] & 0xffff0000u) | e);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        if (P == 0) {
-            st_stream(reinterpret_cast<unsigned int*>(F + ((unsigned)opp(i) * Np + row(0, 0) + ux0)), g[i]);
-        } else {
-            const unsigned int base = (unsigned)i * Np + row(cy(i), cz(i));
-            if (cx(i) == 0) {
-                st_stream(reinterpret_cast<unsigned int*>(F + (base + ux0)), g[i]);
-            } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
-                st_stream(F + (base + ux0 + 1), (unsigned short)(g[i] & 0xffffu));
-                st_stream(F + (base + xp1), (unsigned short)(g[i] >> 16));
-            } else {  // targets x0 - 1 and x0
-                st_stream(F + (base + xm0), (unsigned short)(g[i] & 0xffffu));
-                st_stream(F + (base + ux0), (unsigned short)(g[i] >> 16));
-            }
-        }
-    }
-}
-
-// 16-bit storages, two cells (x0, x0 + 1) per thread on several planes of
-// the same column, software-pipelined: the loads of the next plane are issued
-// before the collision of the current one, so a thread keeps its loads in
-// flight while it computes (the 16-bit sweep is short of bytes in flight per
-// SM).  In-place AA makes this safe: a cell's read and write slots are its own
-// 19 slots, disjoint from any other cell's.  Values stay packed (e0 | e1 <<
-// 16) between load and collision; per-cell arithmetic as sweep_one.
-template <int S, int P>
-__device__ __forceinline__ void load_pair16(const SweepArgs& a, int x0, int y, int z, unsigned int (&g)[Q]) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
-    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
-    const int xm0 = x0 == 0 ? nx - 1 : x0 - 1;
-    const int xp1 = x0 + 2 == nx ? 0 : x0 + 2;
-    const unsigned short* F = (const unsigned short*)a.F;
-    const int64_t Np = a.Np;
-    auto row = [&](int dy, int dz) -> int64_t { return (int64_t)nx * (ys[1 + dy] + (int64_t)ny * zs[1 + dz]); };
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        if (P == 0) {
-            g[i] = ld_stream(reinterpret_cast<const unsigned int*>(F + (int64_t)i * Np + row(0, 0) + x0));
-        } else {
-            const unsigned short* base = F + (int64_t)opp(i) * Np + row(-cy(i), -cz(i));
-            if (cx(i) == 0) g[i] = ld_stream(reinterpret_cast<const unsigned int*>(base + x0));
-            else if (cx(i) == 1) g[i] = (unsigned int)ld_stream(base + xm0) | ((unsigned int)ld_stream(base + x0) << 16);
-            else g[i] = (unsigned int)ld_stream(base + x0 + 1) | ((unsigned int)ld_stream(base + xp1) << 16);
-        }
-    }
-}
-
-template <int S, int P>
-__device__ __forceinline__ void collide_store_pair16(const SweepArgs& a, int x0, int y, int z, unsigned int (&g)[Q]) {
-    const float rho0 = (float)a.rho0 * a.scale;  // scaled units (see kScaled)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        float gc[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) gc[i] = dec16<S>(c ? (g[i] >> 16) : (g[i] & 0xffffu), 1.0f);
-        collide_trt<float, true>(gc, a.K, rho0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const unsigned int e = enc16<S>(gc[i], 1.0f);
-            g[i] = c ? ((g[i] & 0xffffu) | (e << 16)) : ((g[i] & 0xffff0000u) | e);
-        }
-    }
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
-    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
-    const int xm0 = x0 == 0 ? nx - 1 : x0 - 1;
-    const int xp1 = x0 + 2 == nx ? 0 : x0 + 2;
-    unsigned short* F = (unsigned short*)a.F;
-    const int64_t Np = a.Np;
-    auto row = [&](int dy, int dz) -> int64_t { return (int64_t)nx * (ys[1 + dy] + (int64_t)ny * zs[1 + dz]); };
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        if (P == 0) {
-            st_stream(reinterpret_cast<unsigned int*>(F + (int64_t)opp(i) * Np + row(0, 0) + x0), g[i]);
-        } else {
-            unsigned short* base = F + (int64_t)i * Np + row(cy(i), cz(i));
-            if (cx(i) == 0) {
-                st_stream(reinterpret_cast<unsigned int*>(base + x0), g[i]);
-            } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
-                st_stream(base + x0 + 1, (unsigned short)(g[i] & 0xffffu));
-                st_stream(base + xp1, (unsigned short)(g[i] >> 16));
-            } else {  // targets x0 - 1 and x0
-                st_stream(base + xm0, (unsigned short)(g[i] & 0xffffu));
-                st_stream(base + x0, (unsigned short)(g[i] >> 16));
-            }
-        }
-    }
-}
-
-// 16-bit storages, four cells per thread.  A warp sweeps 128 consecutive
-// cells x0 .. x0 + 127 of one row (lane l: x0 + 4l .. x0 + 4l + 3), so every
-// population plane is read and written in aligned 8-byte chunks.  On odd
-// steps the x-shifted directions need the chunk moved by one cell: the
-// missing element comes from the neighbouring lane by a shuffle, and only
-// lanes 0 and 31 touch the single element beyond the warp's cells (with the
-// periodic wrap at the row ends).  Requires nx % 128 == 0 and 19 Np < 2^31
-// (32-bit element offsets keep the address arithmetic light).  The per-cell
-// arithmetic is that of sweep_one, so the results are the same bit for bit.
-template <int S, int P>
-__device__ __forceinline__ void sweep_four(const SweepArgs& a, int x0, int y, int z, int lane) {
-    constexpr unsigned kAll = 0xffffffffu;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    // element offsets fit 32 bits (19 Np < 2^31, checked at launch)
-    const unsigned int Np = (unsigned int)a.Np, unx = (unsigned int)nx;
-    const unsigned int ys[3] = {(unsigned)(y == 0 ? ny - 1 : y - 1), (unsigned)y, (unsigned)(y == ny - 1 ? 0 : y + 1)};
-    const unsigned int zs[3] = {(unsigned)(z == 0 ? nz - 1 : z - 1), (unsigned)z, (unsigned)(z == nz - 1 ? 0 : z + 1)};
-    const unsigned int xl = x0 == 0 ? nx - 1 : x0 - 1;  // the element left of the lane's chunk
-    const unsigned int xr = x0 + 4 == nx ? 0 : x0 + 4;  // and right of it
-    unsigned short* F = (unsigned short*)a.F;
-    const float isc = 1.0f, sc = 1.0f, rho0 = (float)a.rho0 * a.scale;  // scaled units (see kScaled)
-    auto row = [&](int dy, int dz) -> unsigned int { return unx * (ys[1 + dy] + (unsigned)ny * zs[1 + dz]); };
-    // chunk of 4 packed elements: .x = e0 | e1 << 16, .y = e2 | e3 << 16
-    uint2 g[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        if (P == 0) {
-            g[i] = ld_stream(reinterpret_cast<const uint2*>(F + ((unsigned)i * Np + row(0, 0) + x0)));
-        } else {
-            const unsigned int base = (unsigned)opp(i) * Np + row(-cy(i), -cz(i));
-            const uint2 c = ld_stream(reinterpret_cast<const uint2*>(F + (base + x0)));
-            if (cx(i) == 0) {
-                g[i] = c;
-            } else if (cx(i) == 1) {  // sources x0 - 1 .. x0 + 2
-                unsigned int prev = __shfl_up_sync(kAll, c.y, 1) >> 16;
-                if (lane == 0) prev = ld_stream(F + (base + xl));
-                g[i] = make_uint2(prev | (c.x << 16), (c.x >> 16) | (c.y << 16));
-            } else {  // sources x0 + 1 .. x0 + 4
-                unsigned int next = __shfl_down_sync(kAll, c.x, 1) & 0xffffu;
-                if (lane == 31) next = ld_stream(F + (base + xr));
-                g[i] = make_uint2((c.x >> 16) | (c.y << 16), (c.y >> 16) | (next << 16));
-            }
-        }
-    }
-    // collide the cells one at a time, each result back into its 16-bit slot
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        float gc[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const unsigned int w = c < 2 ? g[i].x : g[i].y;
-            gc[i] = dec16<S>((c & 1) ? (w >> 16) : (w & 0xffffu), isc);
-        }
-        collide_trt<float, true>(gc, a.K, rho0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const unsigned int e = enc16<S>(gc[i], sc);
-            unsigned int& w = c < 2 ? g[i].x : g[i].y;
-            w = (c & 1) ? ((w & 0xffffu) | (e << 16)) : ((w & 0xffff0000u) | e);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const uint2 o = g[i];  // post-collision f_i of cells x0 .. x0 + 3
-        if (P == 0) {
-            st_stream(reinterpret_cast<uint2*>(F + ((unsigned)opp(i) * Np + row(0, 0) + x0)), o);
-        } else {
-            const unsigned int base = (unsigned)i * Np + row(cy(i), cz(i));
-            if (cx(i) == 0) {
-                st_stream(reinterpret_cast<uint2*>(F + (base + x0)), o);
-            } else if (cx(i) == 1) {  // targets x0 + 1 .. x0 + 4
-                const unsigned int prev3 = __shfl_up_sync(kAll, o.y, 1) >> 16;
-                if (lane != 0) {
-                    st_stream(reinterpret_cast<uint2*>(F + (base + x0)),
-                              make_uint2(prev3 | (o.x << 16), (o.x >> 16) | (o.y << 16)));
-                } else {  // element x0 comes from the warp to the left
-                    st_stream(F + (base + x0 + 1), (unsigned short)(o.x & 0xffffu));
-                    st_stream(reinterpret_cast<unsigned int*>(F + (base + x0 + 2)), (o.x >> 16) | (o.y << 16));
-                }
-                if (lane == 31) st_stream(F + (base + xr), (unsigned short)(o.y >> 16));
-            } else {  // targets x0 - 1 .. x0 + 2
-                const unsigned int next0 = __shfl_down_sync(kAll, o.x, 1) & 0xffffu;
-                if (lane != 31) {
-                    st_stream(reinterpret_cast<uint2*>(F + (base + x0)),
-                              make_uint2((o.x >> 16) | (o.y << 16), (o.y >> 16) | (next0 << 16)));
-                } else {  // element x0 + 3 comes from the warp to the right
-                    st_stream(reinterpret_cast<unsigned int*>(F + (base + x0)), (o.x >> 16) | (o.y << 16));
-                    st_stream(F + (base + x0 + 2), (unsigned short)(o.y >> 16));
-                }
-                if (lane == 0) st_stream(F + (base + xl), (unsigned short)(o.x & 0xffffu));
-            }
-        }
-    }
-}
-
 // 16-bit storages, four cells per thread, blocks of whole rows: a row of nx
 // cells is nx / 4 threads (nx % 4 == 0, nx <= 768), so the x-neighbours of
 // every cell, the periodic wrap included, lie in the block.  Every global
@@ -769,6 +582,7 @@ __host__ __device__ inline SweepArgs sweep_args(const Lattice& L, double lambda_
     a.lambda_o = lambda_o;
     a.K = trt_constants(lambda_e, lambda_o);
     a.K.inc = L.inc;
+    a.K.df = df_constants(lambda_e, lambda_o, L.rho0);
     a.rho0 = L.rho0;
     a.scale = L.scale;
     a.inv_scale = L.inv_scale;

@@ -652,7 +652,7 @@ def test_swim_speed_matches_fig_resolution():
     periodic box L = 10R swims at the speed the paper prints, 0.9737 v0
     (v0 = 2 B1 / 3), within 1.5%.  Taking the wall velocity and lever arm at
     the boundary node, as the text of Sec. III words it, instead of the link
-    midpoint misses the printed speed by far more (reading R6)."""
+    midpoint misses the printed speed by far more."""
     rows = np.loadtxt(os.path.join(GOLDEN, "fig_resolution_squirmer.txt"))
     ref = rows[(rows[:, 0] == 4) & (rows[:, 1] == 10)][0, 2]
     ratio = _swim_speed_R4()
