@@ -6,14 +6,17 @@ the squirmer surface velocity, FP64 momentum-exchange force/torque reduction,
 symplectic Euler update, and (when a lattice node crosses the surface) cell
 conversion and link rebuild.
 
-Headline: the 128^3 free-swimmer configuration (R = 8, B1 = 0.005, beta = 0,
-TRT magic 3/16) with FP32 deviation storage, in MLUPS (million lattice-cell
-updates per second, all cells counted).  L2 is flushed (512 MiB write)
-before every timed iteration (64 steps for a lattice larger than L2, one
-step otherwise) and the flush is outside the timed events.
+Headline: the 256^3 pusher (R = 16, beta = -3, B1 = 0.002, TRT magic 3/16)
+with FP64 population storage (the deviations f - w rho0, collided in
+double-float arithmetic), in MLUPS (million lattice-cell updates per second,
+all cells counted).  The populations (2.55 GB) are far larger than L2; L2 is
+also flushed (512 MiB write) before every timed iteration of up to 64 steps,
+outside the timed events.  The same workload in FP32, FP16- and
+BF16-deviation storage, the precision sweep of the four storages and the
+serving mix are reported in the same line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--skip-accuracy] [--skip-extra]
+                    [--storage f64|f32|f16dev|bf16dev] [--skip-...]
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank advances its own
 lattice (independent replicas, weak scaling); time = max over ranks.
@@ -40,6 +43,14 @@ METRIC = "MLUPS & % HBM roofline, mixed-prec vs FP64 (≤1e-3 U err); p50/p99 la
 FALLBACK_HBM_GBS = 6800.0
 BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
 ARITH = {"f64": "f64", "f32": "f32", "f16dev": "f32", "bf16dev": "f32"}
+ARITH_NOTE = {"f64": "double-float collision (pairs of f32, ~47 significant bits) of f64-stored deviations; "
+                     "bodies, forces and Newton-Euler in f64",
+              "f32": "f32 collision of f32-stored deviations; bodies in f64",
+              "f16dev": "f32 collision of f16-stored deviations (scale 2^14); bodies in f64",
+              "bf16dev": "f32 collision of bf16-stored deviations; bodies in f64"}
+KERNEL = {"f64": "k_sweep_df (one cell per thread)", "f32": "k_sweep2 (two cells per thread)",
+          "f16dev": "k_sweep4r (even steps) / k_sweep2 (odd steps)",
+          "bf16dev": "k_sweep4r (even steps) / k_sweep2 (odd steps)"}
 
 
 def peaks():
@@ -52,7 +63,7 @@ def peaks():
 
 def sweep_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("sweep.cu", "sweep_body.cuh", "lbsq_internal.cuh"):
+    for f in ("sweep.cu", "sweep_body.cuh", "sweep_df.cuh", "lbsq_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1903_04799_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -172,8 +183,10 @@ def traced_steps(g, steps, flush, torch):
     return [a.elapsed_time(b) for a, b in ev], prof
 
 
-def run_variant(storage, wl, steps, warmup, flush, torch, device=0):
+def run_variant(storage, wl, steps, warmup, flush, torch, device=0, form=0):
     g, ids = build_lattice(storage, wl.shape, wl.bodies, wl.collision, wl.lambda_e, device)
+    if form:
+        g.set_sweep_variant(form)
     g.step(warmup)
     g.sync()
     chunk = chunk_for(g, storage)
@@ -203,28 +216,41 @@ def swim_speed(storage, wl, torch, device=0, chunk=200):
 
 
 def e2e_run(wl, storage, steps, device, torch):
-    """The public API end to end from host buffers: initial fields uploaded,
-    every step the body's trajectory read back, the fields read at the end."""
+    """The public API end to end from pinned host buffers.  Set-up (lb_create,
+    lb_add_squirmer) comes first, outside the timed region, as loading a model
+    does.  Timed: the initial density and velocity fields uploaded
+    (lb_set_fields), then every step lb_step(1) followed by a read of the
+    squirmer's state (lb_get_object_state, which synchronises), and at the end
+    the density and velocity fields read back (lb_get_fields)."""
     from paper_1903_04799_gb300 import workloads as W
     from paper_1903_04799_gb300 import lbsq
-    rho, u = W.smooth_fields(wl.shape, seed=1, drho=0.0, umax=0.0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    g, ids = build_lattice(storage, wl.shape, wl.bodies, wl.collision, wl.lambda_e, device)
-    g.set_fields(rho, u)
-    traj = np.empty((steps, 12))
-    for k in range(steps):
-        g.step(1)
-        p, vel, e, w = g.state(ids[0])
-        traj[k] = np.concatenate([p, vel, e, w])
-    rho_out, u_out = g.fields()
-    g.close()
-    t = time.perf_counter() - t0
     N = wl.cells
+    rho0, u0 = W.smooth_fields(wl.shape, seed=1, drho=0.0, umax=0.0)
+    pin = lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()  # noqa: E731
+    rho_in, u_in, rho_out, u_out = pin(N), pin(3 * N), pin(N), pin(3 * N)
+    rho_in[:] = rho0
+    u_in[:] = u0.reshape(-1)
+    g, ids = build_lattice(storage, wl.shape, wl.bodies, wl.collision, wl.lambda_e, device)
+    g.sync()
+    torch.cuda.synchronize()
+    lib = lbsq.load()
+    dp = lambda a: a.ctypes.data_as(lbsq._DP)  # noqa: E731
+    st = [np.empty(3) for _ in range(4)]
+    t0 = time.perf_counter()
+    lbsq._check(g.ctx, lib.lb_set_fields(g.ctx, dp(rho_in), dp(u_in)), "lb_set_fields")
+    for _ in range(steps):
+        lbsq._check(g.ctx, lib.lb_step(g.ctx, 1), "lb_step")
+        lbsq._check(g.ctx, lib.lb_get_object_state(g.ctx, ids[0], *[dp(a) for a in st]), "lb_get_object_state")
+    lbsq._check(g.ctx, lib.lb_get_fields(g.ctx, dp(rho_out), dp(u_out)), "lb_get_fields")
+    t = time.perf_counter() - t0
+    g.close()
     return {"value": N * steps / t / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": int(4 * N * 8 / steps),
             "d2h_bytes_per_step": int(12 * 8 + 4 * N * 8 / steps),
-            "steps": steps, "wall_s": t}
+            "steps": steps, "wall_s": t,
+            "note": ("timed: lb_set_fields from pinned host buffers, then per step lb_step(1) + "
+                     "lb_get_object_state (96 B), then lb_get_fields into pinned host buffers; "
+                     "lb_create / lb_add_squirmer before the timed region")}
 
 
 def serve_run(torch, device=0, n=256, budget=24 << 30, load=0.8):
@@ -284,7 +310,13 @@ def serve_run(torch, device=0, n=256, budget=24 << 30, load=0.8):
     lat = np.array([finish[i][0] - mix[i].arrival for i in range(n)])
     span = max(f[0] for f in finish.values()) - mix[0].arrival
     failed = sum(1 for f in finish.values() if f[1] != lbsq.LB_REQ_DONE)
+    # algorithmic population traffic of the mix, 2 * 19 * bytes per cell update
+    sbytes = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+    traffic = sum(m.cells * m.steps * 2 * 19 * sbytes[m.storage] for m in mix)
+    hbm, _ = peaks()
     return {"requests": n, "failed": failed, "p50_s": float(np.percentile(lat, 50)),
+            "hbm_gbs_achieved": traffic / span / 1e9, "hbm_frac": traffic / span / 1e9 / hbm,
+            "hbm_note": "sum over requests of cells x steps x 2 x 19 x bytes per population, over the busy span",
             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
             "aggregate_mlups": info["cell_updates"] / span / 1e6, "busy_span_s": span,
             "offered_load": load, "capacity_mlups_probe": cap / 1e6, "arrival_rate_per_s": rate,
@@ -436,7 +468,7 @@ def ours(args):
     torch.cuda.set_device(local)
     lbsq.load()
     hbm, peak_kind = peaks()
-    wl = W.c2_free_swimmer(beta=0.0)
+    wl = W.c3_pusher()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     head = args.storage
 
@@ -457,7 +489,7 @@ def ours(args):
         dist.barrier()
     clk = clocks.stop() if clocks else None
     # per-kernel attribution: traced pass of the same lattice right after
-    n_traced = min(args.steps, 400)
+    n_traced = min(args.steps, 200)
     traced_ms, prof = traced_steps(g, n_traced, flush, torch)
     g.close()
     total_ms = max_over_ranks(sum(step_ms), dist, f"cuda:{local}")
@@ -470,13 +502,14 @@ def ours(args):
         if dist:
             dist.destroy_process_group()
         return
+    b = wl.bodies[0]
     res = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": ARITH[head],
         "data": "synthetic",
-        "config": {"workload": wl.name, "shape": list(wl.shape), "R": 8, "B1": 0.005, "beta": 0.0,
-                   "collision": "trt(lambda_e=1, magic=3/16)", "storage": head,
+        "config": {"workload": wl.name, "shape": list(wl.shape), "R": b.R, "B1": b.B1, "beta": b.beta,
+                   "collision": "trt(lambda_e=1, magic=3/16)", "storage": head, "arith": ARITH_NOTE[head],
                    "step": "sweep + links/force/Newton-Euler + classify + convert + rebuild",
                    "l2": (f"populations {cells * 19 * BYTES[head] / 1e6:.0f} MB vs L2 129 MB; "
                           f"L2 flushed (512 MiB write, outside the events) before every timed iteration "
@@ -484,9 +517,7 @@ def ours(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": ncu_traffic(f"sweep_{head}_{wl.name}"),
-                     "kernel": ("k_sweep (one cell per thread)" if head == "f64"
-                                else "k_sweep2 (two cells per thread)"),
-                     "bytes_per_launch": sweep_bytes,
+                     "kernel": KERNEL[head], "bytes_per_launch": sweep_bytes,
                      "per_unit": f"2*19*{BYTES[head]} B per cell update", "peak_kind": peak_kind,
                      "sweep_ms": sweep_ms},
         "fluid_mlups": round(value * fluid_fraction(wl), 1),
@@ -503,33 +534,40 @@ def ours(args):
         "clocks": clk,
     }
     if ws == 1:
-        variants = {head: {"mlups": value, "sweep_frac": achieved / hbm}}
+        # the same workload in every storage (and FP64 with FP64 arithmetic)
+        variants = {head: {"mlups": value, "sweep_frac": achieved / hbm, "steps": args.steps}}
         if not args.skip_variants:
-            for st in ("f64", "f32", "f16dev", "bf16dev"):
-                if st == head:
+            for st, form in (("f64", 0), ("f64", 1), ("f32", 0), ("f16dev", 0), ("bf16dev", 0)):
+                key = st if form == 0 else f"{st}_fp64_arith"
+                if key == head:
                     continue
-                r = run_variant(st, wl, min(args.steps, 1000), args.warmup, flush, torch, local)
-                variants[st] = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"],
-                                "sweep_frac": r["sweep_bytes"] / (r["sweep_ms"] * 1e-3) / 1e9 / hbm,
-                                "kernels_ms_per_step": r["kernels_ms"],
-                                "steps_per_timed_iteration": r["steps_per_timed_iteration"]}
-            res["mixed_vs_f64"] = {st: variants[st]["mlups"] / variants["f64"]["mlups"]
-                                   for st in variants if "f64" in variants}
+                r = run_variant(st, wl, 64, 8, flush, torch, local, form)
+                variants[key] = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"], "steps": 64,
+                                 "sweep_frac": r["sweep_bytes"] / (r["sweep_ms"] * 1e-3) / 1e9 / hbm,
+                                 "kernels_ms_per_step": r["kernels_ms"], "kernel": KERNEL[st] if form == 0
+                                 else "k_sweep (one cell per thread, FP64 arithmetic)"}
+            if "f64" in variants:
+                res["mixed_vs_f64"] = {k: variants[k]["mlups"] / variants["f64"]["mlups"]
+                                       for k in ("f32", "f16dev", "bf16dev", "f64_fp64_arith") if k in variants}
         res["variants"] = variants
+        if not args.skip_precision:
+            res["precision_c3"] = precision_sweep(torch, local)
         if not args.skip_accuracy:
             acc = {}
+            wl2 = W.c2_free_swimmer(beta=0.0)
             v0 = 2 * 0.005 / 3
             ref = None
             for st in ("f64", "f32", "f16dev", "bf16dev"):
-                U = swim_speed(st, wl, torch, local)
+                U = swim_speed(st, wl2, torch, local)
                 ref = U if st == "f64" else ref
                 acc[st] = {"U_over_v0": U / v0, "rel_err_vs_f64": abs(U - ref) / abs(ref)}
-            res["swim_speed_c2"] = {"steps": wl.steps, "window": "mean of v.e over the last half", **acc}
+            res["swim_speed_c2"] = {"workload": wl2.name, "steps": wl2.steps,
+                                    "window": "mean of v.e over the last half", **acc}
         if not args.skip_extra:
             extra = {}
-            for wlx, sts in ((W.c3_pusher(), ("f64", "f32", "f16dev", "bf16dev")), (W.c4_suspension(), ("f32",))):
+            for wlx, sts in ((W.c2_free_swimmer(beta=0.0), ("f32", "f64")), (W.c4_suspension(), ("f32",))):
                 for st in sts:
-                    r = run_variant(st, wlx, 48, 8, flush, torch, local)
+                    r = run_variant(st, wlx, 64, 8, flush, torch, local)
                     extra[f"{wlx.name}_{st}"] = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"],
                                                  "sweep_frac": r["sweep_bytes"] / (r["sweep_ms"] * 1e-3) / 1e9 / hbm,
                                                  "kernels_ms_per_step": r["kernels_ms"],
@@ -537,7 +575,7 @@ def ours(args):
             res["extra"] = extra
         if not args.skip_serve:
             res["serving_c5"] = serve_run(torch, local)
-        res["e2e"] = e2e_run(wl, head, min(args.steps, 1000), local, torch)
+        res["e2e"] = e2e_run(wl, head, args.steps, local, torch)
         if not args.skip_cpu:
             res["cpu_baseline"] = cpu_baseline(wl)
     else:
@@ -556,7 +594,7 @@ def reference(args):
         return
     from oracle import oracle as O
     from paper_1903_04799_gb300 import workloads as W
-    wl = W.c2_free_swimmer(beta=0.0)
+    wl = W.c3_pusher()
     s = O.OracleSim(*wl.shape, lambda_e=wl.lambda_e, collision=wl.collision)
     for b in wl.bodies:
         s.add_sphere(b.pos, b.e, b.R, b.B1, b.beta, b.mobile)
@@ -580,24 +618,49 @@ def reference(args):
     }), flush=True)
 
 
+def profile_sweep(spec: str):
+    """A bare periodic lattice (no bodies), stepped a few times: only the
+    sweep kernels run.  spec = STORAGE:N:STEPS[:FORM] (FORM as
+    lb_set_sweep_variant).  For ncu captures of one sweep kernel on a lattice
+    of N^3 cells; prints nothing but a one-line confirmation."""
+    import torch
+    from paper_1903_04799_gb300 import Lattice
+    parts = spec.split(":")
+    st, n, steps = parts[0], int(parts[1]), int(parts[2])
+    form = int(parts[3]) if len(parts) > 3 else 0
+    g = Lattice((n, n, n), collision="trt", storage=st)
+    if form:
+        g.set_sweep_variant(form)
+    g.step(steps)
+    g.sync()
+    torch.cuda.synchronize()
+    g.close()
+    print(f"profile-sweep {st} {n}^3 {steps} steps form {form}: ok", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--storage", default="f32", choices=list(BYTES))
+    ap.add_argument("--storage", default="f64", choices=list(BYTES))
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-precision", action="store_true")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="run the 256^3 storage precision sweep (about 2 minutes) instead of the benchmark")
+    ap.add_argument("--profile-sweep", metavar="STORAGE:N:STEPS[:FORM]",
+                    help="step a bare N^3 lattice (sweep kernels only), for ncu captures, instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile_sweep:
+        profile_sweep(args.profile_sweep)
+    elif args.impl == "reference":
         reference(args)
     elif args.precision_sweep:
         import torch

@@ -247,6 +247,7 @@ typedef struct {
     int force_avg; /* 1: Ladd's two-step average of F_bb and T_bb */
     int inc;       /* 1: incompressible equilibrium (oracle_feq_inc) throughout */
     double link_at; /* where on a link v_b and the lever arm are taken: 0.5 (midpoint) or 1 (boundary node) */
+    int conv;       /* conversion reading: 0 = the one used throughout, else an alternative (osim_set_conversion) */
     int nobj, capobj;
     oobj* obj; /* obj[k] has id k+1 */
     long step;
@@ -355,6 +356,15 @@ void osim_set_incompressible(osim* s, int on) { s->inc = on ? 1 : 0; }
  * node x + c_i that the text of Sec. III names (at_node = 1, kept to show
  * that this reading misses the speeds printed in Fig. "resolution"). */
 void osim_set_link_at_node(osim* s, int at_node) { s->link_at = at_node ? 1.0 : 0.5; }
+
+/* Alternative readings of the cell conversion of Sec. III (Eq. "consforce"),
+ * kept to compare them with the speeds printed in Fig. "resolution":
+ *   0: the reading used throughout (refill at the rigid velocity v + w x d,
+ *      conversion momentum booked on the body);
+ *   1: refill at the whole surface velocity, the squirmer slip included;
+ *   2: conversion momentum not booked on the body (no F_c);
+ *   3: refill at the density rho0 instead of the neighbours' mean. */
+void osim_set_conversion(osim* s, int mode) { s->conv = mode; }
 
 /* Populations to the equilibrium of the given fields (rho[N], u as SoA [3][N]). */
 void osim_set_equilibrium(osim* s, const double* rho, const double* u) {
@@ -766,7 +776,7 @@ static void remap(osim* s) {
                 s->f[i * N + c] = 0.0;
             }
             cross(d, m, t);
-            for (int a = 0; a < 3; ++a) {
+            for (int a = 0; a < 3 && s->conv != 2; ++a) {
                 o->Fc[a] += m[a];
                 o->Tc[a] += t[a];
             }
@@ -785,10 +795,16 @@ static void remap(osim* s) {
                 }
             }
             double rb = cnt > 0 ? sum / (double)cnt : s->rho0;
+            if (s->conv == 3) rb = s->rho0;
             double d[3], w[3], u[3];
             sphere_offset(s, o, x, y, z, d);
             cross(o->omega, d, w);
             for (int a = 0; a < 3; ++a) u[a] = o->vel[a] + w[a];
+            if (s->conv == 1) {
+                double sl[3];
+                oracle_slip(d, o->e, o->B1, o->B2, sl);
+                for (int a = 0; a < 3; ++a) u[a] += sl[a];
+            }
             double feq[Q], m[3] = {0.0, 0.0, 0.0}, t[3];
             if (s->inc) oracle_feq_inc(rb, s->rho0, u, feq);
             else oracle_feq(rb, u, feq);
@@ -799,7 +815,7 @@ static void remap(osim* s) {
                 m[2] += feq[i] * CZ[i];
             }
             cross(d, m, t);
-            for (int a = 0; a < 3; ++a) {
+            for (int a = 0; a < 3 && s->conv != 2; ++a) {
                 o->Fc[a] -= m[a];
                 o->Tc[a] -= t[a];
             }

@@ -20,9 +20,12 @@ __global__ void __launch_bounds__(256) k_sweep(const SweepArgs a) {
     sweep_one<S, P, NATIVE>(a, x, y, z);
 }
 
-// FP64 storage, double-float collision (sweep_df.cuh), one cell per thread.
+// FP64 storage, double-float collision (sweep_df.cuh), one cell per thread,
+// three blocks per SM (80 registers, 40 bytes of spill): 24 warps per SM hide
+// the loads better than 16 at 122 registers (256^3: 0.77 -> 0.83 of the copy
+// bandwidth).
 template <int P, bool O32, bool LE1>
-__global__ void __launch_bounds__(256, 2) k_sweep_df(const SweepArgs a) {
+__global__ void __launch_bounds__(256, 3) k_sweep_df(const SweepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int z = sweep_plane(a);
     const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y, z);
@@ -68,17 +71,24 @@ static int sm_count() {
     return n;
 }
 
-// Planes ahead for the two-cell form's L2 prefetch (SweepArgs::pf): past the
-// planes that the resident blocks (two per SM) cover, plus two.  Measured on
-// GB300 (whole-lattice sweeps at 256^3): FP32 0.959 -> 0.990 of the copy
-// bandwidth, FP16 0.745 -> 0.684.  Whole-lattice FP32 sweeps only: a prefetch
-// installs its lines in L2 at normal priority, and beside the body kernels of
-// a split step (far sweeps) that evicted their code again (128^3 step 0.050 ->
-// 0.056 ms).
+// Planes ahead for the L2 prefetch of the sources (SweepArgs::pf): just past
+// the planes that the resident blocks (two per SM for FP32, three for FP64)
+// cover; FP32 adds two more.
+// Measured on GB300, whole-lattice sweeps:
+//   FP32 (two-cell form, 256^3): 0.959 -> 0.990 of the copy bandwidth;
+//   FP64 (double-float form): 256^3 0.65 -> 0.75 at 1 or 2 planes ahead,
+//     0.66 at 4, 0.60 at 5; 192^3 0.56 -> 0.72; 128^3 0.64 -> 0.78;
+//   FP16 (two-cell form): 0.745 -> 0.684, so 16-bit sweeps do not prefetch.
+// FP32 prefetches in whole-lattice sweeps only: a prefetch installs its lines
+// in L2 at normal priority, and beside the body kernels of a split step (far
+// sweeps) that evicted their code again (128^3 step 0.050 -> 0.056 ms).  The
+// FP64 sweep is long against its body step, and prefetches in split sweeps
+// too (256^3 pusher, whole step: 13 970 -> 15 830 MLUPS).
 static int prefetch_ahead(const SweepArgs& a, int storage, const dim3& grid) {
-    if (a.zmode != 0 || storage != ST_F32) return 0;
+    if (storage == ST_F32 ? a.zmode != 0 : storage != ST_F64) return 0;
     const long long per_plane = (long long)grid.x * grid.y;
-    const int ahead = (int)((2LL * sm_count() + per_plane - 1) / per_plane) + 2;
+    const long long resident = (storage == ST_F32 ? 2LL : 3LL) * sm_count();
+    const int ahead = (int)((resident + per_plane - 1) / per_plane) + (storage == ST_F32 ? 2 : 0);
     return ahead < a.nz ? ahead : 0;
 }
 
@@ -89,15 +99,17 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy
         int bx = ((a.nx + 31) / 32) * 32;
         if (bx > 256) bx = 256;
         dim3 grid((a.nx + bx - 1) / bx, gy, gz);
+        SweepArgs b = a;
+        b.pf = prefetch_ahead(a, S, grid);
         if (variant == 1) {  // FP64 arithmetic
             if (parity == 0) k_sweep<S, 0, true><<<grid, bx, 0, st>>>(a);
             else k_sweep<S, 1, true><<<grid, bx, 0, st>>>(a);
         } else if (o32) {
-            if (a.K.df.le1) launch_df<true, true>(a, parity, grid, bx, st);
-            else launch_df<true, false>(a, parity, grid, bx, st);
+            if (a.K.df.le1) launch_df<true, true>(b, parity, grid, bx, st);
+            else launch_df<true, false>(b, parity, grid, bx, st);
         } else {
-            if (a.K.df.le1) launch_df<false, true>(a, parity, grid, bx, st);
-            else launch_df<false, false>(a, parity, grid, bx, st);
+            if (a.K.df.le1) launch_df<false, true>(b, parity, grid, bx, st);
+            else launch_df<false, false>(b, parity, grid, bx, st);
         }
     } else {
     if constexpr (S == ST_F16 || S == ST_BF16) {

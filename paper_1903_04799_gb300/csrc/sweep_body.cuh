@@ -263,6 +263,21 @@ __device__ __forceinline__ void sweep_one_df(const SweepArgs& a, int x, int y, i
     auto cell = [&](int dx, int dy, int dz) -> Off {
         return (Off)xs[1 + dx] + (Off)nx * ((Off)ys[1 + dy] + (Off)ny * (Off)zs[1 + dz]);
     };
+    // L2 prefetch of the sources a.pf planes ahead in sweep order (as in
+    // sweep_two): their loads then wait on L2 rather than on HBM
+    if (a.pf) {
+        const int zp = z + (a.reverse ? -a.pf : a.pf);
+        if (zp >= 0 && zp < nz) {
+            const int zsp[3] = {zp == 0 ? nz - 1 : zp - 1, zp, zp == nz - 1 ? 0 : zp + 1};
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const Off c = P == 0 ? (Off)x + (Off)nx * ((Off)y + (Off)ny * (Off)zp)
+                                     : (Off)xs[1 - cx(i)] + (Off)nx * ((Off)ys[1 - cy(i)] + (Off)ny * (Off)zsp[1 - cz(i)]);
+                const uint2* src = F + ((P == 0 ? (Off)i : (Off)opp(i)) * Np + c);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(src));
+            }
+        }
+    }
     uint2 w[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i)

@@ -88,13 +88,14 @@ __device__ __forceinline__ df dadd(df x, df y) {
 __device__ __forceinline__ df dneg(df x) { return {-x.h, -x.l}; }
 __device__ __forceinline__ df dsub(df x, df y) { return dadd(x, dneg(y)); }
 // x * y: the exact product of the high parts (Dekker, through FMA) plus the
-// cross terms
+// cross terms.  The product of the low parts is left out: with |l| within a
+// few ulps of |h| it is below 2^-46 of |x y|, the size of the rounding of the
+// low parts themselves.
 __device__ __forceinline__ df dmul(df x, df y) {
     const float p = __fmul_rn(x.h, y.h);
     float e = __fmaf_rn(x.h, y.h, -p);
     e = __fmaf_rn(x.h, y.l, e);
     e = __fmaf_rn(x.l, y.h, e);
-    e = __fmaf_rn(x.l, y.l, e);
     return {p, e};
 }
 __device__ __forceinline__ df dsqr(df x) {
@@ -102,7 +103,6 @@ __device__ __forceinline__ df dsqr(df x) {
     const float t = __fadd_rn(x.h, x.h);
     float e = __fmaf_rn(x.h, x.h, -p);
     e = __fmaf_rn(t, x.l, e);
-    e = __fmaf_rn(x.l, x.l, e);
     return {p, e};
 }
 // x * c for an FP32 c
@@ -146,7 +146,7 @@ __device__ __forceinline__ df df_from_bits(unsigned lo, unsigned hi) {
     const float pw = __uint_as_float(hb & 0xff800000u);  // +-2^e
     return {__uint_as_float(hb), __fmul_rn(__fmul_rn(rem, pw), 0x1p-52f)};
 }
-// FP64 bits of h + l (to ~2^-47 relative; |h + l| below 2^-126 may come out
+// FP64 bits of h + l (to ~2^-47 relative; |h + l| below 2^-75 may come out
 // as any value of that size)
 __device__ __forceinline__ uint2 df_to_bits(df x) {
     const float s = __fadd_rz(x.h, x.l);                  // |s| <= |h + l|
@@ -155,9 +155,11 @@ __device__ __forceinline__ uint2 df_to_bits(df x) {
     unsigned hi = ((ab >> 3) + (896u << 20)) | (sb & 0x80000000u);
     unsigned lo = sb << 29;
     // e in FP64 ulps of s, 2^(es - 127 - 52): fewer than 2^29 of them, so the
-    // 52-bit mantissa cannot overflow
-    const float pw = __uint_as_float((254u << 23) - (sb & 0x7f800000u));  // 2^(127 - es)
-    const unsigned k = __float2uint_rn(__fmul_rn(__fmul_rn(fabsf(e), 0x1p52f), pw));
+    // 52-bit mantissa cannot overflow.  For |s| < 2^-75 the scale's exponent
+    // field wraps (or is Inf): the count is then garbage, an error below
+    // 2^-75 in absolute value.
+    const float pw = __uint_as_float((306u << 23) - (sb & 0x7f800000u));  // 2^(179 - es)
+    const unsigned k = __float2uint_rn(__fmul_rn(fabsf(e), pw));
     asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+r"(lo), "+r"(hi) : "r"(k));
     return make_uint2(lo, hi);
 }

@@ -632,33 +632,43 @@ def test_two_step_force_average_momentum_invariant():
     assert worst > 1e-6
 
 
-def _swim_speed_R4(at_node=False):
-    R, L, B1 = 4, 40, 0.01
+def _swim_speed_R4(at_node=False, steps=3000):
+    """v.e / v0 of a free squirmer R = 4 in a periodic box L = 40 (L = 10R),
+    sampled every step; B1 = 0.001 (Reynolds number 2 v0 R / nu = 0.032: the
+    paper does not print B1, and its speeds are those of the Stokes limit)."""
+    R, L, B1 = 4, 40, 0.001
     s = O.OracleSim(L, L, L, lambda_e=1.0, collision="trt")
     if at_node:
         s.set_link_at_node(True)
     oid = s.add_sphere((L / 2 + 0.1, L / 2 + 0.2, L / 2), (0, 0, 1), R, B1=B1, beta=0.0)
     vs = []
-    for k in range(1500):
+    for _ in range(steps):
         s.step(1)
-        if k >= 750:
-            _, v, e, _ = s.state(oid)
-            vs.append(v @ e)
-    return np.mean(vs) / (2 * B1 / 3)
+        _, v, e, _ = s.state(oid)
+        vs.append(v @ e)
+    return np.array(vs) / (2 * B1 / 3)
 
 
 def test_swim_speed_matches_fig_resolution():
     """Eq. "squirmer-speed" and Fig. "resolution": a free squirmer of R = 4 in a
     periodic box L = 10R swims at the speed the paper prints, 0.9737 v0
-    (v0 = 2 B1 / 3), within 1.5%.  Taking the wall velocity and lever arm at
-    the boundary node, as the text of Sec. III words it, instead of the link
-    midpoint misses the printed speed by far more."""
+    (v0 = 2 B1 / 3).  The speed is taken at steady state: the mean over steps
+    1500 .. 3000 (the viscous time L^2 / nu is 9600 steps, but the speed is
+    set by the flow near the sphere, which settles within R^2 / nu ~ 100
+    steps; the means over the two halves of the window agree within 1 %, and
+    over steps 3000 .. 12000 the oracle gives 0.9739 too).  Within 0.5 %.
+    Taking the wall velocity and lever arm at the boundary node, as the text
+    of Sec. III words it, instead of the link midpoint gives 1.113 at steady
+    state, more than 10 % too fast."""
     rows = np.loadtxt(os.path.join(GOLDEN, "fig_resolution_squirmer.txt"))
     ref = rows[(rows[:, 0] == 4) & (rows[:, 1] == 10)][0, 2]
-    ratio = _swim_speed_R4()
-    assert abs(ratio / ref - 1) < 0.015, ratio
-    node = _swim_speed_R4(at_node=True)
-    assert abs(node / ref - 1) > 0.08, node
+    v = _swim_speed_R4()
+    first, second = v[1500:2250].mean(), v[2250:3000].mean()
+    assert abs(first - second) < 0.01, (first, second)
+    ratio = v[1500:].mean()
+    assert abs(ratio / ref - 1) < 0.005, ratio
+    node = _swim_speed_R4(at_node=True)[1500:].mean()
+    assert abs(node / ref - 1) > 0.10, node
 
 
 def _periodic_drag_ratio(R, L, off, steps, g=1e-7):
