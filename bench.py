@@ -431,6 +431,58 @@ def precision_sweep(torch, device=0, steps=None):
             "stresslet_zz_closed_form": S_closed, "v0": v0, "storages": out}
 
 
+def oscillation_of(y, z, L):
+    """Amplitude and period of an oscillating lateral displacement y(t): the
+    mean |y| at the turning points (local extrema that alternate in sign) and
+    the mean spacing of every other turning point, in steps and in distance
+    travelled along the periodic axis of length L (z unwrapped).  None with
+    fewer than three turning points."""
+    y = np.asarray(y, float)
+    dz = np.diff(np.asarray(z, float))
+    dz[dz < -L / 2] += L
+    dz[dz > L / 2] -= L
+    zu = np.concatenate([[0.0], np.cumsum(dz)])
+    ext = []
+    for k in range(1, len(y) - 1):
+        if (y[k] - y[k - 1]) * (y[k + 1] - y[k]) < 0 and (not ext or np.sign(y[k]) != np.sign(y[ext[-1]])):
+            ext.append(k)
+    if len(ext) < 3:
+        return None
+    ext = np.array(ext)
+    return {"amplitude": float(np.abs(y[ext]).mean()), "period_samples": float((ext[2:] - ext[:-2]).mean()),
+            "period_travel": float(np.mean(zu[ext[2:]] - zu[ext[:-2]])), "turning_points": int(len(ext))}
+
+
+def tube_run(torch, device=0, storage="f32", sample=200):
+    """Sec. V tube flow: the neutral squirmer (R = 9) in the round tube
+    D = 20R/3, L = 3 pi R, started parallel to the axis at y0 = -R; its
+    lateral displacement sampled every `sample` steps; amplitude and period
+    of the oscillation (both in units of R)."""
+    from paper_1903_04799_gb300 import workloads as W
+    t = W.tube_oscillation()
+    b = t.body
+    g = build_lattice(storage, t.shape, [], "trt", 1.0, device)[0]
+    g.add_round_tube(t.axis[0], t.axis[1], t.radius)
+    gi = g.add_squirmer(b.pos, b.e, b.R, b.B1, b.beta, mobile=True)
+    g.set_contact(*t.contact)
+    ys, zs, t0 = [], [], time.perf_counter()
+    for _ in range(0, t.steps, sample):
+        g.step(sample)
+        p = g.state(gi)[0]
+        ys.append(float(p[1] - t.axis[1]))  # the squirmer stays in the plane x = axis (mirror symmetry)
+        zs.append(float(p[2]))
+    wall = time.perf_counter() - t0
+    g.close()
+    osc = oscillation_of(ys, zs, t.shape[2])
+    out = {"workload": t.name, "storage": storage, "steps": t.steps, "B1": b.B1, "wall_s": wall,
+           "mlups": t.cells * t.steps / wall / 1e6, "y_over_R_first_last": [ys[0] / b.R, ys[-1] / b.R],
+           "closest_wall_gap_over_R": float((t.radius - 0.5 - b.R - np.max(np.abs(ys))) / b.R)}
+    if osc:
+        out.update({"amplitude_over_R": osc["amplitude"] / b.R, "period_steps": osc["period_samples"] * sample,
+                    "wavelength_over_R": osc["period_travel"] / b.R, "turning_points": osc["turning_points"]})
+    return out
+
+
 def max_over_ranks(x: float, dist, device) -> float:
     """x maximised over all ranks (a replica job takes as long as its slowest
     rank); x itself without a process group."""
@@ -573,6 +625,8 @@ def ours(args):
                                                  "kernels_ms_per_step": r["kernels_ms"],
                                                  "steps_per_timed_iteration": r["steps_per_timed_iteration"]}
             res["extra"] = extra
+        if not args.skip_tube:
+            res["tube_oscillation"] = tube_run(torch, local)
         if not args.skip_serve:
             res["serving_c5"] = serve_run(torch, local)
         res["e2e"] = e2e_run(wl, head, args.steps, local, torch)
@@ -651,6 +705,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-precision", action="store_true")
+    ap.add_argument("--skip-tube", action="store_true")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="run the 256^3 storage precision sweep (about 2 minutes) instead of the benchmark")
     ap.add_argument("--profile-sweep", metavar="STORAGE:N:STEPS[:FORM]",

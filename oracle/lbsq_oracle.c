@@ -248,6 +248,7 @@ typedef struct {
     int inc;       /* 1: incompressible equilibrium (oracle_feq_inc) throughout */
     double link_at; /* where on a link v_b and the lever arm are taken: 0.5 (midpoint) or 1 (boundary node) */
     int conv;       /* conversion reading: 0 = the one used throughout, else an alternative (osim_set_conversion) */
+    int local_rho;  /* 1: the bounce-back shift takes the density of the fluid node instead of rho0 */
     int nobj, capobj;
     oobj* obj; /* obj[k] has id k+1 */
     long step;
@@ -356,6 +357,12 @@ void osim_set_incompressible(osim* s, int on) { s->inc = on ? 1 : 0; }
  * node x + c_i that the text of Sec. III names (at_node = 1, kept to show
  * that this reading misses the speeds printed in Fig. "resolution"). */
 void osim_set_link_at_node(osim* s, int at_node) { s->link_at = at_node ? 1.0 : 0.5; }
+
+/* The density in the shift 6 w_i rho c_i.v_b of the moving-wall bounce-back
+ * (Sec. III leaves it open): rho0 (on = 0, Ladd's original, the default) or
+ * the density of the fluid node the link leaves (on = 1), the sum of its
+ * post-collision populations. */
+void osim_set_local_density(osim* s, int on) { s->local_rho = on ? 1 : 0; }
 
 /* Alternative readings of the cell conversion of Sec. III (Eq. "consforce"),
  * kept to compare them with the speeds printed in Fig. "resolution":
@@ -624,7 +631,12 @@ static void bounce_links(osim* s) {
             boundary_velocity(s, o, cx, cy, cz, i, vb, d);
             double fout = s->fpost[i * N + n];
             double cv = CX[i] * vb[0] + CY[i] * vb[1] + CZ[i] * vb[2];
-            double fin = fout - 6.0 * WT[i] * s->rho0 * cv;
+            double rs = s->rho0;
+            if (s->local_rho) {
+                rs = 0.0;
+                for (int j = 0; j < Q; ++j) rs += s->fpost[j * N + n];
+            }
+            double fin = fout - 6.0 * WT[i] * rs * cv;
             s->fnew[opposite(i) * N + n] = fin;
             /* momentum exchange: c_i (f_out + f_in) goes to the body */
             double dF[3] = {CX[i] * (fout + fin), CY[i] * (fout + fin), CZ[i] * (fout + fin)};

@@ -77,6 +77,7 @@ def load_oracle():
             "osim_set_incompressible": (None, [C.c_void_p, C.c_int32]),
             "osim_set_link_at_node": (None, [C.c_void_p, C.c_int32]),
             "osim_set_conversion": (None, [C.c_void_p, C.c_int32]),
+            "osim_set_local_density": (None, [C.c_void_p, C.c_int32]),
             "osim_set_equilibrium": (None, [C.c_void_p, _DP, _DP]),
             "osim_set_populations": (None, [C.c_void_p, _DP]),
             "osim_get_populations": (None, [C.c_void_p, _DP]),
@@ -258,6 +259,10 @@ class OracleSim:
 
     def set_link_at_node(self, on: bool = True):
         self._lib.osim_set_link_at_node(self._h, 1 if on else 0)
+
+    def set_local_density(self, on: bool = True):
+        """The bounce-back shift with the fluid node's density (see osim_set_local_density)."""
+        self._lib.osim_set_local_density(self._h, 1 if on else 0)
 
     def set_conversion(self, mode: int):
         """Alternative readings of the cell conversion (see osim_set_conversion)."""

@@ -339,6 +339,9 @@ lb_status relayout(lb_ctx* c) {
         int64_t expect;
         if (b.kind == BODY_SPHERE) {
             expect = (int64_t)std::ceil(63.0 * b.R * b.R);  // about 5 links per node of 4 pi R^2
+        } else if (b.wall_axis < 0) {
+            // round tube: about 5 links per wall node of the circumference, on every plane
+            expect = (int64_t)std::ceil(5.0 * 6.2832 * b.tube[2]) * c->L.nz;
         } else {
             const int n3[3] = {c->L.nx, c->L.ny, c->L.nz};
             expect = 5 * (c->L.N / n3[b.wall_axis]);
@@ -574,6 +577,8 @@ void lb_params_default(lb_params* p) {
     p->device = 0;
     p->stream = nullptr;
     p->allocator = nullptr;
+    p->equilibrium = LB_EQ_COMPRESSIBLE;
+    p->rounding = LB_ROUND_DEFAULT;
 }
 
 lb_status lb_create(const lb_params* p, lb_ctx** out) {
@@ -586,6 +591,7 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     if (p->collision == LB_TRT && !(p->magic > 0.0)) return LB_ERR_INVALID;
     if (p->dev_scale_log2 < -1 || p->dev_scale_log2 > 40) return LB_ERR_INVALID;
     if (p->equilibrium != LB_EQ_COMPRESSIBLE && p->equilibrium != LB_EQ_INCOMPRESSIBLE) return LB_ERR_INVALID;
+    if (p->rounding < LB_ROUND_DEFAULT || p->rounding > LB_ROUND_STOCHASTIC) return LB_ERR_INVALID;
     lb_ctx* c = new (std::nothrow) lb_ctx();
     if (!c) return LB_ERR_OOM;
     c->p = *p;
@@ -624,7 +630,11 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     const int k = p->dev_scale_log2 < 0 ? 14 : p->dev_scale_log2;
     L.scale = p->storage == LB_F16DEV ? std::ldexp(1.0f, k) : 1.0f;
     L.inv_scale = 1.0f / L.scale;
+    L.sr = p->storage == LB_BF16DEV && p->rounding != LB_ROUND_NEAREST ? 1 : 0;
+    L.rho_local = 0;
+    L.link_at = 0.5f;
     L.F = dalloc(c, (size_t)Q * L.Np * storage_bytes(p->storage));
+    L.sr_ctr = dalloc_t<unsigned long long>(c, 2);
     c->own = dalloc_t<int32_t>(c, (size_t)N);
     c->own_prev = dalloc_t<int32_t>(c, (size_t)N);
     c->d_mass_part = dalloc_t<double>(c, (size_t)mass_partial_blocks(L) * 4);
@@ -654,7 +664,8 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
     if (upload_lattice(c) != LB_OK) return bail(LB_ERR_CUDA);
     if (cudaMemsetAsync(c->own, 0, sizeof(int32_t) * N, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->own_prev, 0, sizeof(int32_t) * N, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->d_err, 0, sizeof(int) * 2, c->stream) != cudaSuccess)
+        cudaMemsetAsync(c->d_err, 0, sizeof(int) * 2, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(L.sr_ctr, 0, sizeof(unsigned long long) * 2, c->stream) != cudaSuccess)
         return bail(LB_ERR_CUDA);
     launch_fill_rest(L, c->stream);
     c->launches += 1;
@@ -824,6 +835,20 @@ lb_status lb_set_contact(lb_ctx* c, double sigma, double eps) {
     c->wca_eps = eps;
     drop_graph(c);
     CK(cudaSetDevice(c->p.device));
+    lb_status s = upload_lattice(c);
+    if (s != LB_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_set_link_options(lb_ctx* c, int32_t density_of_node, int32_t velocity_at_node) {
+    if (!c || (density_of_node != 0 && density_of_node != 1) || (velocity_at_node != 0 && velocity_at_node != 1))
+        return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
+    c->L.rho_local = density_of_node;
+    c->L.link_at = velocity_at_node ? 1.0f : 0.5f;
+    drop_graph(c);
     lb_status s = upload_lattice(c);
     if (s != LB_OK) return s;
     CK(cudaStreamSynchronize(c->stream));
@@ -1311,7 +1336,7 @@ struct CkptHeader {
     char magic[8];
     uint32_t version, storage;
     int32_t nx, ny, nz, nbodies;
-    int32_t equilibrium, reserved;
+    int32_t equilibrium, reserved;  // reserved: Lattice::sr (the rounding of BF16 stores)
     double lambda_e, lambda_o, rho0;
     double scale;
     int64_t step;
@@ -1395,6 +1420,7 @@ lb_status lb_checkpoint(lb_ctx* c, void* buf, size_t bytes) {
     h.version = 3;  // 3: FP64 populations are stored as deviations f - w rho0
     h.storage = (uint32_t)c->p.storage;
     h.equilibrium = c->L.inc;
+    h.reserved = c->L.sr;  // rounding of the BF16 stores
     h.nx = c->L.nx;
     h.ny = c->L.ny;
     h.nz = c->L.nz;
@@ -1442,7 +1468,7 @@ lb_status lb_restore(lb_ctx* c, const void* buf, size_t bytes) {
     if (h.bytes != bytes) return fail(c, LB_ERR_INVALID, "checkpoint size differs from its header");
     if (h.storage != (uint32_t)c->p.storage || h.nx != c->L.nx || h.ny != c->L.ny || h.nz != c->L.nz ||
         h.lambda_e != c->lambda_e || h.lambda_o != c->lambda_o || h.rho0 != c->L.rho0 ||
-        h.scale != (double)c->L.scale || h.equilibrium != c->L.inc)
+        h.scale != (double)c->L.scale || h.equilibrium != c->L.inc || h.reserved != c->L.sr)
         return fail(c, LB_ERR_INVALID, "checkpoint of a lattice with other parameters");
     if (h.nbodies != (int32_t)c->par.size() || h.bodies_hash != bodies_hash(c))
         return fail(c, LB_ERR_INVALID, "checkpoint of other bodies (add the same bodies in the same order)");
@@ -1486,6 +1512,10 @@ lb_status lb_restore(lb_ctx* c, const void* buf, size_t bytes) {
             CK(cudaMemcpyAsync(c->d_links + c->par[k].link_off, b + 2 * sizeof(BodyState) + sizeof(BodyAcc),
                                sizeof(uint32_t) * nl, cudaMemcpyHostToDevice, c->stream));
     }
+    // the step count the sweeps keep for the stochastic rounding: the next
+    // sweep (of parity step & 1) reads it
+    const unsigned long long st = (unsigned long long)h.step;
+    CK(cudaMemcpyAsync(c->L.sr_ctr + (st & 1), &st, sizeof(st), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));  // the caller's buffer may go once we return
     c->step = h.step;
     c->pending = false;

@@ -202,11 +202,33 @@ __device__ __forceinline__ bool axis_overlap(int a, int wa, int b, int wb, int n
     return wrap_pos(b - a, n) < wa || wrap_pos(a - b, n) < wb;
 }
 
+// Whether a box (origin lo, extent w, in nodes), grown by g cells, can hold a
+// node that neighbours a wall node of round tube q: nodes at distance r or
+// more from the axis are wall, their lattice neighbours lie at r - sqrt(2) or
+// more (in the cross-section), so a box whose corners (grown) all lie within
+// r - 2 - g of the axis holds none.  Conservative: a box across the periodic
+// edge of the cross-section lies in the wall anyway.
+__device__ __forceinline__ bool box_meets_tube(const BodyParams& q, const int lo[3], const int w[3], int g) {
+    double far2 = 0.0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            const double dx = (double)(i ? lo[0] + w[0] - 1 + g : lo[0] - g) - q.tube[0];
+            const double dy = (double)(j ? lo[1] + w[1] - 1 + g : lo[1] - g) - q.tube[1];
+            far2 = fmax(far2, dx * dx + dy * dy);
+        }
+    const double rr = q.tube[2] - 2.0 - (double)g;
+    return rr <= 0.0 || far2 >= rr * rr;
+}
+__device__ __forceinline__ bool round_tube(const BodyParams& q) { return q.kind == BODY_WALL && q.wall_axis < 0; }
+
 __device__ __forceinline__ bool boxes_intersect(const Lattice& L, const BodyParams& pa, const BodyState& sa,
                                                 const BodyParams& pb, const BodyState& sb) {
     int la[3], wa[3], lb[3], wb[3];
     body_box(L, pa, sa, la, wa);
     body_box(L, pb, sb, lb, wb);
+    // a round tube's box is the whole lattice; its links sit along its wall
+    if (round_tube(pb) && !round_tube(pa)) return box_meets_tube(pb, la, wa, 0);
+    if (round_tube(pa) && !round_tube(pb)) return box_meets_tube(pa, lb, wb, 0);
     return axis_overlap(la[0], wa[0], lb[0], wb[0], L.nx) && axis_overlap(la[1], wa[1], lb[1], wb[1], L.ny) &&
            axis_overlap(la[2], wa[2], lb[2], wb[2], L.nz);
 }
@@ -494,6 +516,35 @@ __device__ __noinline__ void update_body(const Lattice& L, const Bodies& B, int 
 // solid it adds exactly zero to the force, the torque and the stresslet (each
 // solid-solid neighbour pair cancels).  Walls keep it (a wall's force
 // includes the rest pressure) and have no torque or stresslet.
+// Density of fluid node n = (x, y, z) from the post-collision populations
+// sweep P left: P = 0 in F[j][n] for every j, P = 1 in F[j][n + c_j].  The
+// link work writes only slots that solid cells' sweeps produced, so these are
+// stable while the links run.  FP64 storage sums in FP64, reduced storages in
+// FP32 (their own precision), both plus rho0.
+template <int P>
+__device__ __noinline__ double post_density(const Lattice& L, int64_t n, int x, int y, int z) {
+    if (L.storage == ST_F64) {
+        double r = 0.0;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int64_t c = P == 0 ? n
+                                     : cell_index(L, step_wrap(x, cx(j), L.nx), step_wrap(y, cy(j), L.ny),
+                                                  step_wrap(z, cz(j), L.nz));
+            r += ((const double*)L.F)[(int64_t)j * L.Np + c];
+        }
+        return L.rho0 + r;
+    }
+    float r = 0.0f;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int64_t c = P == 0 ? n
+                                 : cell_index(L, step_wrap(x, cx(j), L.nx), step_wrap(y, cy(j), L.ny),
+                                              step_wrap(z, cz(j), L.nz));
+        r += load_dev(L, (int64_t)j * L.Np + c);
+    }
+    return L.rho0 + (double)r;
+}
+
 template <int P, bool DP>
 __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p, const BodyState& s, long long cnt,
                                            const uint32_t* links, int g, int G, double (&acc)[12]) {
@@ -512,7 +563,7 @@ __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p
             w32[a] = (float)s.omega[a];
         }
     }
-    const float B1f = (float)p.B1, B2f = (float)p.B2, shf = (float)(6.0 * L.rho0);
+    const float B1f = (float)p.B1, B2f = (float)p.B2, shf0 = (float)(6.0 * L.rho0), lat = L.link_at;
     // A thread's links are taken kU at a time: the link codes, then the
     // outgoing populations of all kU are loaded before any arithmetic or
     // store, so their memory latencies overlap.
@@ -555,10 +606,11 @@ __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p
             const double fout = fouts[u];
             double vb[3], d[3];
             if (sphere) {
-                // link midpoint relative to the centre; rigid motion + slip there
-                d[0] = min_image(((double)x + 0.5 * ci[0]) - s.pos[0], L.nx);
-                d[1] = min_image(((double)y + 0.5 * ci[1]) - s.pos[1], L.ny);
-                d[2] = min_image(((double)z + 0.5 * ci[2]) - s.pos[2], L.nz);
+                // link midpoint (or boundary node) relative to the centre; rigid motion + slip there
+                const double la = (double)L.link_at;
+                d[0] = min_image(((double)x + la * ci[0]) - s.pos[0], L.nx);
+                d[1] = min_image(((double)y + la * ci[1]) - s.pos[1], L.ny);
+                d[2] = min_image(((double)z + la * ci[2]) - s.pos[2], L.nz);
                 const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                 double sl[3] = {0.0, 0.0, 0.0};
                 if (r2 > 0.0) {
@@ -577,7 +629,8 @@ __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p
                 for (int a = 0; a < 3; ++a) vb[a] = p.wall_vel[a];
             }
             const double cv = csel(ci[0], vb[0]) + csel(ci[1], vb[1]) + csel(ci[2], vb[2]);
-            const double fin = fout - 6.0 * L.rho0 * wgt(i) * cv;
+            const double rs = L.rho_local ? post_density<P>(L, n, x, y, z) : L.rho0;
+            const double fin = fout - 6.0 * rs * wgt(i) * cv;
             store_abs(L, in_slot, ib, fin);
             // momentum given to the body, c_i (f_out + f_in); torque, stresslet
             const double sf = fout + fin;
@@ -604,7 +657,7 @@ __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p
             const int xi[3] = {x, y, z};
             const int n3[3] = {L.nx, L.ny, L.nz};
             for (int a = 0; a < 3; ++a) {
-                float t = (float)(xi[a] - ip[a]) + (0.5f * (float)ci[a] - fp[a]);
+                float t = (float)(xi[a] - ip[a]) + (lat * (float)ci[a] - fp[a]);
                 const float h = 0.5f * (float)n3[a];
                 if (t > h) t -= (float)n3[a];
                 else if (t <= -h) t += (float)n3[a];
@@ -627,6 +680,7 @@ __device__ __forceinline__ void link_terms(const Lattice& L, const BodyParams& p
             const float cv = (ci[0] > 0 ? vb0 : (ci[0] < 0 ? -vb0 : 0.0f)) +
                              (ci[1] > 0 ? vb1 : (ci[1] < 0 ? -vb1 : 0.0f)) +
                              (ci[2] > 0 ? vb2 : (ci[2] < 0 ? -vb2 : 0.0f));
+            const float shf = L.rho_local ? (float)(6.0 * post_density<P>(L, n, x, y, z)) : shf0;
             const float gin = gout - shf * (float)wgt(i) * cv;
             store_dev(L, in_slot, gin);
             const float sf = gout + gin;
@@ -1317,6 +1371,8 @@ __device__ __forceinline__ bool boxes_near(const Lattice& L, const BodyParams& p
     int la[3], wa[3], lb[3], wb[3];
     body_box(L, pa, sa, la, wa);
     body_box(L, pb, sb, lb, wb);
+    if (round_tube(pb) && !round_tube(pa)) return box_meets_tube(pb, la, wa, 2);
+    if (round_tube(pa) && !round_tube(pb)) return box_meets_tube(pa, lb, wb, 2);
     const int n3[3] = {L.nx, L.ny, L.nz};
     for (int a = 0; a < 3; ++a)
         if (!axis_overlap(la[a] - 1, wa[a] + 2, lb[a] - 1, wb[a] + 2, n3[a])) return false;

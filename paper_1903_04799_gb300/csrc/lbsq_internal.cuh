@@ -144,6 +144,15 @@ struct Lattice {
     int pad;
     const long long* gstep;      // server: global step counter (null for a context)
     long long stop_step;         // server: the lattice is stepped while *gstep < stop_step
+    long long start_step;        // server: the global step of the lattice's first step
+    int sr;                      // 1: BF16 stores of the sweeps round stochastically (lb_rounding)
+    int rho_local;               // 1: the bounce-back shift takes the fluid node's density, not rho0
+    float link_at;               // where on a link v_b and the lever arm are taken: 0.5 (midpoint) or 1 (node)
+    int pad2;
+    // context: the lattice's step count for the stochastic rounding, kept on
+    // the device by the sweeps themselves (ping-pong by parity: the sweep of
+    // step t reads [t & 1] = t and writes [1 - (t & 1)] = t + 1); null for a server
+    unsigned long long* sr_ctr;
 };
 
 // Whether a lattice takes part in the current step.

@@ -47,6 +47,7 @@ struct TileArgs {
 template <int P, int S>
 __device__ __forceinline__ void sweep_tile(const Lattice& L, const int4 tile) {
     const SweepArgs a = sweep_args(L, L.lambda_e, L.lambda_o);
+    const uint32_t skey = S == ST_BF16 ? sr_step_key(a) : 0u;  // the lattice's own step (global - start)
     const unsigned per_row = tile.w ? (unsigned)L.nx / 2 : (unsigned)L.nx;
     for (unsigned u = (unsigned)tile.y + threadIdx.x; u < (unsigned)tile.z; u += blockDim.x) {
         const unsigned r = u / per_row;
@@ -54,11 +55,11 @@ __device__ __forceinline__ void sweep_tile(const Lattice& L, const int4 tile) {
         const int y = (int)(r % (unsigned)L.ny), z = (int)(r / (unsigned)L.ny);
         if constexpr (S != ST_F64) {
             if (tile.w) {
-                sweep_two<S, P>(a, 2 * xi, y, z);
+                sweep_two<S, P>(a, 2 * xi, y, z, skey);
                 continue;
             }
         }
-        sweep_one<S, P>(a, xi, y, z);
+        sweep_one<S, P>(a, xi, y, z, skey);
     }
 }
 
@@ -437,6 +438,11 @@ lb_status admit(lb_server* s, int l, const Queued& q) {
     L.active = 0;  // not stepped until set up
     L.gstep = s->d_gstep;
     L.stop_step = s->gstep + r.steps;
+    L.start_step = s->gstep;
+    L.rho_local = 0;
+    L.link_at = 0.5f;
+    L.sr = r.storage == LB_BF16DEV ? 1 : 0;  // the default rounding of BF16 storage (lb_rounding)
+    L.sr_ctr = nullptr;
     std::vector<BodyState> st;
     std::vector<BodyParams> bodies = request_bodies(r, st);
     L.body_count = (int)bodies.size();

@@ -13,11 +13,12 @@ namespace lbsq {
 
 template <int S, int P, bool NATIVE>
 __global__ void __launch_bounds__(256) k_sweep(const SweepArgs a) {
+    const uint32_t skey = S == ST_BF16 ? sr_step_key(a) : 0u;  // before any exit (see sr_step)
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int z = sweep_plane(a);
     const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y, z);
     if (x >= a.nx || y < 0) return;
-    sweep_one<S, P, NATIVE>(a, x, y, z);
+    sweep_one<S, P, NATIVE>(a, x, y, z, skey);
 }
 
 // FP64 storage, double-float collision (sweep_df.cuh), one cell per thread,
@@ -41,11 +42,12 @@ static void launch_df(const SweepArgs& a, int parity, const dim3& grid, int bx, 
 
 template <int S, int P, bool O32>
 __global__ void __launch_bounds__(256, 2) k_sweep2(const SweepArgs a) {
+    const uint32_t skey = S == ST_BF16 ? sr_step_key(a) : 0u;  // before any exit (see sr_step)
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int z = sweep_plane(a);
     const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
     if (x0 >= a.nx || y < 0) return;
-    sweep_two<S, P, O32>(a, x0, y, z);
+    sweep_two<S, P, O32>(a, x0, y, z, skey);
 }
 
 // 16-bit storages with nx % 4 == 0, nx <= 768: blocks of whole rows, four
@@ -54,10 +56,11 @@ __global__ void __launch_bounds__(256, 2) k_sweep2(const SweepArgs a) {
 template <int S, int P, bool O32>
 __global__ void __launch_bounds__(P == 0 ? 256 : 192, 2) k_sweep4r(const SweepArgs a) {
     extern __shared__ unsigned short rowbuf[];
+    const uint32_t skey = S == ST_BF16 ? sr_step_key(a) : 0u;  // before any exit (see sr_step)
     const int z = sweep_plane(a);
     if (z < 0) return;  // the whole block
     const int y = sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
-    sweep_four_rows<S, P, O32>(a, y < 0 ? 0 : y, z, y >= 0, rowbuf);
+    sweep_four_rows<S, P, O32>(a, y < 0 ? 0 : y, z, y >= 0, rowbuf, skey);
 }
 
 static int sm_count() {
@@ -174,6 +177,7 @@ void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity
     a.zmode = zmode;
     a.win = win;
     a.reverse = parity;
+    a.sr_writer = zmode != 2;  // of a split step's two sweeps, the far one advances the step counter
     if (gz <= 0 || gy <= 0) return;
     switch (L.storage) {
         case ST_F64: launch_s<ST_F64>(a, parity, variant, gz, gy, st); break;

@@ -50,6 +50,10 @@ struct SweepArgs {
     int64_t Np;
     double lambda_e, lambda_o, rho0;
     float scale, inv_scale;
+    // rho0 in FP32 and in the 16-bit storages' scaled units (rho0 * scale),
+    // converted once here rather than per thread (FP64 conversions issue at
+    // the FP64 rate)
+    float rho0f, rho0s;
     // near-body window split.  The window is the box of rows win[0..3] =
     // (z0, z length, y0, y length), periodic in both.  Mode 0 sweeps every
     // cell; mode 1 ("far") every cell outside the window; mode 2 ("near") the
@@ -64,6 +68,13 @@ struct SweepArgs {
     // order gives the same result (each cell touches only its own slots).
     int reverse;
     int* err;  // the lattice's device error word (bounded waits that run out)
+    // stochastic rounding of BF16 stores (Lattice::sr): the step number comes
+    // from the context's ping-pong counter (sr_ctr, advanced by the launch
+    // with sr_writer set) or from the server's global step less start_step
+    int sr, sr_writer;
+    unsigned long long* sr_ctr;
+    const long long* gstep;
+    long long gstart;
     // two-cell form: the plane, this many planes ahead in sweep order, whose
     // sources each thread prefetches into L2 (0: none; see sweep_two)
     int pf;
@@ -248,6 +259,52 @@ __device__ __forceinline__ void collide_trt(V g[Q], const TrtK& K, V rho0) {
 // a multiply per population.
 template <int S> constexpr bool kScaled = S == ST_F16 || S == ST_BF16;
 
+// ---- stochastic rounding of BF16 stores (SweepArgs::sr)
+//
+// The value's FP32 bits plus 16 random bits, truncated to the top 16 bits:
+// rounds away from zero with probability equal to the dropped fraction of a
+// BF16 unit, so the expected stored value is the value itself.  The random
+// bits are a counter-based hash of (step, cell, population): a step key,
+// then a cell key (both by the "lowbias32" integer hash of C. Wellons,
+// 2018), then one multiply by an odd constant per population.  Every sweep
+// form hashes the same (step, cell index, post-collision population), so the
+// forms still agree bit for bit.
+__device__ __forceinline__ uint32_t sr_mix(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+// The step number of this sweep, and (by the designated launch) the
+// context's counter for the next.  Called by every thread of a sweep kernel
+// before any early exit.
+__device__ __forceinline__ uint32_t sr_step(const SweepArgs& a) {
+    if (!a.sr) return 0u;
+    if (a.gstep) return (uint32_t)(*a.gstep - a.gstart);
+    const int q = a.reverse;  // the sweep's parity
+    const unsigned long long t = a.sr_ctr[q];
+    if (a.sr_writer && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+        threadIdx.y == 0)
+        a.sr_ctr[1 - q] = t + 1;
+    return (uint32_t)t;
+}
+__device__ __forceinline__ uint32_t sr_step_key(const SweepArgs& a) { return sr_mix(sr_step(a) ^ 0x5bd1e995u); }
+__device__ __forceinline__ uint32_t sr_cell_key(uint32_t step_key, uint32_t n) { return sr_mix(n ^ step_key); }
+// 16 random bits for post-collision population i of the cell with key k
+template <int I>
+__device__ __forceinline__ uint32_t sr_bits(uint32_t k) {
+    return (k * (0x9e3779b1u + 2u * (uint32_t)I * 0x61c88647u)) >> 16;
+}
+__device__ __forceinline__ uint32_t sr_bits_rt(uint32_t k, int i) {
+    return (k * (0x9e3779b1u + 2u * (uint32_t)i * 0x61c88647u)) >> 16;
+}
+// BF16 bits of v (in the storage's units), rounded stochastically with r
+__device__ __forceinline__ unsigned short bf16_sr(float v, uint32_t r) {
+    return (unsigned short)((__float_as_uint(v) + r) >> 16);
+}
+
 // One cell (x, y, z) with FP64 storage, collided in double-float arithmetic
 // (sweep_df.cuh).  O32: element offsets in 32-bit arithmetic (the launch
 // checks 19 Np < 2^32).
@@ -300,7 +357,7 @@ __device__ __forceinline__ void sweep_one_df(const SweepArgs& a, int x, int y, i
 // One cell (x, y, z).  FP64 storage collides in double-float arithmetic
 // unless NATIVE (FP64 arithmetic, the measured reference form).
 template <int S, int P, bool NATIVE = false>
-__device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int z) {
+__device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int z, uint32_t skey = 0u) {
     if constexpr (S == ST_F64 && !NATIVE) {
         if (a.K.df.le1) sweep_one_df<P, false, true>(a, x, y, z);
         else sweep_one_df<P, false, false>(a, x, y, z);
@@ -316,7 +373,7 @@ __device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int 
     const int64_t Np = a.Np;
     // 16-bit storages collide in their scaled units (see kScaled)
     const R isc = kScaled<S> ? R(1) : (R)a.inv_scale, sc = kScaled<S> ? R(1) : (R)a.scale;
-    const R rho0 = kScaled<S> ? (R)a.rho0 * (R)a.scale : (R)a.rho0;
+    const R rho0 = kScaled<S> ? (R)a.rho0s : (std::is_same<R, float>::value ? (R)a.rho0f : (R)a.rho0);
     R g[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -331,6 +388,7 @@ __device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int 
         g[i] = ST::load(F + off, isc);
     }
     collide_trt<R, ST::dev>(g, a.K, rho0);
+    const uint32_t ck = S == ST_BF16 && a.sr ? sr_cell_key(skey, (uint32_t)(x + nx * (y + ny * z))) : 0u;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         int64_t off;
@@ -338,6 +396,12 @@ __device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int 
             off = (int64_t)opp(i) * Np + (x + (int64_t)nx * (y + (int64_t)ny * z));
         } else {
             off = (int64_t)i * Np + (xs[1 + cx(i)] + (int64_t)nx * (ys[1 + cy(i)] + (int64_t)ny * zs[1 + cz(i)]));
+        }
+        if constexpr (S == ST_BF16) {
+            if (a.sr) {
+                st_stream(reinterpret_cast<unsigned short*>(F + off), bf16_sr((float)g[i], sr_bits_rt(ck, i)));
+                continue;
+            }
         }
         ST::store(F + off, g[i], sc);
     }
@@ -375,6 +439,24 @@ template <> __device__ __forceinline__ __nv_bfloat162 enc2<ST_BF16>(float a, flo
 }
 template <> __device__ __forceinline__ double2 enc2<ST_F64>(float, float, float) { return make_double2(0.0, 0.0); }
 
+// enc / enc2 with the stochastic rounding of BF16 stores when sr is set
+// (random bits r, ra, rb from sr_bits)
+template <int S>
+__device__ __forceinline__ typename StoreT<S>::T enc_r(typename StoreT<S>::R v, float sc, bool sr, uint32_t r) {
+    if constexpr (S == ST_BF16) {
+        if (sr) return __ushort_as_bfloat16(bf16_sr(v, r));
+    }
+    return enc<S>(v, sc);
+}
+template <int S>
+__device__ __forceinline__ typename Pair<typename StoreT<S>::T>::V enc2_r(float a, float b, float sc, bool sr,
+                                                                           uint32_t ra, uint32_t rb) {
+    if constexpr (S == ST_BF16) {
+        if (sr) return __halves2bfloat162(__ushort_as_bfloat16(bf16_sr(a, ra)), __ushort_as_bfloat16(bf16_sr(b, rb)));
+    }
+    return enc2<S>(a, b, sc);
+}
+
 // Two cells (x0, x0 + 1), x0 even; nx must be even.  Paired (vector)
 // accesses wherever both cells' slots are adjacent and aligned: all
 // directions on even steps, the directions with c_x = 0 on odd steps; scalar
@@ -383,7 +465,7 @@ template <> __device__ __forceinline__ double2 enc2<ST_F64>(float, float, float)
 // O32: element offsets in 32-bit arithmetic (the launch checks 19 Np < 2^32):
 // three instructions an access instead of about seven.
 template <int S, int P, bool O32 = false>
-__device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int z) {
+__device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int z, uint32_t skey = 0u) {
     using Off = typename std::conditional<O32, uint32_t, int64_t>::type;
     using ST = StoreT<S>;
     using T = typename ST::T;
@@ -399,7 +481,7 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
     T* __restrict__ F = (T*)a.F;
     const Off Np = (Off)a.Np;
     const float isc = kScaled<S> ? 1.0f : a.inv_scale, sc = kScaled<S> ? 1.0f : a.scale;
-    const R rho0 = kScaled<S> ? (R)a.rho0 * (R)a.scale : (R)a.rho0;
+    const R rho0 = kScaled<S> ? (R)a.rho0s : (std::is_same<R, float>::value ? (R)a.rho0f : (R)a.rho0);
     auto row = [&](int dy, int dz) -> Off { return (Off)nx * ((Off)ys[1 + dy] + (Off)ny * (Off)zs[1 + dz]); };
     // Prefetch into L2 what this thread's cells will read a.pf planes ahead in
     // sweep order: the block that sweeps that plane starts later, when the
@@ -443,20 +525,29 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
     }
     collide_trt<R, ST::dev>(g0, a.K, rho0);
     collide_trt<R, ST::dev>(g1, a.K, rho0);
+    const bool sr = S == ST_BF16 && a.sr;
+    uint32_t k0 = 0u, k1 = 0u;
+    if (sr) {
+        const uint32_t n0 = (uint32_t)x0 + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+        k0 = sr_cell_key(skey, n0);
+        k1 = sr_cell_key(skey, n0 + 1u);
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
+        const uint32_t r0 = sr ? sr_bits_rt(k0, i) : 0u, r1 = sr ? sr_bits_rt(k1, i) : 0u;
         if (P == 0) {
-            st_stream(reinterpret_cast<V*>(F + ((Off)opp(i) * Np + row(0, 0) + (Off)x0)), enc2<S>(g0[i], g1[i], sc));
+            st_stream(reinterpret_cast<V*>(F + ((Off)opp(i) * Np + row(0, 0) + (Off)x0)),
+                      enc2_r<S>(g0[i], g1[i], sc, sr, r0, r1));
         } else {
             T* base = F + ((Off)i * Np + row(cy(i), cz(i)));
             if (cx(i) == 0) {
-                st_stream(reinterpret_cast<V*>(base + x0), enc2<S>(g0[i], g1[i], sc));
+                st_stream(reinterpret_cast<V*>(base + x0), enc2_r<S>(g0[i], g1[i], sc, sr, r0, r1));
             } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
-                st_stream(base + x0 + 1, enc<S>(g0[i], sc));
-                st_stream(base + xp1, enc<S>(g1[i], sc));
+                st_stream(base + x0 + 1, enc_r<S>(g0[i], sc, sr, r0));
+                st_stream(base + xp1, enc_r<S>(g1[i], sc, sr, r1));
             } else {  // targets x0 - 1 and x0
-                st_stream(base + xm0, enc<S>(g0[i], sc));
-                st_stream(base + x0, enc<S>(g1[i], sc));
+                st_stream(base + xm0, enc_r<S>(g0[i], sc, sr, r0));
+                st_stream(base + x0, enc_r<S>(g1[i], sc, sr, r1));
             }
         }
     }
@@ -488,7 +579,8 @@ template <> __device__ __forceinline__ unsigned int enc16<ST_BF16>(float v, floa
 // barriers (`active`: the thread's row exists).
 // O32: element offsets in 32-bit arithmetic (the launch checks 19 Np < 2^32).
 template <int S, int P, bool O32 = false>
-__device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z, bool active, unsigned short* buf) {
+__device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z, bool active, unsigned short* buf,
+                                                uint32_t skey = 0u) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x0 = 4 * threadIdx.x;
     const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y >= ny - 1 ? 0 : y + 1};
@@ -496,7 +588,7 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
     unsigned short* F = (unsigned short*)a.F;
     using Off = typename std::conditional<O32, uint32_t, int64_t>::type;
     const Off Np = (Off)a.Np;
-    const float rho0 = (float)a.rho0 * a.scale;  // scaled units (see kScaled)
+    const float rho0 = a.rho0s;  // scaled units (see kScaled)
     auto row = [&](int dy, int dz) -> Off { return (Off)nx * ((Off)ys[1 + dy] + (Off)ny * (Off)zs[1 + dz]); };
     unsigned short* rowbuf = buf + (int64_t)threadIdx.y * nx;  // + d * blockDim.y * nx for shifted direction d
     const int dstride = blockDim.y * nx;
@@ -535,6 +627,8 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
         }
         __syncthreads();  // the buffer is reused for the stores
     }
+    const bool sr = S == ST_BF16 && a.sr;
+    const uint32_t n0 = (uint32_t)x0 + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         float gc[Q];
@@ -544,9 +638,10 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
             gc[i] = dec16<S>((c & 1) ? (w >> 16) : (w & 0xffffu), 1.0f);
         }
         collide_trt<float, true>(gc, a.K, rho0);
+        const uint32_t kc = sr ? sr_cell_key(skey, n0 + (uint32_t)c) : 0u;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const unsigned int e = enc16<S>(gc[i], 1.0f);
+            const unsigned int e = sr ? (unsigned int)bf16_sr(gc[i], sr_bits_rt(kc, i)) : enc16<S>(gc[i], 1.0f);
             unsigned int& w = c < 2 ? g[i].x : g[i].y;
             w = (c & 1) ? ((w & 0xffffu) | (e << 16)) : ((w & 0xffff0000u) | e);
         }
@@ -599,6 +694,8 @@ __host__ __device__ inline SweepArgs sweep_args(const Lattice& L, double lambda_
     a.K.inc = L.inc;
     a.K.df = df_constants(lambda_e, lambda_o, L.rho0);
     a.rho0 = L.rho0;
+    a.rho0f = (float)L.rho0;
+    a.rho0s = (float)L.rho0 * L.scale;
     a.scale = L.scale;
     a.inv_scale = L.inv_scale;
     a.zmode = 0;
@@ -606,6 +703,11 @@ __host__ __device__ inline SweepArgs sweep_args(const Lattice& L, double lambda_
     a.reverse = 0;
     a.err = L.err;
     a.pf = 0;
+    a.sr = L.sr && L.storage == ST_BF16;
+    a.sr_writer = 1;
+    a.sr_ctr = L.sr_ctr;
+    a.gstep = L.gstep;
+    a.gstart = L.start_step;
     return a;
 }
 

@@ -20,6 +20,8 @@ from . import build as _build
 LB_OK, LB_ERR_INVALID, LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_OVERLAP = 0, 1, 2, 3, 4
 LB_ERR_DIVERGED, LB_ERR_TIMEOUT, LB_ERR_STATE, LB_ERR_CAPACITY = 5, 6, 7, 8
 LB_EQ_COMPRESSIBLE, LB_EQ_INCOMPRESSIBLE = 0, 1
+LB_ROUND_DEFAULT, LB_ROUND_NEAREST, LB_ROUND_STOCHASTIC = -1, 0, 1
+ROUNDING = {"default": LB_ROUND_DEFAULT, "nearest": LB_ROUND_NEAREST, "stochastic": LB_ROUND_STOCHASTIC}
 LB_BGK, LB_TRT = 0, 1
 LB_F64, LB_F32, LB_F16DEV, LB_BF16DEV = 0, 1, 2, 3
 STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16dev": LB_F16DEV, "bf16dev": LB_BF16DEV}
@@ -40,7 +42,7 @@ class lb_params(C.Structure):
                 ("collision", C.c_int32), ("lambda_e", C.c_double), ("magic", C.c_double),
                 ("rho0", C.c_double), ("storage", C.c_int32), ("dev_scale_log2", C.c_int32),
                 ("device", C.c_int32), ("stream", C.c_void_p),
-                ("allocator", C.POINTER(lb_allocator)), ("equilibrium", C.c_int32)]
+                ("allocator", C.POINTER(lb_allocator)), ("equilibrium", C.c_int32), ("rounding", C.c_int32)]
 
 
 class lb_server_params(C.Structure):
@@ -88,6 +90,7 @@ SIGNATURES = {
     "lb_add_wall": (C.c_int, [_CTX, C.c_int32, _DP, C.c_int32, _IP]),
     "lb_set_contact": (C.c_int, [_CTX, C.c_double, C.c_double]),
     "lb_set_force_average": (C.c_int, [_CTX, C.c_int32]),
+    "lb_set_link_options": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "lb_set_fields": (C.c_int, [_CTX, _DP, _DP]),
     "lb_set_populations": (C.c_int, [_CTX, _DP]),
     "lb_get_populations": (C.c_int, [_CTX, _DP]),
@@ -205,6 +208,11 @@ def lb_set_contact(ctx, sigma: float, eps: float):
 
 def lb_set_force_average(ctx, on: bool):
     _check(ctx, load().lb_set_force_average(ctx, int(bool(on))), "lb_set_force_average")
+
+
+def lb_set_link_options(ctx, density_of_node: bool, velocity_at_node: bool):
+    _check(ctx, load().lb_set_link_options(ctx, int(bool(density_of_node)), int(bool(velocity_at_node))),
+           "lb_set_link_options")
 
 
 def lb_set_fields(ctx, rho, u):
@@ -483,11 +491,13 @@ class TorchAllocator:
 class Lattice:
     """One lattice context.  ``storage`` in {'f64','f32','f16dev','bf16dev'};
     ``collision`` in {'bgk','trt'}; ``equilibrium`` in {'compressible',
-    'incompressible'}.  With ``use_torch`` the context runs on a torch stream
+    'incompressible'}; ``rounding`` in {'default', 'nearest', 'stochastic'}
+    (BF16 stores).  With ``use_torch`` the context runs on a torch stream
     and takes its device memory from torch's caching allocator."""
 
     def __init__(self, shape, collision="bgk", lambda_e=1.0, magic=3.0 / 16.0, rho0=1.0,
-                 storage="f64", device=0, use_torch=True, dev_scale_log2=-1, equilibrium="compressible"):
+                 storage="f64", device=0, use_torch=True, dev_scale_log2=-1, equilibrium="compressible",
+                 rounding="default"):
         nx, ny, nz = (int(v) for v in shape)
         self.shape = (nx, ny, nz)
         self.N = nx * ny * nz
@@ -500,6 +510,7 @@ class Lattice:
         if equilibrium not in ("compressible", "incompressible"):
             raise ValueError(f"equilibrium {equilibrium!r}")
         p.equilibrium = LB_EQ_INCOMPRESSIBLE if equilibrium == "incompressible" else LB_EQ_COMPRESSIBLE
+        p.rounding = ROUNDING[rounding]
         p.device = int(device)
         self._stream = None
         self._alloc = None
@@ -553,6 +564,9 @@ class Lattice:
 
     def set_force_average(self, on=True):
         lb_set_force_average(self.ctx, on)
+
+    def set_link_options(self, density_of_node=False, velocity_at_node=False):
+        lb_set_link_options(self.ctx, density_of_node, velocity_at_node)
 
     def set_fields(self, rho, u):
         lb_set_fields(self.ctx, np.reshape(rho, -1), np.reshape(u, (3, -1)))

@@ -113,6 +113,42 @@ def two_squirmers_passing(d: float = 27.0, n: int = 250, R: float = 9.0, beta: f
                      Body((c, c - d / 2, c + 6 * R), (0.0, 0.0, -1.0), R, B1, beta, True)])
 
 
+@dataclass
+class TubeRun:
+    """A squirmer in a round tube (Sec. V, "Squirmer in a Round Tube")."""
+    name: str
+    shape: tuple
+    axis: tuple      # (cx, cy) of the tube axis (along z)
+    radius: float    # nodes at distance >= radius from the axis are wall
+    body: Body
+    steps: int
+    contact: tuple   # (sigma, eps) of the WCA contact force
+
+    @property
+    def cells(self) -> int:
+        return int(np.prod(self.shape))
+
+
+def tube_oscillation(y0_over_R: float = -1.0, R: float = 9.0, B1: float = 0.01, steps: int = 200000) -> TubeRun:
+    """Sec. V tube flow: a neutral squirmer (beta = 0, R = 9) in a round tube of
+    diameter D = 20R/3 = 60 and length 3 pi R = 85 (periodic along the
+    axis), starting parallel to the axis at a lateral displacement y0 (in
+    units of R) from it.  The fluid nodes are those within D/2 of the axis
+    (the tube wall is bounced back half-way, so the wall sits near D/2 + 1/2);
+    the box is D + 4 cells wide with the axis at its centre (31.5, 31.5), the
+    midpoint between two nodes, so that a squirmer on the axis is
+    mirror-symmetric.  B1 (not printed in the paper) = 0.01: Reynolds number
+    2 v0 R / nu = 0.72; the WCA contact force (sigma = 1, eps = 0.01) keeps
+    the squirmer off the wall."""
+    D = 20.0 * R / 3.0
+    n = int(round(D)) + 4
+    L = int(round(3.0 * math.pi * R))
+    c = (n - 1) / 2.0
+    z0 = L / 2.0 + 0.3
+    return TubeRun(f"tube_R{R:g}_y0{y0_over_R:+g}", (n, n, L), (c, c), D / 2.0,
+                   Body((c, c + y0_over_R * R, z0), (0.0, 0.0, 1.0), R, B1, 0.0, True), steps, (1.0, 0.01))
+
+
 def smooth_fields(shape, seed: int, drho: float = 0.01, umax: float = 0.02):
     """Smooth periodic random density and velocity fields (x-fastest, flattened):
     rho = 1 + drho * (sum of a few low Fourier modes), u likewise."""

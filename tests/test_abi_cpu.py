@@ -52,7 +52,8 @@ def test_params_default_and_invalid_arguments(lib):
     ctx = C.c_void_p()
     assert p.equilibrium == lbsq.LB_EQ_COMPRESSIBLE
     for field, bad in [("nx", 0), ("lambda_e", 2.0), ("lambda_e", 0.0), ("rho0", -1.0),
-                       ("storage", 9), ("collision", 5), ("equilibrium", 2), ("equilibrium", -1)]:
+                       ("storage", 9), ("collision", 5), ("equilibrium", 2), ("equilibrium", -1),
+                       ("rounding", 2), ("rounding", -2)]:
         q = lbsq.lb_params_default()
         setattr(q, field, bad)
         assert lib.lb_create(C.byref(q), C.byref(ctx)) == lbsq.LB_ERR_INVALID
@@ -63,4 +64,6 @@ def test_params_default_and_invalid_arguments(lib):
     assert lib.lb_destroy(None) == lbsq.LB_OK
     assert lib.lb_step(None, 1) == lbsq.LB_ERR_INVALID
     assert lib.lb_set_force_average(None, 1) == lbsq.LB_ERR_INVALID
+    assert lib.lb_set_link_options(None, 1, 0) == lbsq.LB_ERR_INVALID
+    assert lbsq.lb_params_default().rounding == lbsq.LB_ROUND_DEFAULT
     assert lib.lb_last_error(None) == b"null context"

@@ -273,6 +273,91 @@ def test_walls_couette_and_tube():
         _compare_bodies(g, o, [gs, gob], [os_, oob])
 
 
+@pytest.mark.parametrize("density_of_node,velocity_at_node", [(1, 0), (0, 1), (1, 1)])
+def test_link_options_against_oracle(density_of_node, velocity_at_node):
+    """The two open readings of the moving-wall bounce-back (lb_set_link_options
+    against the oracle's switches): the shift with the fluid node's density,
+    and the wall velocity and lever arm at the boundary node.  A free swimmer
+    crossing cells (FP64, 1e-12 against the oracle; FP32 storage within the
+    reduced-storage bound) and a Couette flow at density 1.05 (rho0 = 1)
+    with a moving wall.  (The double-float FP64 sweep carries about 47 bits
+    of the deviation f - w rho0: at a density 30 % off rho0 its rounding
+    grows to a few times 1e-12 of u over these 301 steps.)"""
+    shape = (28, 26, 30)
+    args = ((13.3, 12.7, 14.1), (0.3, -0.4, 1.0), 4.5, 0.03, -2.0)
+    o = OracleSim(*shape, lambda_e=1.0, collision="trt")
+    o.set_local_density(bool(density_of_node))
+    o.set_link_at_node(bool(velocity_at_node))
+    oi = o.add_sphere(*args, mobile=True)
+    runs = {}
+    for storage in ("f64", "f32"):
+        g = Lattice(shape, collision="trt", storage=storage)
+        g.set_link_options(density_of_node, velocity_at_node)
+        runs[storage] = (g, g.add_squirmer(*args, mobile=True))
+    for _ in range(3):
+        o.step(40)
+        for g, _ in runs.values():
+            g.step(40)
+        g, gi = runs["f64"]
+        _compare_bodies(g, o, [gi], [oi], R=4.5)
+    g, gi = runs["f32"]
+    _, ug = g.fields()
+    _, uo = o.fields()
+    both = (g.owner() == 0) & (o.owner() == 0)
+    assert rel(ug[:, both], uo[:, both]) < 2e-6
+    for g, _ in runs.values():
+        g.close()
+
+    shape = (6, 14, 5)
+    N = int(np.prod(shape))
+    g, o = make_pair(shape, "bgk", 0.9)
+    g.set_link_options(density_of_node, velocity_at_node)
+    o.set_local_density(bool(density_of_node))
+    o.set_link_at_node(bool(velocity_at_node))
+    rho, u = np.full(N, 1.05), np.zeros((3, N))
+    g.set_fields(rho, u)
+    o.set_equilibrium(rho, u)
+    g.add_plane_wall(1, 0)
+    gw = g.add_plane_wall(1, 13, vel=(1e-3, 0, 2e-4))
+    o.add_plane_wall(1, 0)
+    ow = o.add_plane_wall(1, 13, vel=(1e-3, 0, 2e-4))
+    g.step(301)
+    o.step(301)
+    _compare_bodies(g, o, [gw], [ow])
+
+
+def test_classification_band_adversarial():
+    """The fused body kernel decides "inside" in FP32 away from the sphere
+    surface and in exact FP64 within an error band around it.  Here every
+    sphere has R = 5, so R^2 = 25 is the squared distance of 30 lattice
+    vectors ((5,0,0), (3,4,0), ...), and starts a random 1e-9 .. 1e-4 off an
+    integer centre: at each re-classification of the first steps (the
+    spheres move by about 1e-5 per step, and a sphere with a node on its
+    surface re-classifies every step) dozens of nodes per sphere lie inside
+    the band or at its edges.  Owners bit-exact with the oracle's exact FP64
+    test at every step, and the fields and states within 1e-12."""
+    shape = (64, 64, 64)
+    rng = np.random.default_rng(77)
+    g, o = make_pair(shape, "trt", 1.0)
+    gids, oids = [], []
+    for cx in (12, 32, 52):
+        for cy in (12, 32, 52):
+            for cz in (12, 42):
+                off = rng.choice([-1.0, 1.0], 3) * 10.0 ** rng.uniform(-9, -4, 3)
+                e = rng.standard_normal(3)
+                args = ((cx + off[0], cy + off[1], cz + off[2]), tuple(e / np.linalg.norm(e)), 5.0, 0.02,
+                        float(rng.uniform(-3, 3)))
+                gids.append(g.add_squirmer(*args, mobile=True))
+                oids.append(o.add_sphere(*args, mobile=True))
+    for _ in range(12):
+        g.step(1)
+        o.step(1)
+        assert (g.owner() == o.owner()).all()
+    g.step(20)
+    o.step(20)
+    _compare_bodies(g, o, gids, oids, R=5.0)
+
+
 def test_round_tube_swimmer_f64():
     """Sec. V tube flow: a squirmer swimming toward the wall of a round tube
     (lb_add_wall kind 3), with the contact force on (Eq. "wca"), which it
@@ -488,14 +573,17 @@ def test_near_window_split_several_bodies_bitwise(bodies, storage):
 
 # ------------------------------------------------------------------ reduced storage
 
-@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16dev", 2e-2), ("bf16dev", 3e-1)])
+@pytest.mark.parametrize("storage,tol", [("f32", 2e-6), ("f16dev", 2e-3), ("bf16dev", 1.5e-2)])
 def test_reduced_storage_free_swimmer(storage, tol):
     """Reduced storages against the FP64 oracle: u field and body velocity after
-    200 steps.  Tolerances: the worst cell relative to max|u|, from the storage
-    rounding of the deviations (FP32 2^-24, FP16 2^-11 at scale 2^14, BF16
-    2^-9) accumulated over the run: u sums populations of about ten times its
-    own size, so BF16 adds about 2^-9 * 10 |u| per step, and 200 steps of a
-    random walk make about 0.28 max|u|."""
+    200 steps, the worst cell relative to max|u|.  The storage rounds each
+    deviation g to 2^-24 (FP32), 2^-11 (FP16 at scale 2^14) or 2^-8 (BF16,
+    stochastic) of itself every step.  |g| is about |u| / 6 here (3 w c.u),
+    and the collision relaxes every non-conserved moment each step, so only
+    the rounding of the conserved ones (rho, j) accumulates, as a random walk
+    spread by diffusion: over 200 steps a few units of 2^-p |u|.  Measured on
+    GB300: FP32 1.8e-7, FP16 1.5e-4, BF16 1.2e-3; the bounds are about ten
+    times those."""
     shape = (28, 26, 30)
     g = Lattice(shape, collision="trt", storage=storage)
     o = OracleSim(*shape, lambda_e=1.0, collision="trt")
@@ -600,6 +688,27 @@ def test_c3_full_size_parity(storage, tol):
     og, oo = g.owner(), o.owner()
     if storage != "f16dev":
         assert (og == oo).all()
+    else:
+        # the FP16 body drifts from the oracle's by about 1e-4 in 12 steps:
+        # owners must agree wherever a node is farther than the drift from
+        # the sphere surface at both positions (at the last classification)
+        pg, po = g.state(gi)[0], o.state(oi)[0]
+        drift = np.abs(pg - po).max() + np.abs(g.state(gi)[1]).max()
+        nx, ny, nz = wl.shape
+        lo = np.floor(pg - b.R - 2).astype(int)
+        ax = [np.arange(lo[a], lo[a] + int(2 * b.R) + 6) for a in range(3)]
+        zz, yy, xx = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        pts = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1).astype(float)
+        idx = (xx % nx) + nx * ((yy % ny) + ny * (zz % nz))
+        near_box = np.zeros(pts.shape[0], bool)
+        for c in (pg, po):
+            d = pts - c
+            d -= np.array(wl.shape) * np.round(d / np.array(wl.shape))
+            near_box |= np.abs(np.linalg.norm(d, axis=1) - b.R) < 2 * drift + 1e-9
+        near = np.zeros(og.size, bool)
+        near[idx.ravel()[near_box]] = True
+        assert near.sum() < 0.2 * (og != 0).sum()
+        assert (og[~near] == oo[~near]).all()
     _, ug = g.fields()
     _, uo = o.fields()
     both = (og == 0) & (oo == 0)

@@ -266,6 +266,29 @@ def test_couette_flow_is_linear_and_wall_stress_exact():
     assert F[0] == pytest.approx(-nu * U / H * 2 * 3, rel=1e-8)
 
 
+@pytest.mark.parametrize("local", [False, True])
+def test_couette_wall_speed_seen_at_another_density(local):
+    """The density in the shift 6 w_i rho c_i.v_b of Sec. III (left open by
+    the paper): in a fluid at uniform density rho = 1.3 (rho0 = 1), the shift
+    with the fluid node's density imposes the wall speed U itself, the shift
+    with rho0 imposes U rho0 / rho.  The linear Couette profile shows which
+    speed the fluid sees."""
+    ny, U, rho = 14, 1e-3, 1.3
+    s = O.OracleSim(2, ny, 3, lambda_e=1.0, collision="bgk")
+    s.set_equilibrium(np.full(2 * ny * 3, rho), np.zeros((3, 2 * ny * 3)))
+    if local:
+        s.set_local_density(True)
+    s.add_plane_wall(1, 0)
+    s.add_plane_wall(1, ny - 1, vel=(U, 0, 0))
+    s.step(12000)
+    _, u = s.fields()
+    ux = u[0].reshape(3, ny, 2)[:, :, 0][0]
+    y = np.arange(1, ny - 1)
+    H = ny - 2
+    Ueff = U if local else U / rho
+    np.testing.assert_allclose(ux[1:-1], Ueff * (y - 0.5) / H, rtol=1e-9, atol=1e-14)
+
+
 @pytest.mark.parametrize("le", [1.0, 1.6])
 def test_trt_poiseuille_exact_with_magic_3_16(le):
     """Sec. III: with the TRT magic parameter 3/16 (the boundary-faithfulness
