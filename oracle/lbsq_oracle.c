@@ -249,6 +249,9 @@ typedef struct {
     double link_at; /* where on a link v_b and the lever arm are taken: 0.5 (midpoint) or 1 (boundary node) */
     int conv;       /* conversion reading: 0 = the one used throughout, else an alternative (osim_set_conversion) */
     int local_rho;  /* 1: the bounce-back shift takes the density of the fluid node instead of rho0 */
+    int psm;        /* 1: spheres couple by partially saturated cells (Noble-Torczynski), not links */
+    double* eps;    /* PSM: solid fraction of each cell, [N] */
+    int32_t* psm_id; /* PSM: the sphere (id) covering each cell, 0 = none, [N] */
     int nobj, capobj;
     oobj* obj; /* obj[k] has id k+1 */
     long step;
@@ -324,6 +327,8 @@ void osim_destroy(osim* s) {
     free(s->fnew);
     free(s->owner);
     free(s->owner_prev);
+    free(s->eps);
+    free(s->psm_id);
     free(s->obj);
     free(s);
 }
@@ -431,6 +436,10 @@ int32_t osim_add_sphere(osim* s, const double* pos, const double* e, double R, d
     o->pos[2] = pos[2] - floor(pos[2] / s->nz) * s->nz;
     for (int k = 0; k < 3; ++k) o->e[k] = e[k] / ne;
     int id = s->nobj + 1;
+    if (s->psm) { /* partially saturated cells: the sphere claims no cell */
+        s->nobj++;
+        return id;
+    }
     /* classify: the sphere's box */
     int lo[3], W;
     sphere_box(o, lo, &W);
@@ -749,7 +758,7 @@ static void remap(osim* s) {
     /* new classification of every mobile sphere's box */
     for (int k = 0; k < s->nobj; ++k) {
         oobj* o = &s->obj[k];
-        if (o->kind != OBJ_SPHERE || !o->mobile) continue;
+        if (o->kind != OBJ_SPHERE || !o->mobile || s->psm) continue;
         int id = k + 1, lo[3], W;
         sphere_box(o, lo, &W);
         for (int bz = 0; bz < W; ++bz)
@@ -837,10 +846,175 @@ static void remap(osim* s) {
     }
 }
 
+/* ---- partially saturated cells (Noble and Torczynski, 1998) -----------
+ * The remedy Sec. IV A names for the speed fluctuation: instead of link
+ * bounce-back and cell conversion, every cell stays fluid and carries the
+ * fraction eps of its volume (the unit cube about the node) that a sphere
+ * covers.  Its collision blends the fluid operator with a solid one,
+ *   f*_i = f_i + (1 - B) Omega_i + B Omega^s_i,
+ *   Omega^s_i = [f_ib - f_ib^eq(rho, u)] - [f_i - f_i^eq(rho, u_s)],
+ *   B = eps (tau - 1/2) / ((1 - eps) + (tau - 1/2)),  tau = 1 / lambda_e,
+ * with Omega_i the TRT collision, (rho, u) the cell's moments and u_s the
+ * sphere's surface velocity at the node (v + w x d + slip, Eq. "vb").  The
+ * fluid gains B sum_i Omega^s_i c_i, which the sphere loses. */
+
+/* Solid fraction of the cell at offset d from the centre of a sphere of
+ * radius R: the share of the 8 x 8 x 8 points (k + 1/2)/8 - 1/2 of the unit
+ * cube inside the sphere (exact multiples of 1/512); 1 or 0 without sampling
+ * when the whole cube lies inside or outside (its half-diagonal is below 0.87). */
+double oracle_psm_fraction(const double* d, double R) {
+    double r2 = d[0] * d[0] + d[1] * d[1];
+    r2 = r2 + d[2] * d[2];
+    double lo = R - 0.87, hi = R + 0.87;
+    if (lo > 0.0 && r2 < lo * lo) return 1.0;
+    if (r2 > hi * hi) return 0.0;
+    int count = 0;
+    for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b)
+            for (int c = 0; c < 8; ++c) {
+                double p[3] = {d[0] + ((a + 0.5) / 8.0 - 0.5), d[1] + ((b + 0.5) / 8.0 - 0.5),
+                               d[2] + ((c + 0.5) / 8.0 - 0.5)};
+                count += oracle_inside(p, R);
+            }
+    return count / 512.0;
+}
+
+static void psm_fraction(osim* s) {
+    long N = s->N;
+    memset(s->eps, 0, sizeof(double) * N);
+    memset(s->psm_id, 0, sizeof(int32_t) * N);
+    for (int k = 0; k < s->nobj; ++k) {
+        oobj* o = &s->obj[k];
+        if (o->kind != OBJ_SPHERE) continue;
+        int lo[3], W;
+        sphere_box(o, lo, &W);
+        for (int bz = 0; bz < W; ++bz)
+            for (int by = 0; by < W; ++by)
+                for (int bx = 0; bx < W; ++bx) {
+                    int x = wrap(lo[0] + bx, s->nx), y = wrap(lo[1] + by, s->ny), z = wrap(lo[2] + bz, s->nz);
+                    long c = cidx(s, x, y, z);
+                    double d[3];
+                    sphere_offset(s, o, x, y, z, d);
+                    double e = oracle_psm_fraction(d, o->R);
+                    if (e == 0.0) continue;
+                    if (s->psm_id[c] != 0 && s->psm_id[c] != k + 1) s->err = OERR_OVERLAP;
+                    s->eps[c] = e;
+                    s->psm_id[c] = k + 1;
+                }
+    }
+}
+
+/* Surface velocity of sphere o at node offset d (the slip by direction only). */
+static void psm_surface_velocity(const oobj* o, const double* d, double* us) {
+    double slip[3];
+    oracle_slip(d, o->e, o->B1, o->B2, slip);
+    us[0] = o->vel[0] + (o->omega[1] * d[2] - o->omega[2] * d[1]) + slip[0];
+    us[1] = o->vel[1] + (o->omega[2] * d[0] - o->omega[0] * d[2]) + slip[1];
+    us[2] = o->vel[2] + (o->omega[0] * d[1] - o->omega[1] * d[0]) + slip[2];
+}
+
+/* The solid operator Omega^s of a cell with populations f, and its weight B. */
+static double psm_solid_term(const osim* s, const double* f, const oobj* o, const double* d, double eps,
+                             double* om) {
+    double rho, j[3], u[3], us[3], feq[Q], feqs[Q];
+    oracle_moments(f, &rho, j);
+    double den = s->inc ? s->rho0 : rho;
+    for (int a = 0; a < 3; ++a) u[a] = j[a] / den;
+    psm_surface_velocity(o, d, us);
+    if (s->inc) {
+        oracle_feq_inc(rho, s->rho0, u, feq);
+        oracle_feq_inc(rho, s->rho0, us, feqs);
+    } else {
+        oracle_feq(rho, u, feq);
+        oracle_feq(rho, us, feqs);
+    }
+    for (int i = 0; i < Q; ++i) {
+        int ib = oracle_opposite(i);
+        om[i] = (f[ib] - feq[ib]) - (f[i] - feqs[i]);
+    }
+    double th = 1.0 / s->lambda_e - 0.5;
+    return eps * th / ((1.0 - eps) + th);
+}
+
+/* Post-collision populations of the cells a sphere covers in part (after
+ * collide_all wrote the fluid operator's result for every cell). */
+static void psm_collide(osim* s) {
+    long N = s->N;
+    for (long n = 0; n < N; ++n) {
+        if (s->psm_id[n] == 0 || s->owner[n] != 0) continue;
+        const oobj* o = &s->obj[s->psm_id[n] - 1];
+        int x, y, z;
+        coords(s, n, &x, &y, &z);
+        double d[3], f[Q], om[Q];
+        sphere_offset(s, o, x, y, z, d);
+        for (int i = 0; i < Q; ++i) f[i] = s->f[i * N + n];
+        double B = psm_solid_term(s, f, o, d, s->eps[n], om);
+        for (int i = 0; i < Q; ++i) {
+            double fl = s->fpost[i * N + n] - f[i]; /* the fluid operator Omega_i */
+            s->fpost[i * N + n] = f[i] + (1.0 - B) * fl + B * om[i];
+        }
+    }
+}
+
+/* Force, torque and stresslet on each sphere: minus the momentum the solid
+ * operator gives the fluid, summed in cell order (after bounce_links, which
+ * zeroes the sums). */
+static void psm_forces(osim* s) {
+    long N = s->N;
+    for (long n = 0; n < N; ++n) {
+        if (s->psm_id[n] == 0 || s->owner[n] != 0) continue;
+        oobj* o = &s->obj[s->psm_id[n] - 1];
+        int x, y, z;
+        coords(s, n, &x, &y, &z);
+        double d[3], f[Q], om[Q];
+        sphere_offset(s, o, x, y, z, d);
+        for (int i = 0; i < Q; ++i) f[i] = s->f[i * N + n];
+        double B = psm_solid_term(s, f, o, d, s->eps[n], om);
+        double m[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < Q; ++i) {
+            m[0] += om[i] * CX[i];
+            m[1] += om[i] * CY[i];
+            m[2] += om[i] * CZ[i];
+        }
+        double dF[3] = {-B * m[0], -B * m[1], -B * m[2]}, dT[3];
+        cross(d, dF, dT);
+        for (int a = 0; a < 3; ++a) {
+            o->Fbb[a] += dF[a];
+            o->Tbb[a] += dT[a];
+        }
+        double tr = (d[0] * dF[0] + d[1] * dF[1] + d[2] * dF[2]) / 3.0;
+        o->Sbb[0] -= d[0] * dF[0] - tr;
+        o->Sbb[1] -= d[1] * dF[1] - tr;
+        o->Sbb[2] -= d[2] * dF[2] - tr;
+        o->Sbb[3] -= 0.5 * (d[0] * dF[1] + d[1] * dF[0]);
+        o->Sbb[4] -= 0.5 * (d[0] * dF[2] + d[2] * dF[0]);
+        o->Sbb[5] -= 0.5 * (d[1] * dF[2] + d[2] * dF[1]);
+    }
+}
+
+/* Couple the spheres by partially saturated cells (on = 1) instead of link
+ * bounce-back and conversion; walls keep their links.  Call before adding
+ * spheres. */
+void osim_set_psm(osim* s, int on) {
+    s->psm = on ? 1 : 0;
+    if (s->psm && !s->eps) {
+        s->eps = (double*)calloc(s->N, sizeof(double));
+        s->psm_id = (int32_t*)calloc(s->N, sizeof(int32_t));
+    }
+}
+
+/* Solid fraction of every cell at the last step ([N], zero without PSM). */
+void osim_get_eps(const osim* s, double* out) {
+    for (long n = 0; n < s->N; ++n) out[n] = s->psm ? s->eps[n] : 0.0;
+}
+
 void osim_step(osim* s, int64_t nsteps) {
     for (int64_t t = 0; t < nsteps; ++t) {
+        if (s->psm) psm_fraction(s);
         collide_all(s);
+        if (s->psm) psm_collide(s);
         bounce_links(s);
+        if (s->psm) psm_forces(s);
         stream_all(s);
         integrate(s);
         remap(s);

@@ -78,6 +78,9 @@ def load_oracle():
             "osim_set_link_at_node": (None, [C.c_void_p, C.c_int32]),
             "osim_set_conversion": (None, [C.c_void_p, C.c_int32]),
             "osim_set_local_density": (None, [C.c_void_p, C.c_int32]),
+            "osim_set_psm": (None, [C.c_void_p, C.c_int32]),
+            "osim_get_eps": (None, [C.c_void_p, _DP]),
+            "oracle_psm_fraction": (C.c_double, [_DP, C.c_double]),
             "osim_set_equilibrium": (None, [C.c_void_p, _DP, _DP]),
             "osim_set_populations": (None, [C.c_void_p, _DP]),
             "osim_get_populations": (None, [C.c_void_p, _DP]),
@@ -181,6 +184,12 @@ def inside(d, R: float) -> bool:
     return bool(load_oracle().oracle_inside(dp, R))
 
 
+def psm_fraction(d, R: float) -> float:
+    """Solid fraction of the unit cell at offset d from a sphere's centre."""
+    d, dp = _d(d)
+    return float(load_oracle().oracle_psm_fraction(dp, R))
+
+
 def min_image(d: float, n: int) -> float:
     return float(load_oracle().oracle_min_image(d, n))
 
@@ -259,6 +268,16 @@ class OracleSim:
 
     def set_link_at_node(self, on: bool = True):
         self._lib.osim_set_link_at_node(self._h, 1 if on else 0)
+
+    def set_psm(self, on: bool = True):
+        """Couple spheres by partially saturated cells (see osim_set_psm);
+        call before adding spheres."""
+        self._lib.osim_set_psm(self._h, 1 if on else 0)
+
+    def eps(self) -> np.ndarray:
+        out = np.empty(self.N)
+        self._lib.osim_get_eps(self._h, out.ctypes.data_as(_DP))
+        return out
 
     def set_local_density(self, on: bool = True):
         """The bounce-back shift with the fluid node's density (see osim_set_local_density)."""

@@ -277,6 +277,11 @@ __device__ __forceinline__ uint32_t sr_mix(uint32_t x) {
     x ^= x >> 16;
     return x;
 }
+// The random bits of a store come in pairs: one 32-bit word per pair of cells
+// (2m, 2m + 1) (cell index n, pair n >> 1) and population i, its low half for
+// the even cell and its high half for the odd one.  (Cells of a pair sit side
+// by side in x when nx is even; for odd nx the pairing still gives every form
+// the same bits.)
 // The step number of this sweep, and (by the designated launch) the
 // context's counter for the next.  Called by every thread of a sweep kernel
 // before any early exit.
@@ -291,18 +296,18 @@ __device__ __forceinline__ uint32_t sr_step(const SweepArgs& a) {
     return (uint32_t)t;
 }
 __device__ __forceinline__ uint32_t sr_step_key(const SweepArgs& a) { return sr_mix(sr_step(a) ^ 0x5bd1e995u); }
-__device__ __forceinline__ uint32_t sr_cell_key(uint32_t step_key, uint32_t n) { return sr_mix(n ^ step_key); }
-// 16 random bits for post-collision population i of the cell with key k
-template <int I>
-__device__ __forceinline__ uint32_t sr_bits(uint32_t k) {
-    return (k * (0x9e3779b1u + 2u * (uint32_t)I * 0x61c88647u)) >> 16;
-}
-__device__ __forceinline__ uint32_t sr_bits_rt(uint32_t k, int i) {
-    return (k * (0x9e3779b1u + 2u * (uint32_t)i * 0x61c88647u)) >> 16;
-}
-// BF16 bits of v (in the storage's units), rounded stochastically with r
+__device__ __forceinline__ uint32_t sr_pair_key(uint32_t step_key, uint32_t n) { return sr_mix((n >> 1) ^ step_key); }
+// 32 random bits for post-collision population i of the pair with key k
+__device__ __forceinline__ uint32_t sr_word(uint32_t k, int i) { return k * (0x9e3779b1u + 2u * (uint32_t)i * 0x61c88647u); }
+// the 16 bits of a word for the even (low half) or odd (high half) cell
+__device__ __forceinline__ uint32_t sr_half(uint32_t w, uint32_t n) { return (n & 1u) ? (w >> 16) : (w & 0xffffu); }
+// BF16 bits of v (in the storage's units), rounded stochastically with the 16 bits r
 __device__ __forceinline__ unsigned short bf16_sr(float v, uint32_t r) {
     return (unsigned short)((__float_as_uint(v) + r) >> 16);
+}
+// BF16 bits of (a, b), rounded stochastically with the halves of w, packed a | b << 16
+__device__ __forceinline__ uint32_t bf16x2_sr(float a, float b, uint32_t w) {
+    return __byte_perm(__float_as_uint(a) + (w & 0xffffu), __float_as_uint(b) + (w >> 16), 0x7632);
 }
 
 // One cell (x, y, z) with FP64 storage, collided in double-float arithmetic
@@ -388,7 +393,8 @@ __device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int 
         g[i] = ST::load(F + off, isc);
     }
     collide_trt<R, ST::dev>(g, a.K, rho0);
-    const uint32_t ck = S == ST_BF16 && a.sr ? sr_cell_key(skey, (uint32_t)(x + nx * (y + ny * z))) : 0u;
+    const uint32_t ncell = (uint32_t)(x + nx * (y + ny * z));
+    const uint32_t ck = S == ST_BF16 && a.sr ? sr_pair_key(skey, ncell) : 0u;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         int64_t off;
@@ -399,7 +405,7 @@ __device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int 
         }
         if constexpr (S == ST_BF16) {
             if (a.sr) {
-                st_stream(reinterpret_cast<unsigned short*>(F + off), bf16_sr((float)g[i], sr_bits_rt(ck, i)));
+                st_stream(reinterpret_cast<unsigned short*>(F + off), bf16_sr((float)g[i], sr_half(sr_word(ck, i), ncell)));
                 continue;
             }
         }
@@ -450,9 +456,14 @@ __device__ __forceinline__ typename StoreT<S>::T enc_r(typename StoreT<S>::R v, 
 }
 template <int S>
 __device__ __forceinline__ typename Pair<typename StoreT<S>::T>::V enc2_r(float a, float b, float sc, bool sr,
-                                                                           uint32_t ra, uint32_t rb) {
+                                                                           uint32_t w) {
     if constexpr (S == ST_BF16) {
-        if (sr) return __halves2bfloat162(__ushort_as_bfloat16(bf16_sr(a, ra)), __ushort_as_bfloat16(bf16_sr(b, rb)));
+        if (sr) {
+            const uint32_t p = bf16x2_sr(a, b, w);
+            __nv_bfloat162 v;
+            memcpy(&v, &p, 4);
+            return v;
+        }
     }
     return enc2<S>(a, b, sc);
 }
@@ -526,22 +537,19 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
     collide_trt<R, ST::dev>(g0, a.K, rho0);
     collide_trt<R, ST::dev>(g1, a.K, rho0);
     const bool sr = S == ST_BF16 && a.sr;
-    uint32_t k0 = 0u, k1 = 0u;
-    if (sr) {
-        const uint32_t n0 = (uint32_t)x0 + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
-        k0 = sr_cell_key(skey, n0);
-        k1 = sr_cell_key(skey, n0 + 1u);
-    }
+    // cells x0 and x0 + 1 (x0 even, nx even) form one pair of the random bits
+    const uint32_t kp = sr ? sr_pair_key(skey, (uint32_t)x0 + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z)) : 0u;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const uint32_t r0 = sr ? sr_bits_rt(k0, i) : 0u, r1 = sr ? sr_bits_rt(k1, i) : 0u;
+        const uint32_t w = sr ? sr_word(kp, i) : 0u;
+        const uint32_t r0 = w & 0xffffu, r1 = w >> 16;
         if (P == 0) {
             st_stream(reinterpret_cast<V*>(F + ((Off)opp(i) * Np + row(0, 0) + (Off)x0)),
-                      enc2_r<S>(g0[i], g1[i], sc, sr, r0, r1));
+                      enc2_r<S>(g0[i], g1[i], sc, sr, w));
         } else {
             T* base = F + ((Off)i * Np + row(cy(i), cz(i)));
             if (cx(i) == 0) {
-                st_stream(reinterpret_cast<V*>(base + x0), enc2_r<S>(g0[i], g1[i], sc, sr, r0, r1));
+                st_stream(reinterpret_cast<V*>(base + x0), enc2_r<S>(g0[i], g1[i], sc, sr, w));
             } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
                 st_stream(base + x0 + 1, enc_r<S>(g0[i], sc, sr, r0));
                 st_stream(base + xp1, enc_r<S>(g1[i], sc, sr, r1));
@@ -628,7 +636,9 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
         __syncthreads();  // the buffer is reused for the stores
     }
     const bool sr = S == ST_BF16 && a.sr;
+    // the four cells are two pairs of the random bits (x0 and nx are multiples of 4)
     const uint32_t n0 = (uint32_t)x0 + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+    const uint32_t k01 = sr ? sr_pair_key(skey, n0) : 0u, k23 = sr ? sr_pair_key(skey, n0 + 2u) : 0u;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         float gc[Q];
@@ -638,10 +648,12 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
             gc[i] = dec16<S>((c & 1) ? (w >> 16) : (w & 0xffffu), 1.0f);
         }
         collide_trt<float, true>(gc, a.K, rho0);
-        const uint32_t kc = sr ? sr_cell_key(skey, n0 + (uint32_t)c) : 0u;
+        const uint32_t kc = c < 2 ? k01 : k23;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const unsigned int e = sr ? (unsigned int)bf16_sr(gc[i], sr_bits_rt(kc, i)) : enc16<S>(gc[i], 1.0f);
+            const uint32_t rw = sr_word(kc, i);
+            const unsigned int e = sr ? (unsigned int)bf16_sr(gc[i], (c & 1) ? (rw >> 16) : (rw & 0xffffu))
+                                      : enc16<S>(gc[i], 1.0f);
             unsigned int& w = c < 2 ? g[i].x : g[i].y;
             w = (c & 1) ? ((w & 0xffffu) | (e << 16)) : ((w & 0xffff0000u) | e);
         }
