@@ -189,6 +189,39 @@ lb_status lb_set_contact(lb_ctx* c, double sigma, double eps);
  * every body of the context.  Errors: LB_ERR_INVALID (a value not 0 or 1). */
 lb_status lb_set_link_options(lb_ctx* c, int32_t density_of_node, int32_t velocity_at_node);
 
+/* Coupling of the spheres to the fluid.
+ *   LB_COUPLE_LINKS (default): Sec. III -- the cells a sphere covers are
+ *     solid, the links between them and the fluid bounce back from the moving
+ *     surface, and cells the surface sweeps over are converted.
+ *   LB_COUPLE_PSM: partially saturated cells (Noble and Torczynski, the
+ *     remedy Sec. IV A names for the fluctuating swim speed of the link
+ *     coupling).  Every cell stays fluid.  At the start of each step each
+ *     sphere's solid fraction eps of every cell (its share of 8^3 sample
+ *     points of the unit cube about the node, exact multiples of 1/512) is
+ *     found; a covered cell collides with
+ *       f_i + (1 - B) Omega_i + B Omega^s_i,
+ *       Omega^s_i = [f_ib - f_ib^eq(rho, u)] - [f_i - f_i^eq(rho, u_s)],
+ *       B = eps (tau - 1/2) / ((1 - eps) + tau - 1/2),  tau = 1 / lambda_e,
+ *     Omega_i the fluid collision, u_s the surface velocity at the node
+ *     (rigid motion plus the squirmer slip of Eq. "squirmer" by direction);
+ *     the sphere receives -B sum_i Omega^s_i c_i from each covered cell
+ *     (force, torque about its centre and stresslet), computed from the
+ *     populations the step starts from.  The blended collision is FP64
+ *     arithmetic for every storage; stores round to nearest.  Walls keep their
+ *     links; a covered wall cell stays a wall cell.  A cell covered by two
+ *     spheres sets LB_ERR_OVERLAP.  Spheres claim no cells (lb_get_owner
+ *     shows none) and have no links.
+ * Set it before the first sphere (obstacles of lb_add_wall kind 2 are
+ * spheres).  Errors: LB_ERR_INVALID (another value, or spheres exist),
+ * LB_ERR_OOM. */
+typedef enum { LB_COUPLE_LINKS = 0, LB_COUPLE_PSM = 1 } lb_coupling;
+lb_status lb_set_coupling(lb_ctx* c, int32_t coupling);
+
+/* Solid fraction of every cell found at the start of the last step
+ * (eps[N], x-fastest), all zero under link coupling.  Errors: LB_ERR_INVALID,
+ * LB_ERR_CUDA and the device error word. */
+lb_status lb_get_solid_fraction(lb_ctx* c, double* eps);
+
 /* Ladd's two-step force average (Sec. III): with on = 1, every body's update
  * applies (F_bb(t) + F_bb(t-1)) / 2 and (T_bb(t) + T_bb(t-1)) / 2 instead of
  * this step's momentum exchange, F_bb(t-1) = 0 before a body's first step;
@@ -337,8 +370,9 @@ lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant);
  * launches each kernel of a step directly (no graph) with a CUDA event
  * recorded on the context's stream before and after it.  lb_profile_end
  * synchronises and writes, per kernel kind in launch order
- *   0 sweep, 1 links (bounce-back, force reduction, Newton-Euler),
- *   2 classify, 3 convert, 4 rebuild, 5 tick (end of step),
+ *   0 sweep, 1 links (bounce-back, force reduction, Newton-Euler; with
+ *   partially saturated cells also the solid fractions and the spheres'
+ *   forces and updates), 2 classify, 3 convert, 4 rebuild, 5 tick (end of step),
  * the summed device time in ms (total_ms[6]) and the launch count
  * (launches[6]).  Either pointer may be NULL. */
 lb_status lb_profile_begin(lb_ctx* c);

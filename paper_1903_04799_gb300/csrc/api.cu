@@ -12,6 +12,7 @@
 
 #include "../../include/lbsq.h"
 #include "lbsq_internal.cuh"
+#include "psm.cuh"
 
 namespace lbsq {
 void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, int zmode,
@@ -38,6 +39,9 @@ void launch_tube_overlap(const Lattice& L, const int32_t* own, const int* kind, 
                          cudaStream_t st);
 void launch_tube_claim(const Lattice& L, int32_t* own, const BodyParams& q, int id, cudaStream_t st);
 void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, cudaStream_t st);
+void launch_psm_step(const Bodies& B, int parity, int grid, cudaStream_t st);
+void launch_sweep_psm(const Lattice& L, double lambda_e, double lambda_o, int parity, const PsmArgs& q,
+                      cudaStream_t st);
 }  // namespace lbsq
 
 using namespace lbsq;
@@ -85,6 +89,15 @@ struct lb_ctx {
     Lattice* d_lat = nullptr;  // the one lattice descriptor on the device
     double wca_sigma = 1.0, wca_eps = 0.0;
     int force_avg = 0;  // lb_set_force_average
+    // spheres coupled by partially saturated cells (lb_set_coupling): the
+    // solid fraction and covering sphere per cell, the (body, block) items of
+    // the spheres' boxes and their per-block force partials
+    bool psm = false;
+    float* d_eps = nullptr;
+    int32_t* d_psm_id = nullptr;
+    int2* d_psm_items = nullptr;
+    double* d_part_psm = nullptr;
+    int n_psm_items = 0, psm_alloc = 0, grid_psm = 1;
     // scratch
     double* d_mass_part = nullptr;
     double* d_small = nullptr;  // 8 doubles
@@ -205,6 +218,9 @@ Bodies bodies_view(const lb_ctx* c) {
     B.fused_first = c->d_counts + 7;
     B.stencil = c->d_stencil;
     B.fused_done = c->d_counts + 10;
+    B.psm_items = c->d_psm_items;
+    B.n_psm_items = c->n_psm_items;
+    B.part_psm = c->d_part_psm;
     return B;
 }
 
@@ -316,6 +332,7 @@ lb_status relayout(lb_ctx* c) {
     int gl = 1, gb = 1, sum_gb = 0;
     std::vector<int2> items;
     std::vector<int2> fused;
+    std::vector<int2> psm_items;
     std::vector<uint32_t> stencil;
     for (int k = 0; k < nb; ++k) {
         BodyParams& b = c->par[k];
@@ -351,7 +368,9 @@ lb_status relayout(lb_ctx* c) {
         gl = std::max(gl, b.g_links);
         gb = std::max(gb, b.g_box);
         sum_gb += b.g_box;
-        if (!fused_body(b))
+        if (b.psm)
+            for (int g = 0; g < b.g_box; ++g) psm_items.push_back(make_int2(k, g));
+        else if (!fused_body(b))
             for (int g = 0; g < b.g_links; ++g) items.push_back(make_int2(k, g));
     }
     if ((int)fused.size() > c->fused_alloc) {
@@ -390,6 +409,20 @@ lb_status relayout(lb_ctx* c) {
     c->d_part_conv = dalloc_t<double>(c, (size_t)nb * c->G_box * 6);
     c->d_part_count = dalloc_t<int>(c, (size_t)nb * c->G_box);
     if (!c->d_part_links || !c->d_part_conv || !c->d_part_count) return fail(c, LB_ERR_OOM, "partials");
+    if (!psm_items.empty()) {
+        dfree(c, c->d_part_psm);
+        c->d_part_psm = dalloc_t<double>(c, (size_t)nb * c->G_box * 12);
+        if ((int)psm_items.size() > c->psm_alloc) {
+            dfree(c, c->d_psm_items);
+            c->d_psm_items = dalloc_t<int2>(c, psm_items.size());
+            c->psm_alloc = c->d_psm_items ? (int)psm_items.size() : 0;
+        }
+        if (!c->d_part_psm || !c->d_psm_items) return fail(c, LB_ERR_OOM, "partially saturated cells");
+        CK(cudaMemcpyAsync(c->d_psm_items, psm_items.data(), sizeof(int2) * psm_items.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+    }
+    c->n_psm_items = (int)psm_items.size();
+    c->grid_psm = std::max(1, std::min(c->n_psm_items, 4 * c->n_sm));
     // work lists: every body appears at most once per step in each list
     const int need = std::max<int>((int)items.size(), sum_gb);
     if (need > c->list_alloc) {
@@ -438,7 +471,8 @@ lb_status relayout(lb_ctx* c) {
             across = true;
         }
     }
-    c->split = !across && nb > 0 && wmax * 5 < 3 * c->L.nz;
+    // (partially saturated cells: every step sweeps the whole lattice)
+    c->split = !c->psm && !across && nb > 0 && wmax * 5 < 3 * c->L.nz;
     if (ranges > 1) {
         wmax = c->L.nz;
         ymax = c->L.ny;
@@ -719,6 +753,29 @@ lb_status lb_add_squirmer(lb_ctx* c, const double pos[3], const double e[3], dou
         st.e[a] = e[a] / ne;
     }
     const int W = (int)std::ceil(2.0 * R) + 6;
+    if (c->psm) {
+        // partially saturated cells: the sphere claims no cell and has no
+        // links; its cells are found at the start of every step
+        BodyParams bp{};
+        bp.kind = BODY_SPHERE;
+        bp.psm = 1;
+        bp.mobile = mobile ? 1 : 0;
+        bp.R = R;
+        bp.B1 = B1;
+        bp.B2 = beta * B1;
+        bp.mass = density * (4.0 / 3.0) * M_PI * R * R * R;
+        bp.inertia = 0.4 * bp.mass * R * R;
+        bp.inv_mass = 1.0 / bp.mass;
+        bp.inv_inertia = 1.0 / bp.inertia;
+        bp.link_cap = 0;
+        bp.box_w[0] = bp.box_w[1] = bp.box_w[2] = W;
+        int32_t nid = 0;
+        lb_status s = new_body(c, bp, st, BODY_SPHERE, &nid);
+        if (s == LB_OK) s = relayout(c);
+        if (s != LB_OK) return s;
+        *id = nid;
+        return LB_OK;
+    }
     // overlap check before anything changes
     CK(cudaMemsetAsync(c->d_count, 0, sizeof(int), c->stream));
     CK(cudaMemcpyAsync(c->d_small, st.pos, 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -841,6 +898,48 @@ lb_status lb_set_contact(lb_ctx* c, double sigma, double eps) {
     return LB_OK;
 }
 
+lb_status lb_set_coupling(lb_ctx* c, int32_t coupling) {
+    if (!c || (coupling != LB_COUPLE_LINKS && coupling != LB_COUPLE_PSM)) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
+    const bool want = coupling == LB_COUPLE_PSM;
+    if (want == c->psm) return LB_OK;
+    for (const BodyParams& b : c->par)
+        if (b.kind == BODY_SPHERE) return fail(c, LB_ERR_INVALID, "set the coupling before adding spheres");
+    if (want && !c->d_eps) {
+        c->d_eps = dalloc_t<float>(c, (size_t)c->L.N);
+        c->d_psm_id = dalloc_t<int32_t>(c, (size_t)c->L.N);
+        if (!c->d_eps || !c->d_psm_id) return fail(c, LB_ERR_OOM, "solid fractions");
+        CK(cudaMemsetAsync(c->d_eps, 0, sizeof(float) * c->L.N, c->stream));
+        CK(cudaMemsetAsync(c->d_psm_id, 0, sizeof(int32_t) * c->L.N, c->stream));
+    }
+    c->psm = want;
+    c->L.psm = want ? 1 : 0;
+    c->L.eps = c->d_eps;
+    c->L.psm_id = c->d_psm_id;
+    lb_status s = relayout(c);
+    if (s != LB_OK) return s;
+    return LB_OK;
+}
+
+lb_status lb_get_solid_fraction(lb_ctx* c, double* eps) {
+    if (!c || !eps) return LB_ERR_INVALID;
+    CK(cudaSetDevice(c->p.device));
+    settle(c);
+    lb_status s = sync_checked(c);
+    if (s != LB_OK) return s;
+    const size_t N = (size_t)c->L.N;
+    if (!c->psm) {
+        std::fill(eps, eps + N, 0.0);
+        return LB_OK;
+    }
+    std::vector<float> h(N);
+    CK(cudaMemcpyAsync(h.data(), c->d_eps, sizeof(float) * N, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t n = 0; n < N; ++n) eps[n] = (double)h[n];
+    return LB_OK;
+}
+
 lb_status lb_set_link_options(lb_ctx* c, int32_t density_of_node, int32_t velocity_at_node) {
     if (!c || (density_of_node != 0 && density_of_node != 1) || (velocity_at_node != 0 && velocity_at_node != 1))
         return LB_ERR_INVALID;
@@ -931,6 +1030,21 @@ static void sweep_all(lb_ctx* c, int parity, cudaStream_t st) {
     launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, 0, nullptr, c->L.nz, c->L.ny, st);
 }
 
+// The start of a step of a lattice with partially saturated cells: the solid
+// fractions, the force on each sphere and its Newton-Euler update (from the
+// populations the step starts from), then the sweep, which blends the solid
+// operator into the collision of the covered cells.  Returns the launch count.
+static int psm_sweep(lb_ctx* c, const Bodies& B, int parity, cudaStream_t st) {
+    int n = 0;
+    if (c->n_psm_items > 0) {
+        launch_psm_step(B, parity, c->grid_psm, st);
+        n += 3;
+    }
+    const PsmArgs q = {c->d_eps, c->d_psm_id, c->own, c->d_par, c->d_state[parity]};
+    launch_sweep_psm(c->L, c->lambda_e, c->lambda_o, parity, q, st);
+    return n + 1;
+}
+
 // The body kernels of one step on stream st: the fused kernel (spheres), the
 // link kernel (walls and still obstacles, if any), then classify, convert and
 // rebuild, which re-classify the spheres queued by the other two (bodies near
@@ -960,10 +1074,22 @@ static int body_step(lb_ctx* c, const Bodies& B, int parity, cudaStream_t st, cu
 static void enqueue_traced_step(lb_ctx* c) {
     const int parity = (int)(c->step & 1);
     const int nk = c->par.empty() ? 1 : 5;
+    if (c->psm && c->n_psm_items > 0) {  // kind 1: solid fractions and sphere forces
+        const size_t e0 = 2 * c->ev_used.size();
+        cudaEventRecord(pool_event(c, e0), c->stream);
+        launch_psm_step(bodies_view(c), parity, c->grid_psm, c->stream);
+        c->launches += 3;
+        cudaEventRecord(pool_event(c, e0 + 1), c->stream);
+        c->ev_used.emplace_back(1, (int)e0);
+    }
     for (int k = 0; k < nk; ++k) {
         const size_t e0 = 2 * c->ev_used.size();
         cudaEventRecord(pool_event(c, e0), c->stream);
-        if (k == 0) {
+        if (k == 0 && c->psm) {
+            const PsmArgs q = {c->d_eps, c->d_psm_id, c->own, c->d_par, c->d_state[parity]};
+            launch_sweep_psm(c->L, c->lambda_e, c->lambda_o, parity, q, c->stream);
+            c->launches += 1;
+        } else if (k == 0) {
             sweep_all(c, parity, c->stream);
             c->launches += 1;
         } else if (k == 1) {
@@ -993,8 +1119,12 @@ static void enqueue_steps(lb_ctx* c, int64_t n) {
     const Bodies B = bodies_view(c);
     for (int64_t k = 0; k < n; ++k) {
         const int parity = (int)(c->step & 1);
-        sweep_all(c, parity, c->stream);
-        c->launches += 1;
+        if (c->psm) {
+            c->launches += psm_sweep(c, B, parity, c->stream);
+        } else {
+            sweep_all(c, parity, c->stream);
+            c->launches += 1;
+        }
         if (bodies) c->launches += body_step(c, B, parity, c->stream);
         c->step++;
     }
@@ -1365,6 +1495,7 @@ uint64_t bodies_hash(const lb_ctx* c) {
         mix(&q.wall_axis, sizeof(q.wall_axis));
         mix(&q.wall_index, sizeof(q.wall_index));
         mix(q.tube, sizeof(q.tube));
+        mix(&q.psm, sizeof(q.psm));
     }
     mix(&c->wca_sigma, sizeof(double));
     mix(&c->wca_eps, sizeof(double));
@@ -1516,6 +1647,12 @@ lb_status lb_restore(lb_ctx* c, const void* buf, size_t bytes) {
     // sweep (of parity step & 1) reads it
     const unsigned long long st = (unsigned long long)h.step;
     CK(cudaMemcpyAsync(c->L.sr_ctr + (st & 1), &st, sizeof(st), cudaMemcpyHostToDevice, c->stream));
+    // solid fractions are found afresh at the start of the next step; the
+    // spheres may sit elsewhere than when they were last found
+    if (c->psm) {
+        CK(cudaMemsetAsync(c->d_eps, 0, sizeof(float) * N, c->stream));
+        CK(cudaMemsetAsync(c->d_psm_id, 0, sizeof(int32_t) * N, c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));  // the caller's buffer may go once we return
     c->step = h.step;
     c->pending = false;

@@ -39,6 +39,7 @@
 #include <cooperative_groups.h>
 
 #include "lbsq_internal.cuh"
+#include "psm.cuh"
 
 namespace lbsq {
 
@@ -1787,6 +1788,127 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
 // which: 1 links, 2 classify, 3 convert, 4 rebuild, 5 tick.  The link kernel
 // gets grid_links blocks over its static item list; the box kernels walk their
 // device-built lists with grid_box blocks.
+// ---------------------------------------------------------------- partially saturated cells
+// (psm.cuh).  Per step, before the sweep of parity P: the previous step's
+// solid fractions of each sphere are cleared (its box at the step's position,
+// grown by two cells, covers where it was: a sphere moves under half a cell
+// per step), the new ones written, then the force on each sphere summed from
+// the pre-collision populations and the sphere advanced.  Items (body, block)
+// as for the box kernels.
+
+template <int MODE>  // 0: clear, 1: fill
+__global__ void __launch_bounds__(kBB) k_psm_cells(const Bodies B, int P) {
+    for (int it = blockIdx.x; it < B.n_psm_items; it += gridDim.x) {
+        const int2 item = B.psm_items[it];
+        const int k = item.x, g = item.y;
+        const BodyParams& p = B.par[k];
+        const Lattice& L = B.lats[p.lat];
+        const BodyState& s = B.state[P][k];
+        int lo[3], w[3];
+        body_box(L, p, s, lo, w);
+        if (MODE == 0)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] -= 2;
+                w[a] += 4;
+            }
+        long long b0, b1;
+        box_range((long long)w[0] * w[1] * w[2], g, p.g_box, b0, b1);
+        const int32_t id = k + 1;
+        for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+            int x, y, z;
+            box_cell(L, lo, w, b, x, y, z);
+            const int64_t c = cell_index(L, x, y, z);
+            if (MODE == 0) {
+                if (L.psm_id[c] == id) {
+                    L.psm_id[c] = 0;
+                    L.eps[c] = 0.0f;
+                }
+                continue;
+            }
+            const double d[3] = {min_image((double)x - s.pos[0], L.nx), min_image((double)y - s.pos[1], L.ny),
+                                 min_image((double)z - s.pos[2], L.nz)};
+            const double e = psm_fraction(d, p.R);
+            if (e == 0.0) continue;
+            const int32_t old = atomicCAS(L.psm_id + c, 0, id);
+            if (old != 0 && old != id) set_error(L.err, 4);  // LB_ERR_OVERLAP: two spheres in one cell
+            else L.eps[c] = (float)e;
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kBB) k_psm_force(const Bodies B) {
+    __shared__ double sm[12 * kBB + 12 * 8];
+    __shared__ double s_tot[12];
+    __shared__ int s_flag;
+    for (int it = blockIdx.x; it < B.n_psm_items; it += gridDim.x) {
+        const int2 item = B.psm_items[it];
+        const int k = item.x, g = item.y;
+        const BodyParams& p = B.par[k];
+        const Lattice& L = B.lats[p.lat];
+        const BodyState& s = B.state[P][k];
+        BodyAcc& A = B.acc[k];
+        const int G = p.g_box;
+        int lo[3], w[3];
+        body_box(L, p, s, lo, w);
+        long long b0, b1;
+        box_range((long long)w[0] * w[1] * w[2], g, G, b0, b1);
+        const int32_t id = k + 1;
+        double acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = 0.0;
+        for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+            int x, y, z;
+            box_cell(L, lo, w, b, x, y, z);
+            const int64_t c = cell_index(L, x, y, z);
+            if (L.psm_id[c] != id || L.own[c] != 0) continue;
+            double f[Q], om[Q], us[3];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = load_abs(L, read_slot(L, i, x, y, z, P), i);
+            const double d[3] = {min_image((double)x - s.pos[0], L.nx), min_image((double)y - s.pos[1], L.ny),
+                                 min_image((double)z - s.pos[2], L.nz)};
+            psm_surface_velocity(p, s, d, us);
+            const double Bw = psm_solid(f, L.rho0, L.inc, L.lambda_e, us, (double)L.eps[c], om);
+            double m[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                m[0] += om[i] * cx(i);
+                m[1] += om[i] * cy(i);
+                m[2] += om[i] * cz(i);
+            }
+            const double dF[3] = {-Bw * m[0], -Bw * m[1], -Bw * m[2]};
+            acc[0] += dF[0];
+            acc[1] += dF[1];
+            acc[2] += dF[2];
+            acc[3] += d[1] * dF[2] - d[2] * dF[1];
+            acc[4] += d[2] * dF[0] - d[0] * dF[2];
+            acc[5] += d[0] * dF[1] - d[1] * dF[0];
+            const double tr = (d[0] * dF[0] + d[1] * dF[1] + d[2] * dF[2]) * (1.0 / 3.0);
+            acc[6] -= d[0] * dF[0] - tr;
+            acc[7] -= d[1] * dF[1] - tr;
+            acc[8] -= d[2] * dF[2] - tr;
+            acc[9] -= 0.5 * (d[0] * dF[1] + d[1] * dF[0]);
+            acc[10] -= 0.5 * (d[0] * dF[2] + d[2] * dF[0]);
+            acc[11] -= 0.5 * (d[1] * dF[2] + d[2] * dF[1]);
+        }
+        block_sum_fixed<12, kBB>(acc, sm, s_tot);
+        double* part = B.part_psm + ((size_t)k * B.GB + g) * 12;
+        if (threadIdx.x < 12) part[threadIdx.x] = s_tot[threadIdx.x];
+        if (!last_block(&A.counter_links, G, &s_flag)) continue;
+        ordered_partial_sum<12>(B.part_psm + (size_t)k * B.GB * 12, G, sm, s_tot);
+        if (threadIdx.x < 32) update_body<P>(L, B, k, p, s, A, s_tot, &A, &B.state[1 - P][k]);
+        __syncthreads();
+    }
+}
+
+// The partially saturated cells of one step of parity P (three launches).
+void launch_psm_step(const Bodies& B, int parity, int grid, cudaStream_t st) {
+    k_psm_cells<0><<<grid, kBB, 0, st>>>(B, parity);
+    k_psm_cells<1><<<grid, kBB, 0, st>>>(B, parity);
+    if (parity == 0) k_psm_force<0><<<grid, kBB, 0, st>>>(B);
+    else k_psm_force<1><<<grid, kBB, 0, st>>>(B);
+}
+
 void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, int grid_box, long long* step,
                         cudaStream_t st) {
     if (which == 1) {

@@ -153,6 +153,12 @@ struct Lattice {
     // the device by the sweeps themselves (ping-pong by parity: the sweep of
     // step t reads [t & 1] = t and writes [1 - (t & 1)] = t + 1); null for a server
     unsigned long long* sr_ctr;
+    // partially saturated cells (psm.cuh): spheres couple through the solid
+    // fraction eps of each cell instead of links (0: off)
+    int psm;
+    int pad3;
+    float* eps;        // [N] solid fraction
+    int32_t* psm_id;   // [N] covering sphere (body index + 1), 0 = none
 };
 
 // Whether a lattice takes part in the current step.
@@ -269,7 +275,7 @@ struct BodyParams {
     double inv_mass, inv_inertia;
     int64_t st_off;    // first entry of the sphere's shell stencil (see k_body_fused)
     int st_count;      // stencil entries; 0 for bodies the fused kernel does not handle
-    int st_pad;
+    int psm;           // a sphere coupled by partially saturated cells (no links, no conversion)
 };
 
 struct BodyState {  // ping-pong by step parity
@@ -328,6 +334,11 @@ struct Bodies {
     const int* n_fused;      // [3]
     const uint32_t* stencil; // shell stencils of those spheres
     int* fused_done;         // clusters of a solo fused launch that finished (self-resetting)
+    // spheres coupled by partially saturated cells: items (body, block) of
+    // their boxes, and per-block partial sums [body][GB][12]
+    const int2* psm_items;
+    int n_psm_items;
+    double* part_psm;
 };
 
 // Cluster class of the fused body kernel for a lattice with nf fused spheres:
@@ -343,7 +354,7 @@ constexpr double kStencilMaxR = 400.0;
 // Whether the fused body kernel advances a body: moving-surface spheres with
 // a stencil (still obstacles are plain copies, walls never re-classify).
 inline bool fused_body(const BodyParams& b) {
-    return b.kind == BODY_SPHERE && !b.copy_only && b.R <= kStencilMaxR;
+    return b.kind == BODY_SPHERE && !b.copy_only && !b.psm && b.R <= kStencilMaxR;
 }
 
 // Scan box of a body: origin and extent.

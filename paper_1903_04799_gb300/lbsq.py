@@ -22,6 +22,8 @@ LB_ERR_DIVERGED, LB_ERR_TIMEOUT, LB_ERR_STATE, LB_ERR_CAPACITY = 5, 6, 7, 8
 LB_EQ_COMPRESSIBLE, LB_EQ_INCOMPRESSIBLE = 0, 1
 LB_ROUND_DEFAULT, LB_ROUND_NEAREST, LB_ROUND_STOCHASTIC = -1, 0, 1
 ROUNDING = {"default": LB_ROUND_DEFAULT, "nearest": LB_ROUND_NEAREST, "stochastic": LB_ROUND_STOCHASTIC}
+LB_COUPLE_LINKS, LB_COUPLE_PSM = 0, 1
+COUPLING = {"links": LB_COUPLE_LINKS, "psm": LB_COUPLE_PSM}
 LB_BGK, LB_TRT = 0, 1
 LB_F64, LB_F32, LB_F16DEV, LB_BF16DEV = 0, 1, 2, 3
 STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16dev": LB_F16DEV, "bf16dev": LB_BF16DEV}
@@ -91,6 +93,8 @@ SIGNATURES = {
     "lb_set_contact": (C.c_int, [_CTX, C.c_double, C.c_double]),
     "lb_set_force_average": (C.c_int, [_CTX, C.c_int32]),
     "lb_set_link_options": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
+    "lb_set_coupling": (C.c_int, [_CTX, C.c_int32]),
+    "lb_get_solid_fraction": (C.c_int, [_CTX, _DP]),
     "lb_set_fields": (C.c_int, [_CTX, _DP, _DP]),
     "lb_set_populations": (C.c_int, [_CTX, _DP]),
     "lb_get_populations": (C.c_int, [_CTX, _DP]),
@@ -213,6 +217,16 @@ def lb_set_force_average(ctx, on: bool):
 def lb_set_link_options(ctx, density_of_node: bool, velocity_at_node: bool):
     _check(ctx, load().lb_set_link_options(ctx, int(bool(density_of_node)), int(bool(velocity_at_node))),
            "lb_set_link_options")
+
+
+def lb_set_coupling(ctx, coupling: int):
+    _check(ctx, load().lb_set_coupling(ctx, int(coupling)), "lb_set_coupling")
+
+
+def lb_get_solid_fraction(ctx, n: int):
+    eps = np.empty(n, np.float64)
+    _check(ctx, load().lb_get_solid_fraction(ctx, _dp(eps)), "lb_get_solid_fraction")
+    return eps
 
 
 def lb_set_fields(ctx, rho, u):
@@ -568,6 +582,11 @@ class Lattice:
     def set_link_options(self, density_of_node=False, velocity_at_node=False):
         lb_set_link_options(self.ctx, density_of_node, velocity_at_node)
 
+    def set_coupling(self, coupling="links"):
+        """'links' (bounce-back on links, the default) or 'psm' (partially
+        saturated cells); before the first sphere (see lb_set_coupling)."""
+        lb_set_coupling(self.ctx, COUPLING[coupling] if isinstance(coupling, str) else int(coupling))
+
     def set_fields(self, rho, u):
         lb_set_fields(self.ctx, np.reshape(rho, -1), np.reshape(u, (3, -1)))
 
@@ -598,6 +617,9 @@ class Lattice:
 
     def owner(self):
         return lb_get_owner(self.ctx, self.N)
+
+    def solid_fraction(self):
+        return lb_get_solid_fraction(self.ctx, self.N)
 
     def force_torque(self, oid):
         return lb_get_force_torque(self.ctx, oid)

@@ -65,5 +65,7 @@ def test_params_default_and_invalid_arguments(lib):
     assert lib.lb_step(None, 1) == lbsq.LB_ERR_INVALID
     assert lib.lb_set_force_average(None, 1) == lbsq.LB_ERR_INVALID
     assert lib.lb_set_link_options(None, 1, 0) == lbsq.LB_ERR_INVALID
+    assert lib.lb_set_coupling(None, lbsq.LB_COUPLE_PSM) == lbsq.LB_ERR_INVALID
+    assert lib.lb_get_solid_fraction(None, None) == lbsq.LB_ERR_INVALID
     assert lbsq.lb_params_default().rounding == lbsq.LB_ROUND_DEFAULT
     assert lib.lb_last_error(None) == b"null context"
