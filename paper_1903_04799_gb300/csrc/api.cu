@@ -12,7 +12,6 @@
 
 #include "../../include/lbsq.h"
 #include "lbsq_internal.cuh"
-#include "psm.cuh"
 
 namespace lbsq {
 void launch_sweep(const Lattice& L, double lambda_e, double lambda_o, int parity, int variant, int zmode,
@@ -39,9 +38,8 @@ void launch_tube_overlap(const Lattice& L, const int32_t* own, const int* kind, 
                          cudaStream_t st);
 void launch_tube_claim(const Lattice& L, int32_t* own, const BodyParams& q, int id, cudaStream_t st);
 void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, cudaStream_t st);
-void launch_psm_step(const Bodies& B, int parity, int grid, cudaStream_t st);
-void launch_sweep_psm(const Lattice& L, double lambda_e, double lambda_o, int parity, const PsmArgs& q,
-                      cudaStream_t st);
+void launch_psm_cover(const Bodies& B, int parity, int grid, bool f64, cudaStream_t st);
+void launch_psm_scatter(const Bodies& B, int parity, int grid, cudaStream_t st);
 }  // namespace lbsq
 
 using namespace lbsq;
@@ -91,12 +89,17 @@ struct lb_ctx {
     int force_avg = 0;  // lb_set_force_average
     // spheres coupled by partially saturated cells (lb_set_coupling): the
     // solid fraction and covering sphere per cell, the (body, block) items of
-    // the spheres' boxes and their per-block force partials
+    // the spheres' boxes, their per-block force partials and the covered
+    // cells' post-collision populations
     bool psm = false;
     float* d_eps = nullptr;
     int32_t* d_psm_id = nullptr;
     int2* d_psm_items = nullptr;
     double* d_part_psm = nullptr;
+    double* d_psm_out = nullptr;
+    int32_t* d_psm_cell = nullptr;
+    int32_t* d_psm_count = nullptr;
+    int64_t psm_cap = 0, psm_out_alloc = 0;
     int n_psm_items = 0, psm_alloc = 0, grid_psm = 1;
     // scratch
     double* d_mass_part = nullptr;
@@ -221,6 +224,10 @@ Bodies bodies_view(const lb_ctx* c) {
     B.psm_items = c->d_psm_items;
     B.n_psm_items = c->n_psm_items;
     B.part_psm = c->d_part_psm;
+    B.psm_out = c->d_psm_out;
+    B.psm_cell = c->d_psm_cell;
+    B.psm_count = c->d_psm_count;
+    B.psm_cap = c->psm_cap;
     return B;
 }
 
@@ -334,6 +341,7 @@ lb_status relayout(lb_ctx* c) {
     std::vector<int2> fused;
     std::vector<int2> psm_items;
     std::vector<uint32_t> stencil;
+    int64_t psm_cap = 0;
     for (int k = 0; k < nb; ++k) {
         BodyParams& b = c->par[k];
         b.link_off = off;
@@ -368,8 +376,12 @@ lb_status relayout(lb_ctx* c) {
         gl = std::max(gl, b.g_links);
         gb = std::max(gb, b.g_box);
         sum_gb += b.g_box;
-        if (b.psm)
-            for (int g = 0; g < b.g_box; ++g) psm_items.push_back(make_int2(k, g));
+        b.psm_off = psm_cap;
+        if (b.psm) {  // one item per chunk of the box
+            const int64_t nq = (box + kPsmChunk - 1) / kPsmChunk;
+            for (int64_t q = 0; q < nq; ++q) psm_items.push_back(make_int2(k, (int)q));
+            psm_cap += nq * kPsmChunk;
+        }
         else if (!fused_body(b))
             for (int g = 0; g < b.g_links; ++g) items.push_back(make_int2(k, g));
     }
@@ -411,17 +423,28 @@ lb_status relayout(lb_ctx* c) {
     if (!c->d_part_links || !c->d_part_conv || !c->d_part_count) return fail(c, LB_ERR_OOM, "partials");
     if (!psm_items.empty()) {
         dfree(c, c->d_part_psm);
-        c->d_part_psm = dalloc_t<double>(c, (size_t)nb * c->G_box * 12);
+        c->d_part_psm = dalloc_t<double>(c, (size_t)(psm_cap / kPsmChunk) * 12);
         if ((int)psm_items.size() > c->psm_alloc) {
             dfree(c, c->d_psm_items);
             c->d_psm_items = dalloc_t<int2>(c, psm_items.size());
             c->psm_alloc = c->d_psm_items ? (int)psm_items.size() : 0;
         }
-        if (!c->d_part_psm || !c->d_psm_items) return fail(c, LB_ERR_OOM, "partially saturated cells");
+        if (psm_cap > c->psm_out_alloc) {
+            dfree(c, c->d_psm_out);
+            dfree(c, c->d_psm_cell);
+            dfree(c, c->d_psm_count);
+            c->d_psm_out = dalloc_t<double>(c, (size_t)Q * psm_cap);
+            c->d_psm_cell = dalloc_t<int32_t>(c, (size_t)psm_cap);
+            c->d_psm_count = dalloc_t<int32_t>(c, (size_t)(psm_cap / kPsmChunk));
+            c->psm_out_alloc = c->d_psm_out && c->d_psm_cell && c->d_psm_count ? psm_cap : 0;
+        }
+        if (!c->d_part_psm || !c->d_psm_items || !c->d_psm_out || !c->d_psm_cell || !c->d_psm_count)
+            return fail(c, LB_ERR_OOM, "partially saturated cells");
         CK(cudaMemcpyAsync(c->d_psm_items, psm_items.data(), sizeof(int2) * psm_items.size(),
                            cudaMemcpyHostToDevice, c->stream));
     }
     c->n_psm_items = (int)psm_items.size();
+    c->psm_cap = psm_cap;
     c->grid_psm = std::max(1, std::min(c->n_psm_items, 4 * c->n_sm));
     // work lists: every body appears at most once per step in each list
     const int need = std::max<int>((int)items.size(), sum_gb);
@@ -1030,19 +1053,19 @@ static void sweep_all(lb_ctx* c, int parity, cudaStream_t st) {
     launch_sweep(c->L, c->lambda_e, c->lambda_o, parity, c->sweep_variant, 0, nullptr, c->L.nz, c->L.ny, st);
 }
 
-// The start of a step of a lattice with partially saturated cells: the solid
-// fractions, the force on each sphere and its Newton-Euler update (from the
-// populations the step starts from), then the sweep, which blends the solid
-// operator into the collision of the covered cells.  Returns the launch count.
+// The sweep of a lattice with partially saturated cells: before it the
+// solid fractions, the covered cells' collisions and each sphere's force and
+// update (from the populations the step starts from); after it the covered
+// cells' results over the sweep's.  Returns the launch count.
 static int psm_sweep(lb_ctx* c, const Bodies& B, int parity, cudaStream_t st) {
-    int n = 0;
-    if (c->n_psm_items > 0) {
-        launch_psm_step(B, parity, c->grid_psm, st);
-        n += 3;
+    if (c->n_psm_items == 0) {
+        sweep_all(c, parity, st);
+        return 1;
     }
-    const PsmArgs q = {c->d_eps, c->d_psm_id, c->own, c->d_par, c->d_state[parity]};
-    launch_sweep_psm(c->L, c->lambda_e, c->lambda_o, parity, q, st);
-    return n + 1;
+    launch_psm_cover(B, parity, c->grid_psm, c->p.storage == LB_F64, st);
+    sweep_all(c, parity, st);
+    launch_psm_scatter(B, parity, c->grid_psm, st);
+    return 4;
 }
 
 // The body kernels of one step on stream st: the fused kernel (spheres), the
@@ -1074,22 +1097,27 @@ static int body_step(lb_ctx* c, const Bodies& B, int parity, cudaStream_t st, cu
 static void enqueue_traced_step(lb_ctx* c) {
     const int parity = (int)(c->step & 1);
     const int nk = c->par.empty() ? 1 : 5;
-    if (c->psm && c->n_psm_items > 0) {  // kind 1: solid fractions and sphere forces
+    const bool psm = c->psm && c->n_psm_items > 0;
+    if (psm) {  // kind 1: solid fractions, covered cells, sphere forces
         const size_t e0 = 2 * c->ev_used.size();
         cudaEventRecord(pool_event(c, e0), c->stream);
-        launch_psm_step(bodies_view(c), parity, c->grid_psm, c->stream);
-        c->launches += 3;
+        launch_psm_cover(bodies_view(c), parity, c->grid_psm, c->p.storage == LB_F64, c->stream);
+        c->launches += 2;
         cudaEventRecord(pool_event(c, e0 + 1), c->stream);
         c->ev_used.emplace_back(1, (int)e0);
     }
     for (int k = 0; k < nk; ++k) {
+        if (k == 1 && psm) {  // kind 1: the covered cells' results
+            const size_t e0 = 2 * c->ev_used.size();
+            cudaEventRecord(pool_event(c, e0), c->stream);
+            launch_psm_scatter(bodies_view(c), parity, c->grid_psm, c->stream);
+            c->launches += 1;
+            cudaEventRecord(pool_event(c, e0 + 1), c->stream);
+            c->ev_used.emplace_back(1, (int)e0);
+        }
         const size_t e0 = 2 * c->ev_used.size();
         cudaEventRecord(pool_event(c, e0), c->stream);
-        if (k == 0 && c->psm) {
-            const PsmArgs q = {c->d_eps, c->d_psm_id, c->own, c->d_par, c->d_state[parity]};
-            launch_sweep_psm(c->L, c->lambda_e, c->lambda_o, parity, q, c->stream);
-            c->launches += 1;
-        } else if (k == 0) {
+        if (k == 0) {
             sweep_all(c, parity, c->stream);
             c->launches += 1;
         } else if (k == 1) {

@@ -45,6 +45,7 @@ namespace lbsq {
 
 constexpr int kLB = 128;  // threads of the link kernel
 constexpr int kBB = 256;  // threads of the box kernels
+static_assert(kBB == kPsmChunk, "a chunk of partially saturated cells is one block of the box kernels");
 
 // ---------------------------------------------------------------- reductions
 
@@ -1796,117 +1797,290 @@ __global__ void __launch_bounds__(kFT, 2) k_body_fused(const Bodies B, int cls, 
 // the pre-collision populations and the sphere advanced.  Items (body, block)
 // as for the box kernels.
 
-template <int MODE>  // 0: clear, 1: fill
-__global__ void __launch_bounds__(kBB) k_psm_cells(const Bodies B, int P) {
+// Partially saturated cells (psm.cuh).  A step of parity P of a lattice
+// whose spheres couple this way runs
+//   k_psm_clear       the coverage the last step recorded, over each
+//                     sphere's box grown by 2 (a sphere moves < 1/2 a step);
+//   k_psm_cover<P>    each sphere's box at the state the step starts from,
+//                     in chunks of kBB cells: the solid fraction and the
+//                     covering sphere of every cell, and for each covered
+//                     fluid cell the blended collision of the populations the
+//                     step starts from (kept in psm_out) and its share of the
+//                     force, torque and stresslet; the last block of a
+//                     sphere sums the chunks' shares in chunk order and
+//                     updates the sphere;
+//   the sweep         every cell as usual, in place;
+//   k_psm_scatter<P>  the covered fluid cells' results from psm_out into
+//                     their write slots, over the sweep's.
+// A covered cell's read and write slots belong to it alone within a sweep,
+// so the sweep's own result for it is simply overwritten.
+//
+// Within a chunk the work is compacted, in cell order, so that warps run
+// full: the cells to sample are taken one per warp (32 lanes share the 512
+// sample points), and the covered fluid cells one per thread.
+
+// Chunks of sphere p's box (kBB cells each) and the first one's index among
+// all spheres' chunks.
+__device__ __forceinline__ int psm_chunks(const BodyParams& p) {
+    return (int)(((long long)p.box_w[0] * p.box_w[1] * p.box_w[2] + kBB - 1) / kBB);
+}
+
+// psm_out entry t of chunk q of sphere p, population i.
+__device__ __forceinline__ int64_t psm_entry(const Bodies& B, const BodyParams& p, int q, int t, int i) {
+    return (int64_t)i * B.psm_cap + p.psm_off + (int64_t)q * kBB + t;
+}
+
+// Write slot of population i of cell (x, y, z) in a sweep of parity q.
+__device__ __forceinline__ int64_t write_slot(const Lattice& L, int i, int x, int y, int z, int q) {
+    if (q == 0) return (int64_t)opp(i) * L.Np + cell_index(L, x, y, z);
+    const int xs = wrapi(x + cx(i), L.nx), ys = wrapi(y + cy(i), L.ny), zs = wrapi(z + cz(i), L.nz);
+    return (int64_t)i * L.Np + cell_index(L, xs, ys, zs);
+}
+
+// Ordered compaction within a block: the position of a kept thread among the
+// kept threads of lower index, and (return) how many are kept.  sw: kBB / 32
+// ints of shared memory.  Ends with the block synchronised.
+__device__ __forceinline__ int block_compact(bool keep, int* sw, int* pos) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) sw[wid] = __popc(bal);
+    __syncthreads();
+    int off = 0, total = 0;
+    for (int w = 0; w < kBB / 32; ++w) {
+        off += w < wid ? sw[w] : 0;
+        total += sw[w];
+    }
+    *pos = off + __popc(bal & ((1u << lane) - 1u));
+    __syncthreads();
+    return total;
+}
+
+// Fixed-order sum of G partials of K values each (any G), staged through
+// shared memory kBB partials at a time: K x SEG threads each keep a running
+// sum over their run of each pass, in pass order, then K threads add the SEG
+// run sums.  sm: K * kBB + K * 8 doubles of shared memory.
+template <int K>
+__device__ __forceinline__ void ordered_sum_staged(const double* part, int G, double* sm, double* out) {
+    constexpr int SEG = 8, LEN = kBB / SEG;
+    double a = 0.0;  // thread t < K * SEG: component t / SEG, run t % SEG
+    for (int base = 0; base < G; base += kBB) {
+        const int n = G - base < kBB ? G - base : kBB;
+        for (int t = threadIdx.x; t < n * K; t += blockDim.x) sm[t] = __ldcg(part + (size_t)base * K + t);
+        __syncthreads();
+        if ((int)threadIdx.x < K * SEG) {
+            const int c = threadIdx.x / SEG, sg = threadIdx.x % SEG;
+            for (int g = sg * LEN; g < (sg + 1) * LEN && g < n; ++g) a += sm[g * K + c];
+        }
+        __syncthreads();
+    }
+    double* sm2 = sm + K * kBB;
+    if ((int)threadIdx.x < K * SEG) sm2[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double r = 0.0;
+        for (int sg = 0; sg < SEG; ++sg) r += sm2[threadIdx.x * SEG + sg];
+        out[threadIdx.x] = r;
+    }
+    __syncthreads();
+}
+
+// Step (4) of k_psm_cover for covered fluid cell t of chunk q at offset d
+// (entry threadIdx.x of the chunk): the blended collision in V (FP64 for
+// FP64 storage, FP32 for the others) of the deviations the step starts from,
+// kept in psm_out, and the cell's force, torque and stresslet shares in acc.
+template <class V, int P>
+__device__ __forceinline__ void psm_cell_work(const Lattice& L, const Bodies& B, const BodyParams& p,
+                                              const BodyState& s, int q, int t, const int lo[3], const int w[3],
+                                              const V d[3], float eps, double acc[12]) {
+    int x, y, z;
+    box_cell(L, lo, w, (long long)q * kBB + t, x, y, z);
+    V g[Q], out[Q], us[3], m[3] = {V(0), V(0), V(0)};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int64_t slot = read_slot(L, i, x, y, z, P);
+        if constexpr (sizeof(V) == 8) g[i] = ((const double*)L.F)[slot];
+        else g[i] = load_dev(L, slot);
+    }
+    psm_surface_velocity<V>(p, s, d, us);
+    const V Bw = psm_update<V>(g, (V)L.rho0, L.inc, (V)L.lambda_e, (V)L.lambda_o, us, (V)eps, out, m);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) B.psm_out[psm_entry(B, p, q, threadIdx.x, i)] = (double)out[i];
+    B.psm_cell[p.psm_off + (int64_t)q * kBB + threadIdx.x] = t;
+    const V dF[3] = {-Bw * m[0], -Bw * m[1], -Bw * m[2]};
+    const V tr = (d[0] * dF[0] + d[1] * dF[1] + d[2] * dF[2]) * V(1.0 / 3.0);
+    const V a[12] = {dF[0], dF[1], dF[2],
+                     d[1] * dF[2] - d[2] * dF[1], d[2] * dF[0] - d[0] * dF[2], d[0] * dF[1] - d[1] * dF[0],
+                     -(d[0] * dF[0] - tr), -(d[1] * dF[1] - tr), -(d[2] * dF[2] - tr),
+                     V(-0.5) * (d[0] * dF[1] + d[1] * dF[0]), V(-0.5) * (d[0] * dF[2] + d[2] * dF[0]),
+                     V(-0.5) * (d[1] * dF[2] + d[2] * dF[1])};
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = (double)a[c];
+}
+
+__global__ void __launch_bounds__(kBB) k_psm_clear(const Bodies B, int P) {
     for (int it = blockIdx.x; it < B.n_psm_items; it += gridDim.x) {
         const int2 item = B.psm_items[it];
-        const int k = item.x, g = item.y;
+        const int k = item.x, q = item.y;
         const BodyParams& p = B.par[k];
         const Lattice& L = B.lats[p.lat];
-        const BodyState& s = B.state[P][k];
         int lo[3], w[3];
-        body_box(L, p, s, lo, w);
-        if (MODE == 0)
-            for (int a = 0; a < 3; ++a) {
-                lo[a] -= 2;
-                w[a] += 4;
-            }
+        body_box(L, p, B.state[P][k], lo, w);
+        for (int a = 0; a < 3; ++a) {
+            lo[a] -= 2;
+            w[a] += 4;
+        }
         long long b0, b1;
-        box_range((long long)w[0] * w[1] * w[2], g, p.g_box, b0, b1);
+        box_range((long long)w[0] * w[1] * w[2], q, psm_chunks(p), b0, b1);
         const int32_t id = k + 1;
         for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
             int x, y, z;
             box_cell(L, lo, w, b, x, y, z);
             const int64_t c = cell_index(L, x, y, z);
-            if (MODE == 0) {
-                if (L.psm_id[c] == id) {
-                    L.psm_id[c] = 0;
-                    L.eps[c] = 0.0f;
-                }
-                continue;
+            if (L.psm_id[c] == id) {
+                L.psm_id[c] = 0;
+                L.eps[c] = 0.0f;
             }
-            const double d[3] = {min_image((double)x - s.pos[0], L.nx), min_image((double)y - s.pos[1], L.ny),
-                                 min_image((double)z - s.pos[2], L.nz)};
-            const double e = psm_fraction(d, p.R);
-            if (e == 0.0) continue;
-            const int32_t old = atomicCAS(L.psm_id + c, 0, id);
-            if (old != 0 && old != id) set_error(L.err, 4);  // LB_ERR_OVERLAP: two spheres in one cell
-            else L.eps[c] = (float)e;
         }
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(kBB) k_psm_force(const Bodies B) {
+template <int P, class V>
+__global__ void __launch_bounds__(kBB, 2) k_psm_cover(const Bodies B) {
     __shared__ double sm[12 * kBB + 12 * 8];
     __shared__ double s_tot[12];
     __shared__ int s_flag;
+    __shared__ int s_w[kBB / 32];
+    __shared__ int s_list[kBB];
+    __shared__ float s_eps[kBB];
+    __shared__ double s_d[3][kBB];  // each cell's offset from the centre
+    __shared__ float s_df[3][kBB];  // the same in FP32
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int it = blockIdx.x; it < B.n_psm_items; it += gridDim.x) {
         const int2 item = B.psm_items[it];
-        const int k = item.x, g = item.y;
+        const int k = item.x, q = item.y;
         const BodyParams& p = B.par[k];
         const Lattice& L = B.lats[p.lat];
         const BodyState& s = B.state[P][k];
         BodyAcc& A = B.acc[k];
-        const int G = p.g_box;
         int lo[3], w[3];
         body_box(L, p, s, lo, w);
-        long long b0, b1;
-        box_range((long long)w[0] * w[1] * w[2], g, G, b0, b1);
+        const long long nbox = (long long)w[0] * w[1] * w[2];
         const int32_t id = k + 1;
+        // (1) this thread's cell: its offset, the shortcut, the cells to sample
+        const long long b = (long long)q * kBB + threadIdx.x;
+        int x = 0, y = 0, z = 0, cls = 0;
+        double d[3] = {0.0, 0.0, 0.0};
+        if (b < nbox) {
+            box_cell(L, lo, w, b, x, y, z);
+            d[0] = min_image((double)x - s.pos[0], L.nx);
+            d[1] = min_image((double)y - s.pos[1], L.ny);
+            d[2] = min_image((double)z - s.pos[2], L.nz);
+            cls = psm_class(d, p.R);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            s_d[a][threadIdx.x] = d[a];
+            s_df[a][threadIdx.x] = (float)d[a];
+        }
+        s_eps[threadIdx.x] = cls == 1 ? 1.0f : 0.0f;
+        int pos;
+        const int nsample = block_compact(cls == 2, s_w, &pos);
+        if (cls == 2) s_list[pos] = threadIdx.x;
+        __syncthreads();
+        // (2) sampling, one cell per warp
+        const float2 band = psm_screen(p.R);
+        for (int j = wid; j < nsample; j += kBB / 32) {
+            const int t = s_list[j];
+            const double dt[3] = {s_d[0][t], s_d[1][t], s_d[2][t]};
+            const float ft[3] = {s_df[0][t], s_df[1][t], s_df[2][t]};
+            const int n = __reduce_add_sync(0xffffffffu, psm_lane_count(dt, ft, p.R, band, lane));
+            if (lane == 0) s_eps[t] = n * (1.0f / 512.0f);
+        }
+        __syncthreads();
+        // (3) record the coverage; the covered fluid cells
+        const float e = s_eps[threadIdx.x];
+        bool keep = false;
+        if (e > 0.0f) {
+            const int64_t c = cell_index(L, x, y, z);
+            const int32_t old = atomicCAS(L.psm_id + c, 0, id);
+            if (old != 0 && old != id) {
+                set_error(L.err, 4);  // LB_ERR_OVERLAP: two spheres in one cell
+            } else {
+                L.eps[c] = e;
+                keep = L.own[c] == 0;  // a wall cell stays a wall cell
+            }
+        }
+        const int ncov = block_compact(keep, s_w, &pos);
+        if (keep) s_list[pos] = threadIdx.x;
+        __syncthreads();
+        // (4) the covered fluid cells, one per thread, in cell order
         double acc[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) acc[c] = 0.0;
-        for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
-            int x, y, z;
-            box_cell(L, lo, w, b, x, y, z);
-            const int64_t c = cell_index(L, x, y, z);
-            if (L.psm_id[c] != id || L.own[c] != 0) continue;
-            double f[Q], om[Q], us[3];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) f[i] = load_abs(L, read_slot(L, i, x, y, z, P), i);
-            const double d[3] = {min_image((double)x - s.pos[0], L.nx), min_image((double)y - s.pos[1], L.ny),
-                                 min_image((double)z - s.pos[2], L.nz)};
-            psm_surface_velocity(p, s, d, us);
-            const double Bw = psm_solid(f, L.rho0, L.inc, L.lambda_e, us, (double)L.eps[c], om);
-            double m[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                m[0] += om[i] * cx(i);
-                m[1] += om[i] * cy(i);
-                m[2] += om[i] * cz(i);
+        if ((int)threadIdx.x < ncov) {
+            const int t = s_list[threadIdx.x];
+            V dv[3];
+            if constexpr (sizeof(V) == 8) {
+                for (int a = 0; a < 3; ++a) dv[a] = s_d[a][t];
+            } else {
+                for (int a = 0; a < 3; ++a) dv[a] = s_df[a][t];
             }
-            const double dF[3] = {-Bw * m[0], -Bw * m[1], -Bw * m[2]};
-            acc[0] += dF[0];
-            acc[1] += dF[1];
-            acc[2] += dF[2];
-            acc[3] += d[1] * dF[2] - d[2] * dF[1];
-            acc[4] += d[2] * dF[0] - d[0] * dF[2];
-            acc[5] += d[0] * dF[1] - d[1] * dF[0];
-            const double tr = (d[0] * dF[0] + d[1] * dF[1] + d[2] * dF[2]) * (1.0 / 3.0);
-            acc[6] -= d[0] * dF[0] - tr;
-            acc[7] -= d[1] * dF[1] - tr;
-            acc[8] -= d[2] * dF[2] - tr;
-            acc[9] -= 0.5 * (d[0] * dF[1] + d[1] * dF[0]);
-            acc[10] -= 0.5 * (d[0] * dF[2] + d[2] * dF[0]);
-            acc[11] -= 0.5 * (d[1] * dF[2] + d[2] * dF[1]);
+            psm_cell_work<V, P>(L, B, p, s, q, t, lo, w, dv, s_eps[t], acc);
         }
+        const int64_t chunk = p.psm_off / kBB + q;
+        if (threadIdx.x == 0) B.psm_count[chunk] = ncov;
         block_sum_fixed<12, kBB>(acc, sm, s_tot);
-        double* part = B.part_psm + ((size_t)k * B.GB + g) * 12;
-        if (threadIdx.x < 12) part[threadIdx.x] = s_tot[threadIdx.x];
-        if (!last_block(&A.counter_links, G, &s_flag)) continue;
-        ordered_partial_sum<12>(B.part_psm + (size_t)k * B.GB * 12, G, sm, s_tot);
+        if (threadIdx.x < 12) B.part_psm[chunk * 12 + threadIdx.x] = s_tot[threadIdx.x];
+        if (!last_block(&A.counter_links, psm_chunks(p), &s_flag)) continue;
+        ordered_sum_staged<12>(B.part_psm + (p.psm_off / kBB) * 12, psm_chunks(p), sm, s_tot);
         if (threadIdx.x < 32) update_body<P>(L, B, k, p, s, A, s_tot, &A, &B.state[1 - P][k]);
         __syncthreads();
     }
 }
 
-// The partially saturated cells of one step of parity P (three launches).
-void launch_psm_step(const Bodies& B, int parity, int grid, cudaStream_t st) {
-    k_psm_cells<0><<<grid, kBB, 0, st>>>(B, parity);
-    k_psm_cells<1><<<grid, kBB, 0, st>>>(B, parity);
-    if (parity == 0) k_psm_force<0><<<grid, kBB, 0, st>>>(B);
-    else k_psm_force<1><<<grid, kBB, 0, st>>>(B);
+template <int P>
+__global__ void __launch_bounds__(kBB) k_psm_scatter(const Bodies B) {
+    for (int it = blockIdx.x; it < B.n_psm_items; it += gridDim.x) {
+        const int2 item = B.psm_items[it];
+        const int k = item.x, q = item.y;
+        const BodyParams& p = B.par[k];
+        const Lattice& L = B.lats[p.lat];
+        const int n = B.psm_count[p.psm_off / kBB + q];
+        if ((int)threadIdx.x >= n) continue;
+        int lo[3], w[3];
+        body_box(L, p, B.state[P][k], lo, w);  // the box k_psm_cover<P> covered
+        const int t = B.psm_cell[p.psm_off + (int64_t)q * kBB + threadIdx.x];
+        int x, y, z;
+        box_cell(L, lo, w, (long long)q * kBB + t, x, y, z);
+        if (L.storage == ST_F64) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                ((double*)L.F)[write_slot(L, i, x, y, z, P)] = B.psm_out[psm_entry(B, p, q, threadIdx.x, i)];
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                store_dev(L, write_slot(L, i, x, y, z, P), (float)B.psm_out[psm_entry(B, p, q, threadIdx.x, i)]);
+        }
+    }
+}
+
+// Before the sweep of a step of parity P: clear and cover (two launches);
+// f64: the lattice stores FP64 populations.
+void launch_psm_cover(const Bodies& B, int parity, int grid, bool f64, cudaStream_t st) {
+    k_psm_clear<<<grid, kBB, 0, st>>>(B, parity);
+    if (f64) {
+        if (parity == 0) k_psm_cover<0, double><<<grid, kBB, 0, st>>>(B);
+        else k_psm_cover<1, double><<<grid, kBB, 0, st>>>(B);
+    } else {
+        if (parity == 0) k_psm_cover<0, float><<<grid, kBB, 0, st>>>(B);
+        else k_psm_cover<1, float><<<grid, kBB, 0, st>>>(B);
+    }
+}
+
+// After the sweep: the covered cells' results (one launch).
+void launch_psm_scatter(const Bodies& B, int parity, int grid, cudaStream_t st) {
+    if (parity == 0) k_psm_scatter<0><<<grid, kBB, 0, st>>>(B);
+    else k_psm_scatter<1><<<grid, kBB, 0, st>>>(B);
 }
 
 void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, int grid_box, long long* step,

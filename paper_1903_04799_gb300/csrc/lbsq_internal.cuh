@@ -276,6 +276,8 @@ struct BodyParams {
     int64_t st_off;    // first entry of the sphere's shell stencil (see k_body_fused)
     int st_count;      // stencil entries; 0 for bodies the fused kernel does not handle
     int psm;           // a sphere coupled by partially saturated cells (no links, no conversion)
+    int pad_psm;
+    int64_t psm_off;   // its first entry in Bodies::psm_out (a multiple of the chunk size)
 };
 
 struct BodyState {  // ping-pong by step parity
@@ -339,6 +341,14 @@ struct Bodies {
     const int2* psm_items;
     int n_psm_items;
     double* part_psm;
+    // the covered fluid cells of each chunk of kBB box cells, compacted in
+    // cell order: post-collision populations [Q][psm_cap], the cell within
+    // the chunk [psm_cap], the count per chunk [psm_cap / kBB]; sphere k's
+    // chunk q starts at entry psm_off(k) + q kBB
+    double* psm_out;
+    int32_t* psm_cell;
+    int32_t* psm_count;
+    int64_t psm_cap;
 };
 
 // Cluster class of the fused body kernel for a lattice with nf fused spheres:
@@ -350,6 +360,10 @@ inline int fused_class(int nf) { return nf <= 8 ? 0 : (nf <= 64 ? 1 : 2); }
 
 // Largest sphere radius with a shell stencil (stencil offsets fit 10 bits).
 constexpr double kStencilMaxR = 400.0;
+
+// Cells per chunk of a sphere's box under partially saturated cells (one
+// block of the box kernels per chunk).
+constexpr int kPsmChunk = 256;
 
 // Whether the fused body kernel advances a body: moving-surface spheres with
 // a stencil (still obstacles are plain copies, walls never re-classify).

@@ -7,7 +7,6 @@
 // geometry-free: solid cells are swept too (their slots are private to them,
 // and every slot a fluid cell reads from a solid neighbour is rewritten by the
 // link kernel after the sweep), so no flag field is read.
-#include "psm.cuh"
 #include "sweep_body.cuh"
 
 namespace lbsq {
@@ -62,91 +61,6 @@ __global__ void __launch_bounds__(P == 0 ? 256 : 192, 2) k_sweep4r(const SweepAr
     if (z < 0) return;  // the whole block
     const int y = sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
     sweep_four_rows<S, P, O32>(a, y < 0 ? 0 : y, z, y >= 0, rowbuf, skey);
-}
-
-// One cell of a sweep with partially saturated cells (psm.cuh): the cell's
-// populations (read slots of parity P) as absolute FP64 values, the TRT
-// collision and the solid operator blended by B, the result stored as the
-// deviation in the storage's format (rounded to nearest) in the write slots.
-template <int S, int P>
-__device__ __forceinline__ void psm_cell(const SweepArgs& a, const PsmArgs& q, int x, int y, int z, float eps) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-    const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
-    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
-    using T = typename StoreT<S>::T;
-    T* F = (T*)a.F;
-    const int64_t Np = a.Np;
-    auto slot = [&](int plane, int dx, int dy, int dz) -> int64_t {
-        return (int64_t)plane * Np + (xs[1 + dx] + (int64_t)nx * (ys[1 + dy] + (int64_t)ny * zs[1 + dz]));
-    };
-    double f[Q], fc[Q], om[Q], us[3];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int64_t off = P == 0 ? slot(i, 0, 0, 0) : slot(opp(i), -cx(i), -cy(i), -cz(i));
-        double g;
-        if constexpr (S == ST_F64) g = F[off];
-        else if constexpr (S == ST_F32) g = (double)F[off];
-        else if constexpr (S == ST_F16) g = (double)(__half2float(F[off]) * a.inv_scale);
-        else g = (double)(__bfloat162float(F[off]) * a.inv_scale);
-        f[i] = wgt(i) * a.rho0 + g;
-        fc[i] = f[i];
-    }
-    collide_trt<double, false>(fc, a.K, a.rho0);
-    const int k = q.psm_id[x + (int64_t)nx * (y + (int64_t)ny * z)] - 1;
-    const BodyState& s = q.state[k];
-    const BodyParams& p = q.par[k];
-    const double d[3] = {min_image((double)x - s.pos[0], nx), min_image((double)y - s.pos[1], ny),
-                         min_image((double)z - s.pos[2], nz)};
-    psm_surface_velocity(p, s, d, us);
-    const double Bw = psm_solid(f, a.rho0, a.K.inc, a.lambda_e, us, (double)eps, om);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const double out = f[i] + (1.0 - Bw) * (fc[i] - f[i]) + Bw * om[i] - wgt(i) * a.rho0;
-        const int64_t off = P == 0 ? slot(opp(i), 0, 0, 0) : slot(i, cx(i), cy(i), cz(i));
-        if constexpr (S == ST_F64) F[off] = out;
-        else if constexpr (S == ST_F32) F[off] = (float)out;
-        else if constexpr (S == ST_F16) F[off] = __float2half_rn((float)out * a.scale);
-        else F[off] = __float2bfloat16_rn((float)out * a.scale);
-    }
-}
-
-// Sweep with partially saturated cells: cells with eps = 0 (and solid cells
-// of walls) take the ordinary one-cell form, the others psm_cell.
-template <int S, int P>
-__global__ void __launch_bounds__(256) k_sweep_psm(const SweepArgs a, const PsmArgs q) {
-    const uint32_t skey = S == ST_BF16 ? sr_step_key(a) : 0u;  // before any exit (see sr_step)
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int z = sweep_plane(a);
-    const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y, z);
-    if (x >= a.nx || y < 0) return;
-    const int64_t c = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
-    const float e = q.eps[c];
-    if (e == 0.0f || q.own[c] != 0) sweep_one<S, P>(a, x, y, z, skey);
-    else psm_cell<S, P>(a, q, x, y, z, e);
-}
-
-template <int S>
-static void launch_psm_s(const SweepArgs& a, const PsmArgs& q, int parity, cudaStream_t st) {
-    int bx = ((a.nx + 31) / 32) * 32;
-    if (bx > 256) bx = 256;
-    dim3 grid((a.nx + bx - 1) / bx, a.ny, a.nz);
-    if (parity == 0) k_sweep_psm<S, 0><<<grid, bx, 0, st>>>(a, q);
-    else k_sweep_psm<S, 1><<<grid, bx, 0, st>>>(a, q);
-}
-
-// A whole-lattice sweep of a lattice whose spheres are coupled by partially
-// saturated cells (psm.cuh); q.state is the state the step starts from.
-void launch_sweep_psm(const Lattice& L, double lambda_e, double lambda_o, int parity, const PsmArgs& q,
-                      cudaStream_t st) {
-    SweepArgs a = sweep_args(L, lambda_e, lambda_o);
-    a.reverse = parity;
-    switch (L.storage) {
-        case ST_F64: launch_psm_s<ST_F64>(a, q, parity, st); break;
-        case ST_F32: launch_psm_s<ST_F32>(a, q, parity, st); break;
-        case ST_F16: launch_psm_s<ST_F16>(a, q, parity, st); break;
-        default: launch_psm_s<ST_BF16>(a, q, parity, st); break;
-    }
 }
 
 static int sm_count() {
