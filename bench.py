@@ -124,9 +124,11 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ our arm
 
-def build_lattice(storage, shape, bodies, collision="trt", lambda_e=1.0, device=0):
+def build_lattice(storage, shape, bodies, collision="trt", lambda_e=1.0, device=0, coupling="links"):
     from paper_1903_04799_gb300 import Lattice
     g = Lattice(shape, collision=collision, lambda_e=lambda_e, storage=storage, device=device)
+    if coupling != "links":
+        g.set_coupling(coupling)
     ids = [g.add_squirmer(b.pos, b.e, b.R, b.B1, b.beta, mobile=b.mobile) for b in bodies]
     return g, ids
 
@@ -183,8 +185,8 @@ def traced_steps(g, steps, flush, torch):
     return [a.elapsed_time(b) for a, b in ev], prof
 
 
-def run_variant(storage, wl, steps, warmup, flush, torch, device=0, form=0):
-    g, ids = build_lattice(storage, wl.shape, wl.bodies, wl.collision, wl.lambda_e, device)
+def run_variant(storage, wl, steps, warmup, flush, torch, device=0, form=0, coupling="links"):
+    g, ids = build_lattice(storage, wl.shape, wl.bodies, wl.collision, wl.lambda_e, device, coupling)
     if form:
         g.set_sweep_variant(form)
     g.step(warmup)
@@ -213,6 +215,43 @@ def swim_speed(storage, wl, torch, device=0, chunk=200):
             v.append(float(vel @ e))
     g.close()
     return float(np.mean(v))
+
+
+def psm_run(flush, torch, hbm, device=0):
+    """Partially saturated cells (lb_set_coupling), the coupling Sec. IV A
+    names against the speed fluctuation of the link-coupled squirmer:
+    (1) the 256^3 pusher stepped with it in each storage, beside the link
+    coupling; (2) the swim speed of the Fig. "resolution" squirmer (R = 4,
+    L = 10R, B1 = 0.001, FP64) with both couplings: mean and spread of v.e /
+    v0 over steps 1500..3000."""
+    from paper_1903_04799_gb300 import Lattice
+    from paper_1903_04799_gb300 import workloads as W
+    wl = W.c3_pusher()
+    out = {"workload": wl.name, "steps": 64}
+    for st in ("f64", "f32", "bf16dev"):
+        r = run_variant(st, wl, 64, 8, flush, torch, device, coupling="psm")
+        out[st] = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"],
+                   "sweep_frac": r["sweep_bytes"] / (r["sweep_ms"] * 1e-3) / 1e9 / hbm,
+                   "kernels_ms_per_step": r["kernels_ms"]}
+    R, L, B1 = 4.0, 40, 0.001
+    v0 = 2 * B1 / 3
+    spread = {}
+    for coupling in ("links", "psm"):
+        g = Lattice((L, L, L), collision="trt", device=device)
+        if coupling == "psm":
+            g.set_coupling("psm")
+        oid = g.add_squirmer((L / 2 + 0.1, L / 2 + 0.2, L / 2), (0.0, 0.0, 1.0), R, B1, 0.0)
+        g.step(1500)
+        v = []
+        for _ in range(1500):
+            g.step(1)
+            _, vel, e, _ = g.state(oid)
+            v.append(float(vel @ e) / v0)
+        g.close()
+        spread[coupling] = {"U_over_v0": float(np.mean(v)), "spread_over_v0": float(np.std(v))}
+    out["speed_fig_resolution_R4"] = {**spread, "window": "steps 1500..3000, FP64",
+                                      "printed_link_spread": 0.081}
+    return out
 
 
 def e2e_run(wl, storage, steps, device, torch):
@@ -627,6 +666,8 @@ def ours(args):
             res["extra"] = extra
         if not args.skip_tube:
             res["tube_oscillation"] = tube_run(torch, local)
+        if not args.skip_psm:
+            res["psm"] = psm_run(flush, torch, hbm, local)
         if not args.skip_serve:
             res["serving_c5"] = serve_run(torch, local)
         res["e2e"] = e2e_run(wl, head, args.steps, local, torch)
@@ -706,6 +747,7 @@ def main():
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-precision", action="store_true")
     ap.add_argument("--skip-tube", action="store_true")
+    ap.add_argument("--skip-psm", action="store_true")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="run the 256^3 storage precision sweep (about 2 minutes) instead of the benchmark")
     ap.add_argument("--profile-sweep", metavar="STORAGE:N:STEPS[:FORM]",

@@ -576,6 +576,39 @@ template <> __device__ __forceinline__ unsigned int enc16<ST_BF16>(float v, floa
     return __bfloat16_as_ushort(__float2bfloat16_rn(v * sc));
 }
 
+// Collision of four cells x0 .. x0 + 3 of row (y, z) (x0 and nx multiples of
+// 4) whose 16-bit populations g[i] hold two cells per 32-bit word (cell x0 in
+// the low half of .x), in place: decode, TRT in FP32 in the storage's scaled
+// units (see kScaled), encode (BF16 with stochastic rounding: the four cells
+// are two pairs of the random bits).  Every four-cell form calls this, so they
+// all give the same bits.
+template <int S>
+__device__ __forceinline__ void collide_four(uint2 g[Q], const SweepArgs& a, uint32_t skey, int x0, int y, int z) {
+    const bool sr = S == ST_BF16 && a.sr;
+    const float rho0 = a.rho0s;  // scaled units (see kScaled)
+    const uint32_t n0 = (uint32_t)x0 + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
+    const uint32_t k01 = sr ? sr_pair_key(skey, n0) : 0u, k23 = sr ? sr_pair_key(skey, n0 + 2u) : 0u;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float gc[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const unsigned int w = c < 2 ? g[i].x : g[i].y;
+            gc[i] = dec16<S>((c & 1) ? (w >> 16) : (w & 0xffffu), 1.0f);
+        }
+        collide_trt<float, true>(gc, a.K, rho0);
+        const uint32_t kc = c < 2 ? k01 : k23;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t rw = sr_word(kc, i);
+            const unsigned int e = sr ? (unsigned int)bf16_sr(gc[i], (c & 1) ? (rw >> 16) : (rw & 0xffffu))
+                                      : enc16<S>(gc[i], 1.0f);
+            unsigned int& w = c < 2 ? g[i].x : g[i].y;
+            w = (c & 1) ? ((w & 0xffffu) | (e << 16)) : ((w & 0xffff0000u) | e);
+        }
+    }
+}
+
 // 16-bit storages, four cells per thread, blocks of whole rows: a row of nx
 // cells is nx / 4 threads (nx % 4 == 0, nx <= 768), so the x-neighbours of
 // every cell, the periodic wrap included, lie in the block.  Every global
@@ -596,7 +629,6 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
     unsigned short* F = (unsigned short*)a.F;
     using Off = typename std::conditional<O32, uint32_t, int64_t>::type;
     const Off Np = (Off)a.Np;
-    const float rho0 = a.rho0s;  // scaled units (see kScaled)
     auto row = [&](int dy, int dz) -> Off { return (Off)nx * ((Off)ys[1 + dy] + (Off)ny * (Off)zs[1 + dz]); };
     unsigned short* rowbuf = buf + (int64_t)threadIdx.y * nx;  // + d * blockDim.y * nx for shifted direction d
     const int dstride = blockDim.y * nx;
@@ -635,29 +667,7 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
         }
         __syncthreads();  // the buffer is reused for the stores
     }
-    const bool sr = S == ST_BF16 && a.sr;
-    // the four cells are two pairs of the random bits (x0 and nx are multiples of 4)
-    const uint32_t n0 = (uint32_t)x0 + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
-    const uint32_t k01 = sr ? sr_pair_key(skey, n0) : 0u, k23 = sr ? sr_pair_key(skey, n0 + 2u) : 0u;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        float gc[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const unsigned int w = c < 2 ? g[i].x : g[i].y;
-            gc[i] = dec16<S>((c & 1) ? (w >> 16) : (w & 0xffffu), 1.0f);
-        }
-        collide_trt<float, true>(gc, a.K, rho0);
-        const uint32_t kc = c < 2 ? k01 : k23;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const uint32_t rw = sr_word(kc, i);
-            const unsigned int e = sr ? (unsigned int)bf16_sr(gc[i], (c & 1) ? (rw >> 16) : (rw & 0xffffu))
-                                      : enc16<S>(gc[i], 1.0f);
-            unsigned int& w = c < 2 ? g[i].x : g[i].y;
-            w = (c & 1) ? ((w & 0xffffu) | (e << 16)) : ((w & 0xffff0000u) | e);
-        }
-    }
+    collide_four<S>(g, a, skey, x0, y, z);
     d = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

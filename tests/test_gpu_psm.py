@@ -52,8 +52,8 @@ def test_psm_fp64_matches_oracle():
     """96 steps in chunks of 1, 7, 8, 16 and 64 (single steps and the 8-step
     graphs): after each chunk the solid fractions and the owners identical,
     the fields within 1e-12 of max|u|, each squirmer's state within 1e-12,
-    its force and torque within 1e-12 of the size of their cell terms.  At the start nine covered cells are wall cells; they stay wall
-    cells."""
+    its force and torque within 1e-12 of the size of their cell terms.  At
+    the start nine covered cells are wall cells; they stay wall cells."""
     g, o, gi, oi = _setup()
     for n in (1, 7, 8, 16, 64):
         g.step(n)
