@@ -361,10 +361,6 @@ int64_t lb_kernel_launches(const lb_ctx* c);
  * 3 = FP16 / BF16: four cells per thread in blocks of whole rows, the
  *     odd-step x-shifts through shared memory (nx a multiple of 4 up to 768;
  *     else as 2).
- * 4, 5 = FP16 / BF16: tiles of whole rows copied between global and shared
- *     memory by bulk asynchronous copies, in a pipeline of 2 (4) or 3 (5)
- *     stages, one persistent block per SM, four cells per thread (nx a
- *     multiple of 8 from 64 to 1024; else as 3).
  * For FP32, FP16 and BF16 the forms give identical bits; for FP64 the two
  * arithmetics agree to about 1e-14 relative per step.  LB_ERR_INVALID for
  * another value. */

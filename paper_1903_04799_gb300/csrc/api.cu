@@ -22,7 +22,6 @@ void launch_body_step(const Bodies& B, int parity, int grid_links, int grid_box,
 void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st, int tail,
                        cudaEvent_t started = nullptr);
 cudaError_t prepare_body_kernels();
-cudaError_t prepare_sweep_kernels();
 void launch_fill_rest(const Lattice& L, cudaStream_t st);
 void launch_set_eq(const Lattice& L, const double* rho, const double* u, int q, cudaStream_t st);
 void launch_set_pop(const Lattice& L, const double* f, int q, cudaStream_t st);
@@ -661,7 +660,7 @@ lb_status lb_create(const lb_params* p, lb_ctx** out) {
         cudaGetLastError();
         return bail(LB_ERR_CUDA);
     }
-    if (prepare_body_kernels() != cudaSuccess || prepare_sweep_kernels() != cudaSuccess) {
+    if (prepare_body_kernels() != cudaSuccess) {
         cudaGetLastError();
         return bail(LB_ERR_CUDA);
     }
@@ -1300,7 +1299,7 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
 }
 
 lb_status lb_set_sweep_variant(lb_ctx* c, int32_t variant) {
-    if (!c || variant < 0 || variant > 5) return LB_ERR_INVALID;
+    if (!c || variant < 0 || variant > 3) return LB_ERR_INVALID;
     CK(cudaSetDevice(c->p.device));
     settle(c);
     c->sweep_variant = variant;

@@ -8,7 +8,6 @@
 // and every slot a fluid cell reads from a solid neighbour is rewritten by the
 // link kernel after the sweep), so no flag field is read.
 #include "sweep_body.cuh"
-#include "sweep_tma.cuh"
 
 namespace lbsq {
 
@@ -96,50 +95,6 @@ static int prefetch_ahead(const SweepArgs& a, int storage, const dim3& grid) {
     return ahead < a.nz ? ahead : 0;
 }
 
-// The tiled form of the 16-bit sweep (sweep_tma.cuh): ST stages per block,
-// one block per SM; for lattices with 64 <= nx <= 1024, nx % 8 == 0.
-template <int ST> constexpr int tma_rows(int nx) {
-    return tma_tile_cells(ST) / nx < kTmaMaxY ? tma_tile_cells(ST) / nx : kTmaMaxY;
-}
-template <int ST> constexpr size_t tma_smem_bytes(int nx) {
-    return (size_t)kTmaHeader + (size_t)ST * Q * tma_rows<ST>(nx) * nx * 2;
-}
-static bool tma_suits(int nx) { return nx % 8 == 0 && nx >= 64 && nx <= 1024; }
-
-template <int S, int P, int ST>
-static void launch_tma_p(const SweepArgs& a, int gz, int gy, cudaStream_t st) {
-    const int Y = tma_rows<ST>(a.nx);
-    const int nty = (gy + Y - 1) / Y;
-    const int ntiles = gz * nty;
-    const int grid = ntiles < sm_count() ? ntiles : sm_count();  // one persistent block per SM
-    k_sweep_tma<S, P, ST><<<grid, kTmaThreads, tma_smem_bytes<ST>(a.nx), st>>>(a, Y, nty, ntiles);
-}
-
-template <int S, int ST>
-static void launch_tma(const SweepArgs& a, int parity, int gz, int gy, cudaStream_t st) {
-    if (parity == 0) launch_tma_p<S, 0, ST>(a, gz, gy, st);
-    else launch_tma_p<S, 1, ST>(a, gz, gy, st);
-}
-
-template <int S, int ST>
-static cudaError_t prepare_tma() {
-    const int bytes = (int)tma_smem_bytes<ST>(128);  // the largest stages: Y nx = tma_tile_cells(ST)
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_tma<S, 0, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sweep_tma<S, 1, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
-}
-
-// Once per process and device, before the first sweep: the tiled 16-bit
-// sweep's dynamic shared memory (above the default 48 KB).
-cudaError_t prepare_sweep_kernels() {
-    cudaError_t e = prepare_tma<ST_F16, 2>();
-    if (e == cudaSuccess) e = prepare_tma<ST_BF16, 2>();
-    if (e == cudaSuccess) e = prepare_tma<ST_F16, 3>();
-    if (e == cudaSuccess) e = prepare_tma<ST_BF16, 3>();
-    return e;
-}
-
 template <int S>
 static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy, cudaStream_t st) {
     const bool o32 = 19 * a.Np < (int64_t(1) << 32);  // element offsets fit 32 bits
@@ -161,17 +116,12 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy
         }
     } else {
     if constexpr (S == ST_F16 || S == ST_BF16) {
-        if ((variant == 4 || variant == 5) && tma_suits(a.nx)) {
-            if (variant == 4) launch_tma<S, 2>(a, parity, gz, gy, st);
-            else launch_tma<S, 3>(a, parity, gz, gy, st);
-            return;
-        }
         // default: even steps in whole-row four-cell blocks (aligned 8-byte
         // chunks: 0.86 of the copy bandwidth at 256^3, against 0.74 for two
         // cells), odd steps in the two-cell form (0.63; the whole-row form's
         // odd steps, with their x-shifts through shared memory, measured 0.62)
         const bool rows4 = a.nx % 4 == 0 && a.nx <= 768;
-        if ((variant >= 3 || (variant == 0 && parity == 0)) && rows4) {
+        if ((variant == 3 || (variant == 0 && parity == 0)) && rows4) {
             // odd steps (more live values) in blocks of at most 192 threads
             const int tx = a.nx / 4, ty = (parity == 0 ? 256 : 192) / tx > 0 ? (parity == 0 ? 256 : 192) / tx : 1;
             dim3 block(tx, ty), grid(1, (gy + ty - 1) / ty, gz);
