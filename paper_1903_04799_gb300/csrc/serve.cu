@@ -10,8 +10,12 @@
 //
 // A step: k_sweep_tiles (persistent; each block walks the packed list of
 // z-slab tiles of all active lattices, branching per tile on the lattice's
-// storage), then the body kernels of bodies.cu over all bodies (work lists),
-// the last of which advances the device step counter.  A request admitted at
+// storage), then the body kernels of bodies.cu over all bodies (work lists):
+// the fused cluster kernel for every request's squirmer (one cluster each;
+// a squirmer near its walls or obstacle queues its re-classification for the
+// multi-kernel path, as in a context), the link kernel for walls and
+// obstacles, then classify, convert and rebuild, the last of which advances
+// the device step counter.  A request admitted at
 // global step s0 with n steps is active while s0 <= step < s0 + n, so it stops
 // inside a round at its own step; every round starts on an even step, which
 // keeps all resident lattices on the same streaming parity.
@@ -33,11 +37,15 @@ void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, 
 void launch_fill_rest(const Lattice& L, cudaStream_t st);
 void launch_plane_claim(const Lattice& L, int32_t* own, int axis, int index, int id, cudaStream_t st);
 void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, cudaStream_t st);
+void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st, int tail,
+                       cudaEvent_t started);
+cudaError_t prepare_body_kernels();
 
 // ---------------------------------------------------------------- tile sweep
 
 struct TileArgs {
     const Lattice* lats;
+    const SweepArgs* sargs;  // per slot, built on the host at admission (collision constants included)
     const int4* tiles;  // (lattice, first unit, end unit, paired), sorted by storage
     const int* n_tiles; // [5]: tiles of storage S are [n_tiles[S], n_tiles[S+1])
 };
@@ -45,14 +53,14 @@ struct TileArgs {
 // A tile is the unit range [tile.y, tile.z) of one lattice, a unit being a cell
 // pair (paired tiles, nx even) or a cell, numbered x-fastest over the lattice.
 template <int P, int S>
-__device__ __forceinline__ void sweep_tile(const Lattice& L, const int4 tile) {
-    const SweepArgs a = sweep_args(L, L.lambda_e, L.lambda_o);
+__device__ __forceinline__ void sweep_tile(const SweepArgs& a, const int4 tile) {
     const uint32_t skey = S == ST_BF16 ? sr_step_key(a) : 0u;  // the lattice's own step (global - start)
-    const unsigned per_row = tile.w ? (unsigned)L.nx / 2 : (unsigned)L.nx;
+    const unsigned nx = (unsigned)a.nx, ny = (unsigned)a.ny;
+    const unsigned per_row = tile.w ? nx / 2 : nx;
     for (unsigned u = (unsigned)tile.y + threadIdx.x; u < (unsigned)tile.z; u += blockDim.x) {
         const unsigned r = u / per_row;
         const int xi = (int)(u - r * per_row);
-        const int y = (int)(r % (unsigned)L.ny), z = (int)(r / (unsigned)L.ny);
+        const int y = (int)(r % ny), z = (int)(r / ny);
         if constexpr (S != ST_F64) {
             if (tile.w) {
                 sweep_two<S, P>(a, 2 * xi, y, z, skey);
@@ -65,13 +73,46 @@ __device__ __forceinline__ void sweep_tile(const Lattice& L, const int4 tile) {
 
 // One kernel per storage, so that none pays for another's registers; the
 // tile list is sorted by storage and n_tiles[S .. S+1] bounds storage S.
+// The sweep arguments of the tile's lattice are staged in shared memory once
+// per lattice: their collision constants would otherwise be rebuilt per tile,
+// in FP64, which issues at GB300's narrow FP64 rate.  The next tile's
+// descriptor and its lattice's activity are fetched before the current tile
+// is swept, so that their dependent loads (tile, lattice, step counter) do not
+// stall the block between tiles.
 template <int P, int S>
 __global__ void __launch_bounds__(256, S == ST_F64 ? 1 : 2) k_sweep_tiles(const TileArgs T) {
+    __shared__ __align__(16) SweepArgs s_a;
     const int t0 = T.n_tiles[S], t1 = T.n_tiles[S + 1];
-    for (int t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
-        const int4 tile = T.tiles[t];
-        const Lattice& L = T.lats[tile.x];
-        if (lattice_active(L)) sweep_tile<P, S>(L, tile);
+    int cur = -1;
+    int t = t0 + blockIdx.x;
+    int4 tile = make_int4(0, 0, 0, 0);
+    bool act = false;
+    if (t < t1) {
+        tile = T.tiles[t];
+        act = lattice_active(T.lats[tile.x]);
+    }
+    while (t < t1) {
+        const int tn = t + gridDim.x;
+        int4 next = make_int4(0, 0, 0, 0);
+        bool nact = false;
+        if (tn < t1) {
+            next = T.tiles[tn];
+            nact = lattice_active(T.lats[next.x]);
+        }
+        if (act) {  // the same for the whole block
+            if (tile.x != cur) {
+                __syncthreads();  // the previous lattice's readers are done
+                static_assert(sizeof(SweepArgs) % 4 == 0, "word copy");
+                for (int w = threadIdx.x; w < (int)(sizeof(SweepArgs) / 4); w += blockDim.x)
+                    reinterpret_cast<int*>(&s_a)[w] = __ldg(reinterpret_cast<const int*>(T.sargs + tile.x) + w);
+                __syncthreads();
+                cur = tile.x;
+            }
+            if (s_a.F != nullptr) sweep_tile<P, S>(s_a, tile);  // a slot without arguments: nothing
+        }
+        t = tn;
+        tile = next;
+        act = nact;
     }
 }
 
@@ -194,7 +235,11 @@ struct lb_server {
     int2* d_link_items = nullptr;
     int2* d_box_items = nullptr;
     int2* d_rel_items = nullptr;
-    int* d_counts = nullptr;  // link items, box items, relink items, rebuild blocks done
+    int* d_counts = nullptr;  // link items, box items, relink items, rebuild blocks done,
+                              // [4..6] fused squirmers per class, [7..9] first fused item per class,
+                              // [10] clusters of a solo fused launch done (unused here)
+    int2* d_fused_items = nullptr;  // (body, slot) of each resident squirmer the fused kernel advances
+    SweepArgs* d_sargs = nullptr;   // sweep arguments per slot
     int4* d_tiles = nullptr;
     int* d_ntiles = nullptr;
     long long* d_gstep = nullptr;
@@ -209,6 +254,7 @@ struct lb_server {
     int64_t gstep = 0;
     double cell_updates = 0.0;
     int tile_units = 2048, blocks_per_sm = 2;
+    int fused_cls = 0;  // cluster class of the fused launch (fixed by the capacity, see fused_class)
     cudaGraphExec_t graph = nullptr;
     std::string msg;
 };
@@ -262,7 +308,9 @@ std::vector<TableSpec> tables(lb_server* s) {
         {(void**)&s->d_link_items, sizeof(int2) * s->list_cap},
         {(void**)&s->d_box_items, sizeof(int2) * s->list_cap},
         {(void**)&s->d_rel_items, sizeof(int2) * s->list_cap},
-        {(void**)&s->d_counts, sizeof(int) * 4},
+        {(void**)&s->d_counts, sizeof(int) * 11},
+        {(void**)&s->d_fused_items, sizeof(int2) * s->cap_slots},
+        {(void**)&s->d_sargs, sizeof(SweepArgs) * s->cap_slots},
         {(void**)&s->d_tiles, sizeof(int4) * s->tile_cap},
         {(void**)&s->d_ntiles, sizeof(int) * 5},
         {(void**)&s->d_gstep, sizeof(long long)},
@@ -295,13 +343,15 @@ Bodies bodies_view(lb_server* s, bool step) {
     B.err = s->d_errs;  // list overflow is reported on slot 0's word
     B.win = nullptr;
     B.gstep = step ? s->d_gstep : nullptr;
-    B.fused_items = nullptr;  // the server runs every body through the multi-kernel path
-    B.n_fused = nullptr;
-    B.stencil = nullptr;
+    B.fused_items = s->d_fused_items;
+    B.n_fused = s->d_counts + 4;
+    B.fused_first = s->d_counts + 7;
+    B.stencil = (const uint32_t*)s->arena.base;  // each squirmer's stencil is in its request's arena blocks
+    B.fused_done = s->d_counts + 10;
     return B;
 }
 
-TileArgs tile_args(lb_server* s) { return TileArgs{s->d_lats, s->d_tiles, s->d_ntiles}; }
+TileArgs tile_args(lb_server* s) { return TileArgs{s->d_lats, s->d_sargs, s->d_tiles, s->d_ntiles}; }
 
 int storage_bytes_of(int st) { return st == LB_F64 ? 8 : (st == LB_F32 ? 4 : 2); }
 
@@ -377,8 +427,10 @@ size_t request_bytes(const lb_request& r, std::vector<size_t>* parts) {
     auto bodies = request_bodies(r, st);
     int64_t links = 0;
     for (auto& b : bodies) links += b.link_cap;
+    // populations, owners, committed owners, links, the squirmer's shell stencil
+    const size_t stc = r.R <= kStencilMaxR ? shell_stencil(r.R).size() * 4 : 0;
     std::vector<size_t> v = {(size_t)(19 * Np * storage_bytes_of(r.storage)), (size_t)N * 4, (size_t)N * 4,
-                             (size_t)links * 4};
+                             (size_t)links * 4, stc > 0 ? stc : 16};
     size_t tot = 0;
     for (size_t x : v) tot += Arena::round(x);
     if (parts) *parts = v;
@@ -447,13 +499,22 @@ lb_status admit(lb_server* s, int l, const Queued& q) {
     std::vector<BodyParams> bodies = request_bodies(r, st);
     L.body_count = (int)bodies.size();
     int64_t link_off = (int64_t)(blocks[3].first / 4);
+    cudaStream_t str = s->stream;
+    std::vector<uint32_t> stencil;
     for (size_t j = 0; j < bodies.size(); ++j) {
         bodies[j].lat = l;
         bodies[j].link_off = link_off;
         link_off += bodies[j].link_cap;
+        if (fused_body(bodies[j])) {  // the squirmer: its shell stencil for the fused kernel
+            stencil = shell_stencil(bodies[j].R);
+            bodies[j].st_off = (int64_t)(blocks[4].first / 4);
+            bodies[j].st_count = (int)stencil.size();
+        }
         s->par[L.body_begin + j] = bodies[j];
     }
-    cudaStream_t str = s->stream;
+    if (!stencil.empty())
+        SCK(cudaMemcpyAsync(s->arena.base + blocks[4].first, stencil.data(), sizeof(uint32_t) * stencil.size(),
+                            cudaMemcpyHostToDevice, str));
     SCK(cudaMemcpyAsync(s->d_lats + l, &L, sizeof(Lattice), cudaMemcpyHostToDevice, str));
     SCK(cudaMemcpyAsync(s->d_par + L.body_begin, bodies.data(), sizeof(BodyParams) * bodies.size(),
                         cudaMemcpyHostToDevice, str));
@@ -499,6 +560,8 @@ lb_status admit(lb_server* s, int l, const Queued& q) {
     SCK(cudaMemcpyAsync(L.own_prev, L.own, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, str));
     L.active = 1;
     SCK(cudaMemcpyAsync(s->d_lats + l, &L, sizeof(Lattice), cudaMemcpyHostToDevice, str));
+    const SweepArgs sa = sweep_args(L, L.lambda_e, L.lambda_o);
+    SCK(cudaMemcpyAsync(s->d_sargs + l, &sa, sizeof(SweepArgs), cudaMemcpyHostToDevice, str));
     SCK(cudaGetLastError());
     SCK(cudaStreamSynchronize(str));
     int err = 0;
@@ -557,7 +620,7 @@ lb_status fill_result(lb_server* s, int l, lb_result* out) {
 
 // Upload the static work of the resident mix: link items and sweep tiles.
 lb_status upload_mix(lb_server* s) {
-    std::vector<int2> items;
+    std::vector<int2> items, fused;
     std::vector<int4> tiles;
     int bounds[5] = {0, 0, 0, 0, 0};
     for (int l = 0; l < s->cap_slots; ++l) {
@@ -565,6 +628,10 @@ lb_status upload_mix(lb_server* s) {
         if (!sl.used) continue;
         for (int j = 0; j < sl.nbodies; ++j) {
             const int k = sl.L.body_begin + j;
+            if (fused_body(s->par[k])) {
+                fused.push_back(make_int2(k, l));
+                continue;
+            }
             for (int g = 0; g < s->par[k].g_links; ++g) items.push_back(make_int2(k, g));
         }
     }
@@ -587,8 +654,14 @@ lb_status upload_mix(lb_server* s) {
                             s->stream));
     if (!tiles.empty())
         SCK(cudaMemcpyAsync(s->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s->stream));
+    if (!fused.empty())
+        SCK(cudaMemcpyAsync(s->d_fused_items, fused.data(), sizeof(int2) * fused.size(), cudaMemcpyHostToDevice,
+                            s->stream));
     const int ni = (int)items.size();
     SCK(cudaMemcpyAsync(s->d_counts, &ni, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    int fc[7] = {0, 0, 0, 0, 0, 0, 0};  // counts [4..10]: every fused item in the launch's class, from item 0
+    fc[s->fused_cls] = (int)fused.size();
+    SCK(cudaMemcpyAsync(s->d_counts + 4, fc, sizeof(fc), cudaMemcpyHostToDevice, s->stream));
     SCK(cudaMemcpyAsync(s->d_ntiles, bounds, sizeof(bounds), cudaMemcpyHostToDevice, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
     return LB_OK;
@@ -602,6 +675,7 @@ void enqueue_round(lb_server* s, cudaStream_t st) {
     for (int k = 0; k < s->p.round_steps; ++k) {
         const int P = k & 1;  // rounds start on even steps
         launch_tiles(T, P, grid, st);
+        launch_body_fused(B, P, s->fused_cls, s->cap_slots, st, 0, nullptr);
         for (int w = 1; w <= 4; ++w) launch_body_kernel(w, B, P, glinks, gbox, nullptr, st);
     }
 }
@@ -654,6 +728,9 @@ lb_status autotune(lb_server* s) {
         launch_fill_rest(L, s->stream);
     }
     SCK(cudaMemcpyAsync(s->d_lats, Ls, sizeof(Ls), cudaMemcpyHostToDevice, s->stream));
+    const SweepArgs sa[2] = {sweep_args(Ls[0], Ls[0].lambda_e, Ls[0].lambda_o),
+                             sweep_args(Ls[1], Ls[1].lambda_e, Ls[1].lambda_o)};
+    SCK(cudaMemcpyAsync(s->d_sargs, sa, sizeof(sa), cudaMemcpyHostToDevice, s->stream));
     cudaEvent_t e0, e1;
     SCK(cudaEventCreate(&e0));
     SCK(cudaEventCreate(&e1));
@@ -691,6 +768,7 @@ lb_status autotune(lb_server* s) {
     for (auto& b : blocks) s->arena.release(b.first, b.second);
     Lattice zero[2] = {};
     SCK(cudaMemcpyAsync(s->d_lats, zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream));
+    SCK(cudaMemsetAsync(s->d_sargs, 0, sizeof(sa), s->stream));
     const int nt0[5] = {0, 0, 0, 0, 0};
     SCK(cudaMemcpyAsync(s->d_ntiles, nt0, sizeof(nt0), cudaMemcpyHostToDevice, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
@@ -726,6 +804,10 @@ lb_status lb_server_create(const lb_server_params* p, lb_server** out) {
         return st;
     };
     if (cudaSetDevice(p->device) != cudaSuccess) return bail(LB_ERR_CUDA);
+    if (prepare_body_kernels() != cudaSuccess) {
+        cudaGetLastError();
+        return bail(LB_ERR_CUDA);
+    }
     if (p->stream) s->stream = (cudaStream_t)p->stream;
     else {
         if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(LB_ERR_CUDA);
@@ -733,6 +815,7 @@ lb_status lb_server_create(const lb_server_params* p, lb_server** out) {
     }
     cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, p->device);
     s->cap_slots = p->max_resident;
+    s->fused_cls = fused_class(s->cap_slots);  // one cluster per resident squirmer at most
     s->cap_bodies = s->cap_slots * kBodiesPerSlot;
     s->list_cap = s->cap_bodies * kMaxGB;
     s->tile_cap = 1 << 20;

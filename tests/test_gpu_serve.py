@@ -36,8 +36,8 @@ def requests():
     ]
 
 
-def run_server(reqs, arrive_at_round, budget=1 << 30, max_resident=8, round_steps=16):
-    srv = Server(budget_bytes=budget, max_resident=max_resident, round_steps=round_steps, tile_units=700)
+def run_server(reqs, arrive_at_round, budget=1 << 30, max_resident=8, round_steps=16, tile_units=700):
+    srv = Server(budget_bytes=budget, max_resident=max_resident, round_steps=round_steps, tile_units=tile_units)
     tickets = {}
     results = {}
     rnd = 0
@@ -128,3 +128,16 @@ def test_failed_request_reports_overlap():
     assert res[0].state == lbsq.LB_REQ_FAILED and res[0].status == lbsq.LB_ERR_OVERLAP
     alone = run_server([good], arrive_at_round=[0])[0]
     assert np.array_equal(as_array(alone), as_array(res[1]))
+
+
+def test_autotuned_tiles_give_the_same_bits():
+    """A server that picks its tile shape by timing candidates at creation
+    (tile_units = 0; the autotuner sweeps two synthetic 96^3 lattices) serves
+    the mix with the same bits as fixed 700-unit tiles: every cell's update is
+    independent of the tiling."""
+    reqs = requests()
+    fixed = run_server(reqs, [0] * len(reqs))
+    tuned = run_server(reqs, [0] * len(reqs), tile_units=0)
+    for i in range(len(reqs)):
+        assert tuned[i].state == lbsq.LB_REQ_DONE
+        assert np.array_equal(as_array(fixed[i]), as_array(tuned[i])), i
