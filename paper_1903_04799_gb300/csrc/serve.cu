@@ -10,12 +10,8 @@
 //
 // A step: k_sweep_tiles (persistent; each block walks the packed list of
 // z-slab tiles of all active lattices, branching per tile on the lattice's
-// storage), then the body kernels of bodies.cu over all bodies (work lists):
-// the fused cluster kernel for every request's squirmer (one cluster each;
-// a squirmer near its walls or obstacle queues its re-classification for the
-// multi-kernel path, as in a context), the link kernel for walls and
-// obstacles, then classify, convert and rebuild, the last of which advances
-// the device step counter.  A request admitted at
+// storage), then the body kernels of bodies.cu over all bodies (work lists),
+// the last of which advances the device step counter.  A request admitted at
 // global step s0 with n steps is active while s0 <= step < s0 + n, so it stops
 // inside a round at its own step; every round starts on an even step, which
 // keeps all resident lattices on the same streaming parity.
@@ -37,9 +33,6 @@ void launch_body_kernel(int which, const Bodies& B, int parity, int grid_links, 
 void launch_fill_rest(const Lattice& L, cudaStream_t st);
 void launch_plane_claim(const Lattice& L, int32_t* own, int axis, int index, int id, cudaStream_t st);
 void launch_set_flags(BodyAcc* acc, int nb, int k, int reclass, cudaStream_t st);
-void launch_body_fused(const Bodies& B, int parity, int cls, int clusters, cudaStream_t st, int tail,
-                       cudaEvent_t started);
-cudaError_t prepare_body_kernels();
 
 // ---------------------------------------------------------------- tile sweep
 
@@ -235,11 +228,8 @@ struct lb_server {
     int2* d_link_items = nullptr;
     int2* d_box_items = nullptr;
     int2* d_rel_items = nullptr;
-    int* d_counts = nullptr;  // link items, box items, relink items, rebuild blocks done,
-                              // [4..6] fused squirmers per class, [7..9] first fused item per class,
-                              // [10] clusters of a solo fused launch done (unused here)
-    int2* d_fused_items = nullptr;  // (body, slot) of each resident squirmer the fused kernel advances
-    SweepArgs* d_sargs = nullptr;   // sweep arguments per slot
+    int* d_counts = nullptr;  // link items, box items, relink items, rebuild blocks done
+    SweepArgs* d_sargs = nullptr;  // sweep arguments per slot
     int4* d_tiles = nullptr;
     int* d_ntiles = nullptr;
     long long* d_gstep = nullptr;
@@ -254,7 +244,6 @@ struct lb_server {
     int64_t gstep = 0;
     double cell_updates = 0.0;
     int tile_units = 2048, blocks_per_sm = 2;
-    int fused_cls = 0;  // cluster class of the fused launch (fixed by the capacity, see fused_class)
     cudaGraphExec_t graph = nullptr;
     std::string msg;
 };
@@ -308,8 +297,7 @@ std::vector<TableSpec> tables(lb_server* s) {
         {(void**)&s->d_link_items, sizeof(int2) * s->list_cap},
         {(void**)&s->d_box_items, sizeof(int2) * s->list_cap},
         {(void**)&s->d_rel_items, sizeof(int2) * s->list_cap},
-        {(void**)&s->d_counts, sizeof(int) * 11},
-        {(void**)&s->d_fused_items, sizeof(int2) * s->cap_slots},
+        {(void**)&s->d_counts, sizeof(int) * 4},
         {(void**)&s->d_sargs, sizeof(SweepArgs) * s->cap_slots},
         {(void**)&s->d_tiles, sizeof(int4) * s->tile_cap},
         {(void**)&s->d_ntiles, sizeof(int) * 5},
@@ -343,11 +331,12 @@ Bodies bodies_view(lb_server* s, bool step) {
     B.err = s->d_errs;  // list overflow is reported on slot 0's word
     B.win = nullptr;
     B.gstep = step ? s->d_gstep : nullptr;
-    B.fused_items = s->d_fused_items;
-    B.n_fused = s->d_counts + 4;
-    B.fused_first = s->d_counts + 7;
-    B.stencil = (const uint32_t*)s->arena.base;  // each squirmer's stencil is in its request's arena blocks
-    B.fused_done = s->d_counts + 10;
+    // every body takes the multi-kernel path: the fused cluster kernel for the
+    // squirmers measured no faster on the serving mix (28.78k against 28.75k
+    // MLUPS with 8-block clusters, slower with 16)
+    B.fused_items = nullptr;
+    B.n_fused = nullptr;
+    B.stencil = nullptr;
     return B;
 }
 
@@ -427,10 +416,8 @@ size_t request_bytes(const lb_request& r, std::vector<size_t>* parts) {
     auto bodies = request_bodies(r, st);
     int64_t links = 0;
     for (auto& b : bodies) links += b.link_cap;
-    // populations, owners, committed owners, links, the squirmer's shell stencil
-    const size_t stc = r.R <= kStencilMaxR ? shell_stencil(r.R).size() * 4 : 0;
     std::vector<size_t> v = {(size_t)(19 * Np * storage_bytes_of(r.storage)), (size_t)N * 4, (size_t)N * 4,
-                             (size_t)links * 4, stc > 0 ? stc : 16};
+                             (size_t)links * 4};
     size_t tot = 0;
     for (size_t x : v) tot += Arena::round(x);
     if (parts) *parts = v;
@@ -499,22 +486,13 @@ lb_status admit(lb_server* s, int l, const Queued& q) {
     std::vector<BodyParams> bodies = request_bodies(r, st);
     L.body_count = (int)bodies.size();
     int64_t link_off = (int64_t)(blocks[3].first / 4);
-    cudaStream_t str = s->stream;
-    std::vector<uint32_t> stencil;
     for (size_t j = 0; j < bodies.size(); ++j) {
         bodies[j].lat = l;
         bodies[j].link_off = link_off;
         link_off += bodies[j].link_cap;
-        if (fused_body(bodies[j])) {  // the squirmer: its shell stencil for the fused kernel
-            stencil = shell_stencil(bodies[j].R);
-            bodies[j].st_off = (int64_t)(blocks[4].first / 4);
-            bodies[j].st_count = (int)stencil.size();
-        }
         s->par[L.body_begin + j] = bodies[j];
     }
-    if (!stencil.empty())
-        SCK(cudaMemcpyAsync(s->arena.base + blocks[4].first, stencil.data(), sizeof(uint32_t) * stencil.size(),
-                            cudaMemcpyHostToDevice, str));
+    cudaStream_t str = s->stream;
     SCK(cudaMemcpyAsync(s->d_lats + l, &L, sizeof(Lattice), cudaMemcpyHostToDevice, str));
     SCK(cudaMemcpyAsync(s->d_par + L.body_begin, bodies.data(), sizeof(BodyParams) * bodies.size(),
                         cudaMemcpyHostToDevice, str));
@@ -620,7 +598,7 @@ lb_status fill_result(lb_server* s, int l, lb_result* out) {
 
 // Upload the static work of the resident mix: link items and sweep tiles.
 lb_status upload_mix(lb_server* s) {
-    std::vector<int2> items, fused;
+    std::vector<int2> items;
     std::vector<int4> tiles;
     int bounds[5] = {0, 0, 0, 0, 0};
     for (int l = 0; l < s->cap_slots; ++l) {
@@ -628,10 +606,6 @@ lb_status upload_mix(lb_server* s) {
         if (!sl.used) continue;
         for (int j = 0; j < sl.nbodies; ++j) {
             const int k = sl.L.body_begin + j;
-            if (fused_body(s->par[k])) {
-                fused.push_back(make_int2(k, l));
-                continue;
-            }
             for (int g = 0; g < s->par[k].g_links; ++g) items.push_back(make_int2(k, g));
         }
     }
@@ -654,14 +628,8 @@ lb_status upload_mix(lb_server* s) {
                             s->stream));
     if (!tiles.empty())
         SCK(cudaMemcpyAsync(s->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s->stream));
-    if (!fused.empty())
-        SCK(cudaMemcpyAsync(s->d_fused_items, fused.data(), sizeof(int2) * fused.size(), cudaMemcpyHostToDevice,
-                            s->stream));
     const int ni = (int)items.size();
     SCK(cudaMemcpyAsync(s->d_counts, &ni, sizeof(int), cudaMemcpyHostToDevice, s->stream));
-    int fc[7] = {0, 0, 0, 0, 0, 0, 0};  // counts [4..10]: every fused item in the launch's class, from item 0
-    fc[s->fused_cls] = (int)fused.size();
-    SCK(cudaMemcpyAsync(s->d_counts + 4, fc, sizeof(fc), cudaMemcpyHostToDevice, s->stream));
     SCK(cudaMemcpyAsync(s->d_ntiles, bounds, sizeof(bounds), cudaMemcpyHostToDevice, s->stream));
     SCK(cudaStreamSynchronize(s->stream));
     return LB_OK;
@@ -675,7 +643,6 @@ void enqueue_round(lb_server* s, cudaStream_t st) {
     for (int k = 0; k < s->p.round_steps; ++k) {
         const int P = k & 1;  // rounds start on even steps
         launch_tiles(T, P, grid, st);
-        launch_body_fused(B, P, s->fused_cls, s->cap_slots, st, 0, nullptr);
         for (int w = 1; w <= 4; ++w) launch_body_kernel(w, B, P, glinks, gbox, nullptr, st);
     }
 }
@@ -804,10 +771,6 @@ lb_status lb_server_create(const lb_server_params* p, lb_server** out) {
         return st;
     };
     if (cudaSetDevice(p->device) != cudaSuccess) return bail(LB_ERR_CUDA);
-    if (prepare_body_kernels() != cudaSuccess) {
-        cudaGetLastError();
-        return bail(LB_ERR_CUDA);
-    }
     if (p->stream) s->stream = (cudaStream_t)p->stream;
     else {
         if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(LB_ERR_CUDA);
@@ -815,7 +778,6 @@ lb_status lb_server_create(const lb_server_params* p, lb_server** out) {
     }
     cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, p->device);
     s->cap_slots = p->max_resident;
-    s->fused_cls = fused_class(s->cap_slots);  // one cluster per resident squirmer at most
     s->cap_bodies = s->cap_slots * kBodiesPerSlot;
     s->list_cap = s->cap_bodies * kMaxGB;
     s->tile_cap = 1 << 20;
