@@ -733,6 +733,28 @@ def profile_sweep(spec: str):
     print(f"profile-sweep {st} {n}^3 {steps} steps form {form}: ok", flush=True)
 
 
+def profile_psm(spec: str):
+    """The pusher of the 256^3 workload (R = 16, beta = -3) at the centre of
+    an N^3 box, coupled by partially saturated cells, stepped STEPS times one
+    step per call (no graphs): for ncu captures of k_psm_clear, k_psm_cover and
+    k_psm_scatter (their work depends on the sphere, not on N).
+    spec = STORAGE:N:STEPS."""
+    import torch
+    from paper_1903_04799_gb300 import workloads as W
+    st, n, steps = spec.split(":")
+    n, steps = int(n), int(steps)
+    wl = W.c3_pusher(n)
+    b = wl.bodies[0]
+    g, _ = build_lattice(st, wl.shape, [], wl.collision, wl.lambda_e, 0, coupling="psm")
+    g.add_squirmer(b.pos, b.e, b.R, b.B1, b.beta, mobile=True)
+    for _ in range(steps):
+        g.step(1)
+    g.sync()
+    torch.cuda.synchronize()
+    g.close()
+    print(f"profile-psm {st} {n}^3 {steps} steps: ok", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -752,11 +774,15 @@ def main():
                     help="run the 256^3 storage precision sweep (about 2 minutes) instead of the benchmark")
     ap.add_argument("--profile-sweep", metavar="STORAGE:N:STEPS[:FORM]",
                     help="step a bare N^3 lattice (sweep kernels only), for ncu captures, instead of the benchmark")
+    ap.add_argument("--profile-psm", metavar="STORAGE:N:STEPS",
+                    help="step the pusher under partially saturated cells, for ncu captures, instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.profile_sweep:
         profile_sweep(args.profile_sweep)
+    elif args.profile_psm:
+        profile_psm(args.profile_psm)
     elif args.impl == "reference":
         reference(args)
     elif args.precision_sweep:
