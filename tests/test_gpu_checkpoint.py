@@ -38,6 +38,17 @@ def _two_swimmers_and_wall(storage):
     return g, ids
 
 
+def _psm_swimmers(storage):
+    # partially saturated cells: solid fractions found afresh each step, from
+    # positions the restore replaces (the restore clears the recorded ones)
+    g = Lattice((44, 40, 40), collision="trt", storage=storage)
+    g.set_coupling("psm")
+    g.add_plane_wall(2, 0)
+    ids = [g.add_squirmer((14.3, 20.6, 6.3), (0.3, -0.2, 1.0), 5.0, 0.02, -3.0, mobile=True),
+           g.add_squirmer((30.7, 21.1, 24.4), (-0.5, 0.4, -0.6), 5.5, 0.015, 2.0, mobile=True)]
+    return g, ids
+
+
 def _snapshot(g, ids):
     out = [g.populations(), g.owner(), np.int64(g.steps)]
     for i in ids:
@@ -52,24 +63,28 @@ def _snapshot(g, ids):
     (_split_swimmer, "f16dev", 13, 16),
     (_two_swimmers_and_wall, "f16dev", 30, 25),
     (_two_swimmers_and_wall, "f64", 26, 21),
+    (_psm_swimmers, "f64", 19, 22),
+    (_psm_swimmers, "bf16dev", 24, 17),
 ])
 def test_resume_is_bitwise(setup, storage, before, after):
     """Run `before` steps, checkpoint, run `after` more; a second context set
     up the same way, restored from the checkpoint and run `after` steps, ends
     with the same populations, owners, step count, body states, forces,
-    stresslets and link lists, bit for bit.  Step counts cover eager steps,
+    stresslets, link lists and solid fractions, bit for bit.  Step counts cover eager steps,
     graph replays and a checkpoint taken with body kernels pending."""
     a, ids = setup(storage)
     a.step(before)
     blob = a.checkpoint()
     a.step(after)
     want = _snapshot(a, ids)
+    want_eps = a.solid_fraction()
     a.close()
     b, ids_b = setup(storage)
     b.step(3)  # anything done before the restore is replaced
     b.restore(blob)
     b.step(after)
-    got = _snapshot(b, ids_b)
+    got = _snapshot(b, ids_b) + [b.solid_fraction()]
+    want = want + [want_eps]
     b.close()
     assert len(got) == len(want)
     for k, (x, y) in enumerate(zip(got, want)):

@@ -110,6 +110,40 @@ def test_psm_reduced_storage_against_oracle(storage, tol):
     g.close()
 
 
+@pytest.mark.parametrize("option", ["incompressible", "force_average", "bgk_1.3"])
+def test_psm_options_against_oracle(option):
+    """The coupling under the method's options, FP64 against the oracle's
+    same switches, 48 steps of the two-squirmer set-up: the incompressible
+    equilibrium (in both operators of the blend), Ladd's two-step force
+    average, and BGK at lambda_e = 1.3 (B depends on tau = 1 / lambda_e).
+    Fields within 1e-12 of max|u|, states within 1e-12."""
+    le = 1.3 if option == "bgk_1.3" else 1.0
+    coll = "bgk" if option == "bgk_1.3" else "trt"
+    eq = "incompressible" if option == "incompressible" else "compressible"
+    g = Lattice(SHAPE, collision=coll, lambda_e=le, equilibrium=eq)
+    g.set_coupling("psm")
+    o = OracleSim(*SHAPE, lambda_e=le, collision=coll)
+    o.set_psm(True)
+    if option == "incompressible":
+        o.set_incompressible(True)
+    if option == "force_average":
+        g.set_force_average(True)
+        o.set_force_average(True)
+    gi = [g.add_squirmer(pos, e, R, B1, beta, mobile=True) for pos, e, R, B1, beta in SPHERES]
+    oi = [o.add_sphere(pos, e, R, B1, beta, mobile=True) for pos, e, R, B1, beta in SPHERES]
+    for n in (8, 40):
+        g.step(n)
+        o.step(n)
+        _, ug = g.fields()
+        _, uo = o.fields()
+        assert _rel(ug, uo) < 1e-12
+        for a, b in zip(gi, oi):
+            for x, y in zip(g.state(a), o.state(b)):
+                assert np.abs(x - y).max() < 1e-12, (x, y)
+    assert (g.solid_fraction() == o.eps()).all()
+    g.close()
+
+
 def test_psm_momentum_balance_at_96_cubed():
     """A free pusher (R = 8) in a 96^3 periodic box, 200 FP64 steps: every
     cell stays fluid, and fluid momentum plus M v stays zero to roundoff --
