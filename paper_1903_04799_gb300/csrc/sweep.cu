@@ -81,7 +81,7 @@ static int sm_count() {
 //   FP32 (two-cell form, 256^3): 0.959 -> 0.990 of the copy bandwidth;
 //   FP64 (double-float form): 256^3 0.65 -> 0.75 at 1 or 2 planes ahead,
 //     0.66 at 4, 0.60 at 5; 192^3 0.56 -> 0.72; 128^3 0.64 -> 0.78;
-//   FP16 (two-cell form): 0.745 -> 0.684, so 16-bit sweeps do not prefetch.
+//   16-bit sweeps: see prefetch_ahead16.
 // FP32 prefetches in whole-lattice sweeps only: a prefetch installs its lines
 // in L2 at normal priority, and beside the body kernels of a split step (far
 // sweeps) that evicted their code again (128^3 step 0.050 -> 0.056 ms).  The
@@ -92,6 +92,23 @@ static int prefetch_ahead(const SweepArgs& a, int storage, const dim3& grid) {
     const long long per_plane = (long long)grid.x * grid.y;
     const long long resident = (storage == ST_F32 ? 2LL : 3LL) * sm_count();
     const int ahead = (int)((resident + per_plane - 1) / per_plane) + (storage == ST_F32 ? 2 : 0);
+    return ahead < a.nz ? ahead : 0;
+}
+
+// Planes ahead for the L2 prefetch of the 16-bit sweeps (sweep_four_rows on
+// even steps, sweep_two on odd steps): `extra` past the planes the resident
+// blocks (two per SM) cover.  Measured on GB300 at 256^3 over both parities,
+// against no prefetch: FP16 0.765 -> 0.807 with the even steps' (2 past; 0 or
+// 4: the same within 0.3 %), -> 0.840 with the odd steps' too (0 past; 2 or
+// 4: within 0.4 %); BF16 0.679 -> 0.703 -> 0.710.  Split sweeps prefetch
+// too: the 256^3 pusher's whole step, FP16 0.2516 -> 0.2468 ms, BF16 0.2841 ->
+// 0.2850 ms.  (An earlier measurement of the two-cell form prefetching on both
+// parities, 0.745 -> 0.684, was taken before the sweeps' traffic was marked
+// evict-first.)
+static int prefetch_ahead16(const SweepArgs& a, const dim3& grid, int extra) {
+    const long long per_plane = (long long)grid.x * grid.y;
+    const long long resident = 2LL * sm_count();
+    const int ahead = (int)((resident + per_plane - 1) / per_plane) + extra;
     return ahead < a.nz ? ahead : 0;
 }
 
@@ -126,8 +143,10 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy
             const int tx = a.nx / 4, ty = (parity == 0 ? 256 : 192) / tx > 0 ? (parity == 0 ? 256 : 192) / tx : 1;
             dim3 block(tx, ty), grid(1, (gy + ty - 1) / ty, gz);
             if (parity == 0) {
-                if (o32) k_sweep4r<S, 0, true><<<grid, block, 0, st>>>(a);
-                else k_sweep4r<S, 0, false><<<grid, block, 0, st>>>(a);
+                SweepArgs b = a;
+                b.pf = prefetch_ahead16(a, grid, 2);
+                if (o32) k_sweep4r<S, 0, true><<<grid, block, 0, st>>>(b);
+                else k_sweep4r<S, 0, false><<<grid, block, 0, st>>>(b);
             } else {
                 const size_t smem = (size_t)10 * ty * a.nx * sizeof(unsigned short);
                 if (o32) k_sweep4r<S, 1, true><<<grid, block, smem, st>>>(a);
@@ -144,6 +163,7 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy
         dim3 block(bx, by), grid((pairs + bx - 1) / bx, (gy + by - 1) / by, gz);
         SweepArgs b = a;
         b.pf = prefetch_ahead(a, S, grid);
+        if (S == ST_F16 || S == ST_BF16) b.pf = parity == 1 ? prefetch_ahead16(a, grid, 0) : 0;
         if (o32) {
             if (parity == 0) k_sweep2<S, 0, true><<<grid, block, 0, st>>>(b);
             else k_sweep2<S, 1, true><<<grid, block, 0, st>>>(b);

@@ -633,6 +633,16 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
     unsigned short* rowbuf = buf + (int64_t)threadIdx.y * nx;  // + d * blockDim.y * nx for shifted direction d
     const int dstride = blockDim.y * nx;
     auto at = [&](int x) -> int { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
+    // even steps: L2 prefetch of the sources a.pf planes ahead (see sweep_two)
+    if (P == 0 && a.pf && active) {
+        const int zp = z + (a.reverse ? -a.pf : a.pf);
+        if (zp >= 0 && zp < nz) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(F + ((Off)i * Np + (Off)nx * ((Off)y + (Off)ny * (Off)zp) +
+                                                                   (Off)x0)));
+        }
+    }
     uint2 g[Q];
     int d = 0;
 #pragma unroll
