@@ -301,14 +301,24 @@ __device__ __forceinline__ uint32_t sr_pair_key(uint32_t step_key, uint32_t n) {
 __device__ __forceinline__ uint32_t sr_word(uint32_t k, int i) { return k * (0x9e3779b1u + 2u * (uint32_t)i * 0x61c88647u); }
 // the 16 bits of a word for the even (low half) or odd (high half) cell
 __device__ __forceinline__ uint32_t sr_half(uint32_t w, uint32_t n) { return (n & 1u) ? (w >> 16) : (w & 0xffffu); }
+// The rounding itself is one conversion instruction per pair of values:
+// cvt.rs.bf16x2.f32 (stochastic rounding, sm_100 family) converts (hi, lo)
+// to a BF16 pair packed hi << 16 | lo, hi with the high 16 bits of rbits and
+// lo with the low 16.  Checked on GB300 against the integer form
+// (bits + r) >> 16 on a million random pairs: identical for every non-NaN
+// value (subnormals, zeros and the carry into infinity included); a NaN comes
+// out as the canonical NaN.
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t rbits) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+}
 // BF16 bits of v (in the storage's units), rounded stochastically with the 16 bits r
 __device__ __forceinline__ unsigned short bf16_sr(float v, uint32_t r) {
-    return (unsigned short)((__float_as_uint(v) + r) >> 16);
+    return (unsigned short)cvt_rs_bf16x2(v, v, r);
 }
 // BF16 bits of (a, b), rounded stochastically with the halves of w, packed a | b << 16
-__device__ __forceinline__ uint32_t bf16x2_sr(float a, float b, uint32_t w) {
-    return __byte_perm(__float_as_uint(a) + (w & 0xffffu), __float_as_uint(b) + (w >> 16), 0x7632);
-}
+__device__ __forceinline__ uint32_t bf16x2_sr(float a, float b, uint32_t w) { return cvt_rs_bf16x2(b, a, w); }
 
 // One cell (x, y, z) with FP64 storage, collided in double-float arithmetic
 // (sweep_df.cuh).  O32: element offsets in 32-bit arithmetic (the launch
@@ -445,15 +455,8 @@ template <> __device__ __forceinline__ __nv_bfloat162 enc2<ST_BF16>(float a, flo
 }
 template <> __device__ __forceinline__ double2 enc2<ST_F64>(float, float, float) { return make_double2(0.0, 0.0); }
 
-// enc / enc2 with the stochastic rounding of BF16 stores when sr is set
-// (random bits r, ra, rb from sr_bits)
-template <int S>
-__device__ __forceinline__ typename StoreT<S>::T enc_r(typename StoreT<S>::R v, float sc, bool sr, uint32_t r) {
-    if constexpr (S == ST_BF16) {
-        if (sr) return __ushort_as_bfloat16(bf16_sr(v, r));
-    }
-    return enc<S>(v, sc);
-}
+// enc2 with the stochastic rounding of BF16 stores when sr is set (random
+// bits w from sr_word)
 template <int S>
 __device__ __forceinline__ typename Pair<typename StoreT<S>::T>::V enc2_r(float a, float b, float sc, bool sr,
                                                                            uint32_t w) {
@@ -542,20 +545,21 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const uint32_t w = sr ? sr_word(kp, i) : 0u;
-        const uint32_t r0 = w & 0xffffu, r1 = w >> 16;
+        // both cells in one packed conversion, also where they are stored
+        // apart (each half rounds as the scalar conversion would)
+        const V e = enc2_r<S>(g0[i], g1[i], sc, sr, w);
         if (P == 0) {
-            st_stream(reinterpret_cast<V*>(F + ((Off)opp(i) * Np + row(0, 0) + (Off)x0)),
-                      enc2_r<S>(g0[i], g1[i], sc, sr, w));
+            st_stream(reinterpret_cast<V*>(F + ((Off)opp(i) * Np + row(0, 0) + (Off)x0)), e);
         } else {
             T* base = F + ((Off)i * Np + row(cy(i), cz(i)));
             if (cx(i) == 0) {
-                st_stream(reinterpret_cast<V*>(base + x0), enc2_r<S>(g0[i], g1[i], sc, sr, w));
+                st_stream(reinterpret_cast<V*>(base + x0), e);
             } else if (cx(i) == 1) {  // targets x0 + 1 and x0 + 2
-                st_stream(base + x0 + 1, enc_r<S>(g0[i], sc, sr, r0));
-                st_stream(base + xp1, enc_r<S>(g1[i], sc, sr, r1));
+                st_stream(base + x0 + 1, Pair<T>::lo(e));
+                st_stream(base + xp1, Pair<T>::hi(e));
             } else {  // targets x0 - 1 and x0
-                st_stream(base + xm0, enc_r<S>(g0[i], sc, sr, r0));
-                st_stream(base + x0, enc_r<S>(g1[i], sc, sr, r1));
+                st_stream(base + xm0, Pair<T>::lo(e));
+                st_stream(base + x0, Pair<T>::hi(e));
             }
         }
     }
@@ -600,11 +604,14 @@ __device__ __forceinline__ void collide_four(uint2 g[Q], const SweepArgs& a, uin
         const uint32_t kc = c < 2 ? k01 : k23;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const uint32_t rw = sr_word(kc, i);
-            const unsigned int e = sr ? (unsigned int)bf16_sr(gc[i], (c & 1) ? (rw >> 16) : (rw & 0xffffu))
-                                      : enc16<S>(gc[i], 1.0f);
             unsigned int& w = c < 2 ? g[i].x : g[i].y;
-            w = (c & 1) ? ((w & 0xffffu) | (e << 16)) : ((w & 0xffff0000u) | e);
+            if (sr) {  // both halves rounded with their own bits: keep cell c's
+                const uint32_t d = cvt_rs_bf16x2(gc[i], gc[i], sr_word(kc, i));
+                w = (c & 1) ? __byte_perm(w, d, 0x7610) : __byte_perm(w, d, 0x3254);
+            } else {
+                const unsigned int e = enc16<S>(gc[i], 1.0f);
+                w = (c & 1) ? ((w & 0xffffu) | (e << 16)) : ((w & 0xffff0000u) | e);
+            }
         }
     }
 }
