@@ -478,8 +478,8 @@ __device__ __forceinline__ typename Pair<typename StoreT<S>::T>::V enc2_r(float 
 // thread of the one-cell form, for the same arithmetic per cell.
 // O32: element offsets in 32-bit arithmetic (the launch checks 19 Np < 2^32):
 // three instructions an access instead of about seven.
-template <int S, int P, bool O32 = false>
-__device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int z, uint32_t skey = 0u) {
+template <int S, int P, bool O32, bool SR>
+__device__ __forceinline__ void sweep_two_r(const SweepArgs& a, int x0, int y, int z, uint32_t skey) {
     using Off = typename std::conditional<O32, uint32_t, int64_t>::type;
     using ST = StoreT<S>;
     using T = typename ST::T;
@@ -539,7 +539,7 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
     }
     collide_trt<R, ST::dev>(g0, a.K, rho0);
     collide_trt<R, ST::dev>(g1, a.K, rho0);
-    const bool sr = S == ST_BF16 && a.sr;
+    constexpr bool sr = SR;
     // cells x0 and x0 + 1 (x0 even, nx even) form one pair of the random bits
     const uint32_t kp = sr ? sr_pair_key(skey, (uint32_t)x0 + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z)) : 0u;
 #pragma unroll
@@ -565,6 +565,20 @@ __device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int
     }
 }
 
+// The rounding mode is a compile-time branch of the two-cell body: one
+// uniform branch per thread instead of a select between two conversions at
+// every store.
+template <int S, int P, bool O32 = false>
+__device__ __forceinline__ void sweep_two(const SweepArgs& a, int x0, int y, int z, uint32_t skey = 0u) {
+    if constexpr (S == ST_BF16) {
+        if (a.sr) {
+            sweep_two_r<S, P, O32, true>(a, x0, y, z, skey);
+            return;
+        }
+    }
+    sweep_two_r<S, P, O32, false>(a, x0, y, z, skey);
+}
+
 template <int S> __device__ __forceinline__ float dec16(unsigned int h, float isc);
 template <> __device__ __forceinline__ float dec16<ST_F16>(unsigned int h, float isc) {
     return __half2float(__ushort_as_half((unsigned short)h)) * isc;
@@ -586,9 +600,9 @@ template <> __device__ __forceinline__ unsigned int enc16<ST_BF16>(float v, floa
 // units (see kScaled), encode (BF16 with stochastic rounding: the four cells
 // are two pairs of the random bits).  Every four-cell form calls this, so they
 // all give the same bits.
-template <int S>
-__device__ __forceinline__ void collide_four(uint2 g[Q], const SweepArgs& a, uint32_t skey, int x0, int y, int z) {
-    const bool sr = S == ST_BF16 && a.sr;
+template <int S, bool SR>
+__device__ __forceinline__ void collide_four_r(uint2 g[Q], const SweepArgs& a, uint32_t skey, int x0, int y, int z) {
+    constexpr bool sr = SR;
     const float rho0 = a.rho0s;  // scaled units (see kScaled)
     const uint32_t n0 = (uint32_t)x0 + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
     const uint32_t k01 = sr ? sr_pair_key(skey, n0) : 0u, k23 = sr ? sr_pair_key(skey, n0 + 2u) : 0u;
@@ -614,6 +628,16 @@ __device__ __forceinline__ void collide_four(uint2 g[Q], const SweepArgs& a, uin
             }
         }
     }
+}
+template <int S>
+__device__ __forceinline__ void collide_four(uint2 g[Q], const SweepArgs& a, uint32_t skey, int x0, int y, int z) {
+    if constexpr (S == ST_BF16) {
+        if (a.sr) {
+            collide_four_r<S, true>(g, a, skey, x0, y, z);
+            return;
+        }
+    }
+    collide_four_r<S, false>(g, a, skey, x0, y, z);
 }
 
 // 16-bit storages, four cells per thread, blocks of whole rows: a row of nx
