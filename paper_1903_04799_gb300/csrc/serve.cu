@@ -45,6 +45,8 @@ struct TileArgs {
 
 // A tile is the unit range [tile.y, tile.z) of one lattice, a unit being a cell
 // pair (paired tiles, nx even) or a cell, numbered x-fastest over the lattice.
+// A request holds fewer than 2^27 cells (validate), so every population index
+// of its lattice, below 19 x 2^27 < 2^32, fits the sweeps' 32-bit offsets.
 template <int P, int S>
 __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const int4 tile) {
     const uint32_t skey = S == ST_BF16 ? sr_step_key(a) : 0u;  // the lattice's own step (global - start)
@@ -56,11 +58,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, const int4 tile) 
         const int y = (int)(r % ny), z = (int)(r / ny);
         if constexpr (S != ST_F64) {
             if (tile.w) {
-                sweep_two<S, P>(a, 2 * xi, y, z, skey);
+                sweep_two<S, P, true>(a, 2 * xi, y, z, skey);
                 continue;
             }
         }
-        sweep_one<S, P>(a, xi, y, z, skey);
+        sweep_one<S, P, false, true>(a, xi, y, z, skey);
     }
 }
 

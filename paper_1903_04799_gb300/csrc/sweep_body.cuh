@@ -370,12 +370,13 @@ __device__ __forceinline__ void sweep_one_df(const SweepArgs& a, int x, int y, i
 }
 
 // One cell (x, y, z).  FP64 storage collides in double-float arithmetic
-// unless NATIVE (FP64 arithmetic, the measured reference form).
-template <int S, int P, bool NATIVE = false>
+// unless NATIVE (FP64 arithmetic, the measured reference form); O32 (caller
+// checks 19 Np < 2^32) gives that form 32-bit element offsets.
+template <int S, int P, bool NATIVE = false, bool O32 = false>
 __device__ __forceinline__ void sweep_one(const SweepArgs& a, int x, int y, int z, uint32_t skey = 0u) {
     if constexpr (S == ST_F64 && !NATIVE) {
-        if (a.K.df.le1) sweep_one_df<P, false, true>(a, x, y, z);
-        else sweep_one_df<P, false, false>(a, x, y, z);
+        if (a.K.df.le1) sweep_one_df<P, O32, true>(a, x, y, z);
+        else sweep_one_df<P, O32, false>(a, x, y, z);
     } else {
     using ST = StoreT<S>;
     using T = typename ST::T;
