@@ -595,6 +595,21 @@ template <> __device__ __forceinline__ unsigned int enc16<ST_BF16>(float v, floa
     return __bfloat16_as_ushort(__float2bfloat16_rn(v * sc));
 }
 
+// Both values of a pair rounded to nearest, packed a | b << 16.
+template <int S> __device__ __forceinline__ uint32_t enc16x2(float a, float b);
+template <> __device__ __forceinline__ uint32_t enc16x2<ST_F16>(float a, float b) {
+    const __half2 v = __floats2half2_rn(a, b);
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    return u;
+}
+template <> __device__ __forceinline__ uint32_t enc16x2<ST_BF16>(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    return u;
+}
+
 // Collision of four cells x0 .. x0 + 3 of row (y, z) (x0 and nx multiples of
 // 4) whose 16-bit populations g[i] hold two cells per 32-bit word (cell x0 in
 // the low half of .x), in place: decode, TRT in FP32 in the storage's scaled
@@ -607,26 +622,26 @@ __device__ __forceinline__ void collide_four_r(uint2 g[Q], const SweepArgs& a, u
     const float rho0 = a.rho0s;  // scaled units (see kScaled)
     const uint32_t n0 = (uint32_t)x0 + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
     const uint32_t k01 = sr ? sr_pair_key(skey, n0) : 0u, k23 = sr ? sr_pair_key(skey, n0 + 2u) : 0u;
+    // the cells in pairs (x0, x0 + 1) and (x0 + 2, x0 + 3): a pair's word of
+    // each population is decoded, both cells collide, and one packed
+    // conversion writes the word back (each half rounds as the scalar
+    // conversion would)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        float gc[Q];
+    for (int h = 0; h < 2; ++h) {
+        float ga[Q], gb[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const unsigned int w = c < 2 ? g[i].x : g[i].y;
-            gc[i] = dec16<S>((c & 1) ? (w >> 16) : (w & 0xffffu), 1.0f);
+            const unsigned int w = h == 0 ? g[i].x : g[i].y;
+            ga[i] = dec16<S>(w & 0xffffu, 1.0f);
+            gb[i] = dec16<S>(w >> 16, 1.0f);
         }
-        collide_trt<float, true>(gc, a.K, rho0);
-        const uint32_t kc = c < 2 ? k01 : k23;
+        collide_trt<float, true>(ga, a.K, rho0);
+        collide_trt<float, true>(gb, a.K, rho0);
+        const uint32_t kc = h == 0 ? k01 : k23;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            unsigned int& w = c < 2 ? g[i].x : g[i].y;
-            if (sr) {  // both halves rounded with their own bits: keep cell c's
-                const uint32_t d = cvt_rs_bf16x2(gc[i], gc[i], sr_word(kc, i));
-                w = (c & 1) ? __byte_perm(w, d, 0x7610) : __byte_perm(w, d, 0x3254);
-            } else {
-                const unsigned int e = enc16<S>(gc[i], 1.0f);
-                w = (c & 1) ? ((w & 0xffffu) | (e << 16)) : ((w & 0xffff0000u) | e);
-            }
+            const uint32_t e = sr ? cvt_rs_bf16x2(gb[i], ga[i], sr_word(kc, i)) : enc16x2<S>(ga[i], gb[i]);
+            (h == 0 ? g[i].x : g[i].y) = e;
         }
     }
 }
