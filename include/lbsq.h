@@ -355,7 +355,9 @@ int64_t lb_kernel_launches(const lb_ctx* c);
  * 0 = default: FP64 storage collided in double-float arithmetic (pairs of
  * FP32 numbers, about 47 significant bits), one cell per thread; FP32 with
  * even nx: two cells per thread with paired loads; FP16 / BF16: even steps
- * as 3, odd steps as 2.
+ * as 3, odd steps as 2, except in the split steps of a lattice whose bodies
+ * occupy a thin slab, where odd steps take four cells per thread without
+ * shared memory (nx a multiple of 4).
  * 1 = one cell per thread; for FP64 storage, FP64 arithmetic.
  * 2 = two cells per thread where nx is even (not FP64).
  * 3 = FP16 / BF16: four cells per thread in blocks of whole rows, the

@@ -63,6 +63,20 @@ __global__ void __launch_bounds__(P == 0 ? 256 : 192, 2) k_sweep4r(const SweepAr
     sweep_four_rows<S, P, O32>(a, y < 0 ? 0 : y, z, y >= 0, rowbuf, skey);
 }
 
+// 16-bit storages with nx % 4 == 0, odd steps of split sweeps: four cells per
+// thread without shared memory (see sweep_four_odd), blocks of at most 192
+// threads (167 registers, no spill; at 256 threads the 128-register cap
+// spills 72-80 bytes and measured 3-4 % slower).
+template <int S, bool O32>
+__global__ void __launch_bounds__(192, 2) k_sweep4o(const SweepArgs a) {
+    const uint32_t skey = S == ST_BF16 ? sr_step_key(a) : 0u;  // before any exit (see sr_step)
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int z = sweep_plane(a);
+    const int y = z < 0 ? -1 : sweep_row(a, blockIdx.y * blockDim.y + threadIdx.y, z);
+    if (x0 >= a.nx || y < 0) return;
+    sweep_four_odd<S, O32>(a, x0, y, z, skey);
+}
+
 static int sm_count() {
     static int n = 0;
     if (!n) {
@@ -135,9 +149,29 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy
     if constexpr (S == ST_F16 || S == ST_BF16) {
         // default: even steps in whole-row four-cell blocks (aligned 8-byte
         // chunks: 0.86 of the copy bandwidth at 256^3, against 0.74 for two
-        // cells), odd steps in the two-cell form (0.63; the whole-row form's
-        // odd steps, with their x-shifts through shared memory, measured 0.62)
+        // cells), odd steps in the two-cell form (0.63 before the L2
+        // prefetch; the whole-row form's odd steps, with their x-shifts
+        // through shared memory, measured 0.62), or in split sweeps as below
         const bool rows4 = a.nx % 4 == 0 && a.nx <= 768;
+        // odd steps of split sweeps (far and near, mode 1 and 2): four cells per
+        // thread.  Measured on GB300, 256^3 pusher, whole step against the
+        // two-cell form: FP16 0.242 -> 0.232 ms, BF16 with stochastic rounding
+        // 0.260 -> 0.252 ms (BF16 to nearest 0.243 -> 0.245).  In
+        // whole-lattice sweeps the two-cell form stays ahead (bare 256^3 step:
+        // FP16 0.210 against 0.214 ms, BF16 to nearest 0.211 against 0.223),
+        // so they keep it; why the split steps favour four cells is not known.
+        if (variant == 0 && parity == 1 && a.nx % 4 == 0 && a.zmode != 0) {
+            const int quads = a.nx / 4;
+            int bx = ((quads + 31) / 32) * 32;
+            if (bx > 64) bx = 64;
+            const int by = 192 / bx > 0 ? 192 / bx : 1;
+            dim3 block(bx, by), grid((quads + bx - 1) / bx, (gy + by - 1) / by, gz);
+            SweepArgs b = a;
+            b.pf = prefetch_ahead16(a, grid, 0);
+            if (o32) k_sweep4o<S, true><<<grid, block, 0, st>>>(b);
+            else k_sweep4o<S, false><<<grid, block, 0, st>>>(b);
+            return;
+        }
         if ((variant == 3 || (variant == 0 && parity == 0)) && rows4) {
             // odd steps (more live values) in blocks of at most 192 threads
             const int tx = a.nx / 4, ty = (parity == 0 ? 256 : 192) / tx > 0 ? (parity == 0 ? 256 : 192) / tx : 1;
@@ -183,7 +217,8 @@ static void launch_s(const SweepArgs& a, int parity, int variant, int gz, int gy
 
 // variant: 0 = default (FP64: double-float collision, one cell per thread;
 // FP32: two cells per thread (even nx); FP16 / BF16: even steps as 3, odd
-// steps as 2), 1 = one cell per thread (FP64: FP64 arithmetic), 2 = two
+// steps as 2, or four cells per thread without shared memory in split
+// sweeps), 1 = one cell per thread (FP64: FP64 arithmetic), 2 = two
 // cells per thread where possible (not FP64), 3 = FP16 / BF16: four cells per
 // thread in blocks of whole rows on both parities, odd-step x-shifts through
 // shared memory (nx % 4 == 0, nx <= 768; else as 2).

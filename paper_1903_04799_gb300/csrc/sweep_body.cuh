@@ -759,6 +759,72 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
     }
 }
 
+// 16-bit storages, odd steps, four cells x0 .. x0 + 3 per thread (x0 and nx
+// multiples of 4), no shared memory: each direction's four sources are the
+// aligned 8-byte chunk at x0, shifted by one element with the element beyond
+// its end (x0 - 1 for c_x = +1, x0 + 4 for c_x = -1, periodic) loaded on its
+// own; the four results go out as one aligned 4-byte store of the middle two
+// and 2-byte stores of the two ends.  Two memory instructions per direction
+// and four cells where the two-cell form issues four, and the same
+// collision (collide_four), so the same bits.
+template <int S, bool O32 = false>
+__device__ __forceinline__ void sweep_four_odd(const SweepArgs& a, int x0, int y, int z, uint32_t skey) {
+    using Off = typename std::conditional<O32, uint32_t, int64_t>::type;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+    const int xl = x0 == 0 ? nx - 1 : x0 - 1;   // x0 - 1
+    const int xr = x0 + 4 == nx ? 0 : x0 + 4;   // x0 + 4
+    unsigned short* __restrict__ F = (unsigned short*)a.F;
+    const Off Np = (Off)a.Np;
+    auto row = [&](int dy, int dz) -> Off { return (Off)nx * ((Off)ys[1 + dy] + (Off)ny * (Off)zs[1 + dz]); };
+    // L2 prefetch of the sources a.pf planes ahead in sweep order (see sweep_two)
+    if (a.pf) {
+        const int zp = z + (a.reverse ? -a.pf : a.pf);
+        if (zp >= 0 && zp < nz) {
+            const int zsp[3] = {zp == 0 ? nz - 1 : zp - 1, zp, zp == nz - 1 ? 0 : zp + 1};
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(
+                    F + ((Off)opp(i) * Np + (Off)nx * ((Off)ys[1 - cy(i)] + (Off)ny * (Off)zsp[1 - cz(i)]) + (Off)x0)));
+        }
+    }
+    // g[i]: cells x0, x0 + 1 in .x, x0 + 2, x0 + 3 in .y (low half first)
+    uint2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const unsigned short* base = F + ((Off)opp(i) * Np + row(-cy(i), -cz(i)));
+        const uint2 c = ld_stream(reinterpret_cast<const uint2*>(base + x0));
+        if (cx(i) == 0) {
+            g[i] = c;
+        } else if (cx(i) == 1) {  // sources x0 - 1 .. x0 + 2
+            const unsigned int e = ld_stream(base + xl);
+            g[i] = make_uint2(__byte_perm(e, c.x, 0x5410), __byte_perm(c.x, c.y, 0x5432));
+        } else {  // sources x0 + 1 .. x0 + 4
+            const unsigned int e = ld_stream(base + xr);
+            g[i] = make_uint2(__byte_perm(c.x, c.y, 0x5432), __byte_perm(c.y, e, 0x5432));
+        }
+    }
+    collide_four<S>(g, a, skey, x0, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        unsigned short* base = F + ((Off)i * Np + row(cy(i), cz(i)));
+        const uint2 o = g[i];
+        const unsigned int mid = __byte_perm(o.x, o.y, 0x5432);  // cells x0 + 1, x0 + 2
+        if (cx(i) == 0) {
+            st_stream(reinterpret_cast<uint2*>(base + x0), o);
+        } else if (cx(i) == 1) {  // targets x0 + 1 .. x0 + 4
+            st_stream(base + x0 + 1, (unsigned short)(o.x & 0xffffu));
+            st_stream(reinterpret_cast<unsigned int*>(base + x0 + 2), mid);
+            st_stream(base + xr, (unsigned short)(o.y >> 16));
+        } else {  // targets x0 - 1 .. x0 + 2
+            st_stream(base + xl, (unsigned short)(o.x & 0xffffu));
+            st_stream(reinterpret_cast<unsigned int*>(base + x0), mid);
+            st_stream(base + x0 + 2, (unsigned short)(o.y >> 16));
+        }
+    }
+}
+
 // Arguments of a sweep of lattice L.
 __host__ __device__ inline SweepArgs sweep_args(const Lattice& L, double lambda_e, double lambda_o) {
     SweepArgs a;
