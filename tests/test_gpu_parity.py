@@ -523,6 +523,35 @@ def test_near_window_split_bitwise(storage, variant):
             assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("nx", [16, 36])
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+def test_split_odd_steps_narrow_rows_bitwise(storage, nx):
+    """The 16-bit odd steps of split sweeps (four cells per thread, each
+    direction's sources an aligned chunk plus the element beyond its end)
+    against whole-lattice sweeps, on rows of 4 and 9 four-cell groups: most
+    threads of a warp hold no cells, and the groups at x = 0 and x = nx - 4
+    take their end elements across the periodic x boundary, which the swimmer
+    also crosses."""
+    shape = (nx, 40, 72)
+    runs = []
+    for traced in (False, True):
+        g = Lattice(shape, collision="trt", storage=storage)
+        gi = g.add_squirmer((0.6, 20.3, 30.2), (0.6, 0.2, 1.0), 3.0, 0.05, -2.0, mobile=True)
+        if traced:
+            g.profile_begin()
+        g.step(3)
+        g.step(40)
+        if traced:
+            g.profile_end()
+        runs.append((g.populations(), g.owner(), g.state(gi)))
+        g.close()
+    (fa, oa, sa), (fb, ob, sb) = runs
+    assert (oa == ob).all()
+    assert np.array_equal(fa, fb)
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)
+
+
 def _far_apart(g):
     # two isolated spheres 65 planes apart: the window spans the gap
     return [g.add_squirmer((48.3, 30.2, 40.1), (0.2, 0.1, 1.0), 5.0, 0.05, -3.0, mobile=True),
