@@ -764,9 +764,10 @@ __device__ __forceinline__ void sweep_four_rows(const SweepArgs& a, int y, int z
 // aligned 8-byte chunk at x0, shifted by one element with the element beyond
 // its end (x0 - 1 for c_x = +1, x0 + 4 for c_x = -1, periodic) loaded on its
 // own; the four results go out as one aligned 4-byte store of the middle two
-// and 2-byte stores of the two ends.  Two memory instructions per direction
-// and four cells where the two-cell form issues four, and the same
-// collision (collide_four), so the same bits.
+// and 2-byte stores of the two ends.  Per shifted direction and four cells
+// that is two loads and three stores, where two threads of the two-cell form
+// issue four of each; the collision is the same (collide_four), so are the
+// bits.
 template <int S, bool O32 = false>
 __device__ __forceinline__ void sweep_four_odd(const SweepArgs& a, int x0, int y, int z, uint32_t skey) {
     using Off = typename std::conditional<O32, uint32_t, int64_t>::type;
