@@ -755,6 +755,23 @@ def profile_psm(spec: str):
     print(f"profile-psm {st} {n}^3 {steps} steps: ok", flush=True)
 
 
+def profile_bodies(spec: str):
+    """The 200-squirmer suspension (256^3, R = 6), stepped STEPS times one
+    step per call (no graphs): for ncu captures of the fused body kernel with
+    many spheres (4-block clusters).  spec = STORAGE:STEPS."""
+    import torch
+    from paper_1903_04799_gb300 import workloads as W
+    st, steps = spec.split(":")
+    wl = W.c4_suspension()
+    g, _ = build_lattice(st, wl.shape, wl.bodies, wl.collision, wl.lambda_e, 0)
+    for _ in range(int(steps)):
+        g.step(1)
+    g.sync()
+    torch.cuda.synchronize()
+    g.close()
+    print(f"profile-bodies {st} {steps} steps: ok", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -776,6 +793,8 @@ def main():
                     help="step a bare N^3 lattice (sweep kernels only), for ncu captures, instead of the benchmark")
     ap.add_argument("--profile-psm", metavar="STORAGE:N:STEPS",
                     help="step the pusher under partially saturated cells, for ncu captures, instead of the benchmark")
+    ap.add_argument("--profile-bodies", metavar="STORAGE:STEPS",
+                    help="step the 200-squirmer suspension one step per call, for ncu captures, instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -783,6 +802,8 @@ def main():
         profile_sweep(args.profile_sweep)
     elif args.profile_psm:
         profile_psm(args.profile_psm)
+    elif args.profile_bodies:
+        profile_bodies(args.profile_bodies)
     elif args.impl == "reference":
         reference(args)
     elif args.precision_sweep:
