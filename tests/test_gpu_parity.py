@@ -523,7 +523,7 @@ def test_near_window_split_bitwise(storage, variant):
             assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("nx", [16, 36])
+@pytest.mark.parametrize("nx", [16, 36, 45, 50])
 @pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
 def test_split_odd_steps_narrow_rows_bitwise(storage, nx):
     """The 16-bit odd steps of split sweeps (four cells per thread, each
@@ -531,7 +531,8 @@ def test_split_odd_steps_narrow_rows_bitwise(storage, nx):
     against whole-lattice sweeps, on rows of 4 and 9 four-cell groups: most
     threads of a warp hold no cells, and the groups at x = 0 and x = nx - 4
     take their end elements across the periodic x boundary, which the swimmer
-    also crosses."""
+    also crosses.  Ragged rows (nx = 45: one cell per thread; nx = 50: two
+    cells per thread) take the other forms in both kinds of sweep."""
     shape = (nx, 40, 72)
     runs = []
     for traced in (False, True):
