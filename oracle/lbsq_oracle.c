@@ -55,7 +55,8 @@
  *   - mass M = density * 4/3 pi R^3, I = 2/5 M R^2, dt = 1, velocity first;
  *   - WCA force is -dU/dr of the shifted LJ potential, r the surface gap.
  *
- * Parity unpinned (no pin other than agreement with the CUDA library):
+ * Parity unpinned in value (no pin but agreement with the CUDA library and
+ * mirror symmetry, which a mirror-symmetric error passes):
  *   - the trajectories of a squirmer in a tube or near an obstacle (the
  *     boundary-element data the paper compares with are not in its text);
  *     the drag of a fixed sphere and the flow of the round tube are pinned.

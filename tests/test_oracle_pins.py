@@ -918,6 +918,62 @@ def test_round_tube_contact_points_to_the_axis():
     assert abs(v[1]) <= 1e-12 * abs(v[0])
 
 
+def _mirror_pair(setup, pos, e, steps, mirror_y):
+    """Two runs of a squirmer, the second started at the mirror image in y
+    (y -> mirror_y - y, e_y -> -e_y); their states after `steps`."""
+    out = []
+    for sgn in (1.0, -1.0):
+        s = setup()
+        p = (pos[0], pos[1] if sgn > 0 else mirror_y - pos[1], pos[2])
+        d = (e[0], sgn * e[1], e[2])
+        sid = s.add_sphere(p, d, 3.0, 0.01, -1.0, mobile=True)
+        s.step(steps)
+        out.append(s.state(sid))
+    return out
+
+
+def _assert_mirrored(a, b, mirror_y, tol):
+    (pa, va, ea, wa), (pb, vb, eb, wb) = a, b
+    assert abs(pa[0] - pb[0]) < tol and abs(pa[2] - pb[2]) < tol
+    assert abs(pa[1] + pb[1] - mirror_y) < tol
+    for x, y in ((va, vb), (ea, eb)):  # polar vectors: the y component flips
+        assert abs(x[0] - y[0]) < tol and abs(x[2] - y[2]) < tol and abs(x[1] + y[1]) < tol
+    # axial vector: under the mirror y -> -y, omega_x and omega_z flip
+    assert abs(wa[0] + wb[0]) < tol and abs(wa[1] - wb[1]) < tol and abs(wa[2] + wb[2]) < tol
+
+
+def test_round_tube_trajectory_mirror_symmetry():
+    """A swimmer off the axis of the round tube (Sec. V) and its mirror image
+    across the plane y = cy through the axis: the lattice, the tube's wall
+    nodes, the bounce-back and the conversions are all symmetric under the
+    mirror, so after 150 steps the two states are mirror images (position,
+    velocity and axis reflected, angular velocity as an axial vector) to
+    roundoff.  A wall term or index with a preferred side breaks this."""
+    n = 24
+
+    def setup():
+        s = O.OracleSim(n, n, 32, lambda_e=1.0, collision="trt")
+        s.add_tube(11.5, 11.5, 10.0)
+        return s
+
+    a, b = _mirror_pair(setup, (12.1, 13.25, 10.0), (0.2, 0.35, 1.0), 150, 23.0)
+    _assert_mirrored(a, b, 23.0, 1e-9)
+    assert abs(a[0][1] - 13.25) > 1e-4  # it moved across y
+
+
+def test_obstacle_orbit_mirror_symmetry():
+    """The obstacle set-up (Sec. V: a squirmer near a fixed sphere) and its
+    mirror image in y through the obstacle's centre: mirrored states after 150
+    steps, to roundoff."""
+    def setup():
+        s = O.OracleSim(32, 32, 32, lambda_e=1.0, collision="trt")
+        s.add_sphere((15.5, 15.5, 15.5), (0.0, 0.0, 1.0), 4.0, 0.0, 0.0, mobile=False)
+        return s
+
+    a, b = _mirror_pair(setup, (15.7, 24.25, 14.0), (0.1, -0.4, 1.0), 150, 31.0)
+    _assert_mirrored(a, b, 31.0, 1e-9)
+
+
 # ------------------------------------------------------- partially saturated cells
 
 def test_psm_fraction_sums_to_the_sphere_volume():
