@@ -106,7 +106,9 @@ typedef struct {
 } lb_allocator;
 
 typedef struct {
-    int32_t nx, ny, nz;  /* lattice size, each >= 1; nx*ny*nz < 2^31 */
+    int32_t nx, ny, nz;  /* lattice size, each >= 1; nx*ny*nz < 2^27 (a boundary link is
+                            coded in 32 bits as cell << 5 | direction); else
+                            lb_create returns LB_ERR_INVALID */
     int32_t collision;   /* lb_collision */
     double lambda_e;     /* even (viscous) relaxation rate, 0 < lambda_e < 2;
                             kinematic viscosity (1/lambda_e - 1/2)/3 (Sec. III) */

@@ -21,7 +21,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 from oracle.oracle import OracleSim  # noqa: E402
-from paper_1903_04799_gb300 import Lattice  # noqa: E402
+from paper_1903_04799_gb300 import Lattice, lbsq  # noqa: E402
 
 
 def rel(a, b):
@@ -79,6 +79,22 @@ def test_degenerate_lattices():
         g.step(5)
         o.step(5)
         assert np.abs(g.populations() - o.populations()).max() < 1e-14, shape
+
+
+def test_lattice_size_limits():
+    """lb_create admits fewer than 2^27 cells (boundary links are coded as
+    cell << 5 | direction in 32 bits): 512^3 = 2^27 is refused before any
+    allocation, 512 x 512 x 511 (FP16, 5 GB) is created and steps; a zero or
+    negative extent is refused."""
+    for shape in [(512, 512, 512), (0, 8, 8), (8, -1, 8)]:
+        with pytest.raises(lbsq.LBError) as ex:
+            Lattice(shape, collision="trt", storage="f16dev")
+        assert ex.value.status == lbsq.LB_ERR_INVALID
+    g = Lattice((512, 512, 511), collision="trt", storage="f16dev")
+    g.step(2)
+    _, P = g.mass()
+    assert np.abs(P).max() < 1e-6
+    g.close()
 
 
 def test_mass_momentum_conserved_f64():
