@@ -772,6 +772,24 @@ def profile_bodies(spec: str):
     print(f"profile-bodies {st} {steps} steps: ok", flush=True)
 
 
+def profile_serve(spec: str):
+    """The server with the first 24 requests of the serving mix resident
+    (FP32 and FP16-deviation lattices of 32^3 .. 160^3), advanced ROUNDS
+    rounds of 64 steps: for ncu launch lists and captures of the tile sweep
+    and the body kernels.  spec = ROUNDS."""
+    from paper_1903_04799_gb300 import lbsq
+    from paper_1903_04799_gb300 import workloads as W
+    srv = lbsq.Server(budget_bytes=4 << 30, max_resident=64, round_steps=64)  # the 24 requests need 1.7 GB
+    for m in W.serving_mix(n=24, rate=1.0):
+        srv.submit(lbsq.make_request(m.geometry, m.shape, m.storage, pos=m.pos, e=m.e, R=m.R, B1=m.B1,
+                                     beta=m.beta, obstacle=m.obstacle, wca=m.wca, steps=m.steps))
+    for _ in range(int(spec)):
+        srv.advance()
+    info = srv.info()
+    srv.close()
+    print(f"profile-serve {spec} rounds: ok ({info['cell_updates']} cell updates)", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -795,6 +813,8 @@ def main():
                     help="step the pusher under partially saturated cells, for ncu captures, instead of the benchmark")
     ap.add_argument("--profile-bodies", metavar="STORAGE:STEPS",
                     help="step the 200-squirmer suspension one step per call, for ncu captures, instead of the benchmark")
+    ap.add_argument("--profile-serve", metavar="ROUNDS",
+                    help="advance the server with 24 resident requests, for ncu captures, instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -804,6 +824,8 @@ def main():
         profile_psm(args.profile_psm)
     elif args.profile_bodies:
         profile_bodies(args.profile_bodies)
+    elif args.profile_serve:
+        profile_serve(args.profile_serve)
     elif args.impl == "reference":
         reference(args)
     elif args.precision_sweep:
